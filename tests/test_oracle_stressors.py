@@ -1,0 +1,189 @@
+"""Pins for the oracle's stressor checksums: brute force on tiny inputs written a
+second way, closed forms, and plausible-mistake detection."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import ifr_inputs as I
+import oracle
+
+
+def rotl(x, r):
+    r &= 31
+    return ((x << r) | (x >> (32 - r))) & 0xFFFFFFFF if r else x
+
+
+# ---------------------------------------------------------------- stream (L2/HBM)
+def _stream_brute(buf, chunk, A, k, count):
+    n_chunks = buf.size // chunk
+    mine = [c for c in range(n_chunks) if c % A == k]
+    if not mine:
+        return 0
+    X = [int(np.bitwise_xor.reduce(buf[c * chunk:(c + 1) * chunk])) for c in range(n_chunks)]
+    acc = 0
+    for j in range(count):
+        acc ^= rotl(X[mine[j % len(mine)]], j // len(mine))
+    return acc
+
+
+@pytest.mark.parametrize("A,k,count", [(3, 0, 1), (3, 2, 7), (5, 4, 40), (7, 1, 0), (4, 3, 13), (16, 9, 3)])
+def test_stream_checksum_brute(A, k, count):
+    buf = I.np_u32(1, np.arange(64 * 37))
+    assert oracle.stream_block_checksum(buf, 64, A, k, count) == _stream_brute(buf, 64, A, k, count)
+
+
+def test_stream_checksum_two_passes_closed_form():
+    buf = I.np_u32(11, np.arange(128 * 20))
+    A, k = 4, 1
+    mine = [c for c in range(20) if c % A == k]
+    Y = 0
+    for c in mine:
+        Y ^= int(np.bitwise_xor.reduce(buf[c * 128:(c + 1) * 128]))
+    assert oracle.stream_block_checksum(buf, 128, A, k, 2 * len(mine)) == Y ^ rotl(Y, 1)
+    # a dropped word changes the checksum
+    buf2 = buf.copy()
+    buf2[mine[0] * 128 + 5] ^= 1
+    assert oracle.stream_block_checksum(buf2, 128, A, k, 1) != oracle.stream_block_checksum(buf, 128, A, k, 1)
+
+
+# ---------------------------------------------------------------- FMA
+def _round_f32(q: Fraction) -> float:
+    """Correctly rounded (nearest, ties to even) fp32 value of a rational."""
+    if q == 0:
+        return 0.0
+    s = -1 if q < 0 else 1
+    a = abs(q)
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    if Fraction(2) ** e > a:
+        e -= 1
+    if Fraction(2) ** (e + 1) <= a:
+        e += 1
+    scaled = a * Fraction(2) ** (23 - e)
+    m = scaled.numerator // scaled.denominator
+    rem = scaled - m
+    if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and m % 2 == 1):
+        m += 1
+    return s * float(Fraction(m) * Fraction(2) ** (e - 23))
+
+
+def _f32_bits(v: float) -> int:
+    return int(np.array([v], np.float32).view(np.uint32)[0])
+
+
+def _fma_brute(seed, k, block, ilp, steps, rounds):
+    s0 = I.state0(seed)
+    r0 = fin = 0
+    for t in range(block):
+        for j in range(ilp):
+            g = (k * block + t) * ilp + j
+            u0, u1, u2 = (I.splitmix64_at(s0, 3 * g + q) for q in range(3))
+            x = Fraction((u0 >> 40) - 2**23, 2**23)
+            a = 1 - Fraction(1, 2**12) - Fraction(u1 >> 53, 2**23)
+            b = Fraction((u2 >> 40) - 2**23, 2**29)
+            for r in range(rounds):
+                for _ in range(steps):
+                    x = Fraction(_round_f32(x * a + b))
+                if r == 0:
+                    r0 ^= _f32_bits(float(x))
+            fin ^= _f32_bits(float(x))
+    return r0, fin
+
+
+def test_fma_exact_rational_brute_force():
+    assert oracle.fma_block(3, 2, 3, 2, 25, 2) == _fma_brute(3, 2, 3, 2, 25, 2)
+    assert oracle.fma_block(0, 0, 2, 1, 40, 1) == _fma_brute(0, 0, 2, 1, 40, 1)
+
+
+def test_fma_rounds_compose_and_fixed_point():
+    # two rounds of s steps == one round of 2s steps (final value)
+    assert oracle.fma_block(5, 1, 4, 2, 64, 2)[1] == oracle.fma_block(5, 1, 4, 2, 128, 1)[1]
+    # with |a| < 1 the chain converges towards b / (1 - a); fp32 rounding stalls it
+    # within about ulp(x*) / (1 - a) of the fixed point
+    s0 = I.state0(8)
+    u1 = I.splitmix64_at(s0, 1)
+    u2 = I.splitmix64_at(s0, 2)
+    a = 1 - 2.0**-12 - (u1 >> 53) * 2.0**-23
+    b = ((u2 >> 40) - 2**23) * 2.0**-29
+    _, fin = oracle.fma_block(8, 0, 1, 1, 200000, 1)
+    x = np.array([fin], np.uint32).view(np.float32)[0]
+    xs = b / (1 - a)
+    assert abs(float(x) - xs) <= 2.0 * abs(float(np.spacing(np.float32(xs)))) / (1 - a)
+
+
+# ---------------------------------------------------------------- shared memory
+def smem_word(lane, j, ways):
+    """(row, bank) -> word index for lane `lane`, iteration j, conflict degree `ways`."""
+    g, r = divmod(lane, ways)
+    groups = 32 // ways
+    bank = g + groups * (j % ways)
+    row = r + ways * (j // ways)
+    return row * 32 + bank
+
+
+@pytest.mark.parametrize("ways", [1, 2, 4, 8, 16, 32])
+def test_smem_mapping_bijective_and_conflict_degree(ways):
+    seen = set()
+    for j in range(32):
+        banks = {}
+        for lane in range(32):
+            w = smem_word(lane, j, ways)
+            assert w not in seen
+            seen.add(w)
+            banks.setdefault(w % 32, set()).add(w // 32)
+        # every bank touched by this warp instruction sees exactly `ways` distinct rows
+        assert all(len(rows) == ways for rows in banks.values())
+    assert len(seen) == 1024
+
+
+@pytest.mark.parametrize("ways", [1, 8, 32])
+def test_smem_brute_force_matches(ways):
+    seed, k, warps, rounds, passes = 6, 3, 2, 3, 2
+    s0 = I.state0(seed)
+    acc = 0
+    for w in range(warps):
+        mem = [I.splitmix64_at(s0, (k * warps + w) * 1024 + q) & 0xFFFFFFFF for q in range(1024)]
+        for _ in range(rounds * passes):
+            for j in range(32):
+                for lane in range(32):
+                    q = smem_word(lane, j, ways)
+                    mem[q] = (mem[q] * 1664525 + 1013904223) & 0xFFFFFFFF
+        for v in mem:
+            acc ^= v
+    assert oracle.smem_block(seed, k, warps, rounds, passes) == acc
+
+
+def test_lcg_power_geometric_closed_form():
+    a, c = 1664525, 1013904223
+    for n in (0, 1, 2, 17, 1000):
+        A, C = oracle.lcg_power(n)
+        assert A == pow(a, n, 2**32)
+        assert C == (c * ((a**n - 1) // (a - 1))) % 2**32
+
+
+# ---------------------------------------------------------------- tensor
+@pytest.mark.parametrize("k,group", [(0, 1), (3, 256), (7, 64)])
+def test_tensor_matches_integer_matmul(k, group):
+    s0 = I.state0(12)
+    idx = np.arange(8192, dtype=np.uint64)
+    u_a = I.np_u64(12, np.uint64(k * 16384) + idx)
+    u_b = I.np_u64(12, np.uint64(k * 16384 + 8192) + idx)
+    A = ((u_a >> np.uint64(32)) % np.uint64(5)).astype(np.int64).reshape(128, 64) - 2
+    B = ((u_b >> np.uint64(32)) % np.uint64(5)).astype(np.int64).reshape(128, 64) - 2
+    C = (A @ B.T) * group
+    assert np.abs(C).max() < 2**24
+    want = int(np.bitwise_xor.reduce(C.astype(np.float32).view(np.uint32).ravel()))
+    assert oracle.tensor_block(12, k, group) == want
+    assert s0 == 12 << 32
+
+
+# ---------------------------------------------------------------- scheduler
+def test_sched_brute_force():
+    seed = 0xDEADBEEF12
+    acc = 0
+    for q in range(1500):
+        y = (q ^ seed) & 0xFFFFFFFF
+        for _ in range(16):
+            y = (y * 1664525 + 1013904223) & 0xFFFFFFFF
+        acc ^= y
+    assert oracle.sched_checksum(seed, 1500, 16) == acc
