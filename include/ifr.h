@@ -1,0 +1,267 @@
+/*
+ * ifr.h — C ABI of libifr, the B300 (sm_103a) interference-sensitivity library.
+ *
+ * The method (Elvinger, Strati, Enright Jerger, Klimovic, "Understanding GPU
+ * Resource Interference One Level Deeper", SoCC '25):
+ *   - Sec. 1 and Sec. 4.1: quantify a workload's sensitivity to each GPU resource
+ *     by colocating it with custom stressor benchmarks, each of which stresses one
+ *     resource and holds a constant interference level for the whole life of the
+ *     colocated workload; intra-SM colocation uses CUDA streams, inter-SM
+ *     colocation partitions the SMs.
+ *   - Sec. 4.3 / 4.4: slowdown = latency colocated / latency in isolation.
+ *   - Sec. 5.1: a kernel-level estimator that combines each kernel's metrics and
+ *     resource sensitivity to predict its slowdown.
+ *
+ * Conventions for every entry point:
+ *   - Return value: IFR_OK (0) or a negative IFR_ERR_* status; nothing aborts the
+ *     process.  ifr_strerror() names a status.
+ *   - Device pointers are plain CUDA device addresses owned by the caller (for
+ *     example torch tensors' data_ptr()); the library never frees them.  Host
+ *     pointers are plain host memory owned by the caller.
+ *   - Streams are cudaStream_t values passed as void*; NULL selects the context's
+ *     own stream for that role.
+ *   - The context (ifr_ctx) owns its streams, per-run device scratch (flags,
+ *     counters, per-block logs), events and green contexts.  One context per host
+ *     thread; calls on one context are not thread-safe.
+ *   - Every device-side wait in the library's kernels is bounded by a deadline
+ *     (%globaltimer) and an iteration cap; on expiry the kernel records
+ *     IFR_ERR_TIMEOUT / IFR_ERR_NOT_RESIDENT and returns.
+ */
+#ifndef IFR_H
+#define IFR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IFR_ABI_VERSION 1
+
+/* ---- status codes ------------------------------------------------------- */
+#define IFR_OK 0
+#define IFR_ERR_ARG (-1)          /* invalid argument (null, size, alignment, kind) */
+#define IFR_ERR_CUDA (-2)         /* a CUDA runtime/driver call failed */
+#define IFR_ERR_TIMEOUT (-3)      /* a device or host wait reached its deadline */
+#define IFR_ERR_NOT_RESIDENT (-4) /* the stressor never became resident before the victim */
+#define IFR_ERR_LAUNCH (-5)       /* a kernel launch was rejected */
+#define IFR_ERR_BOUNDS (-6)       /* a checked build caught an out-of-range index */
+#define IFR_ERR_UNSUPPORTED (-7)  /* feature unavailable on this device / driver */
+#define IFR_ERR_NOMEM (-8)        /* context scratch allocation failed */
+#define IFR_ERR_CAPACITY (-9)     /* output array too small / no free slot */
+#define IFR_ERR_INVALID_CELL (-10) /* a measurement violated the constant-interference rule */
+#define IFR_ERR_HOL (-11)         /* no victim block could become co-resident with the stressor
+                                     (block-scheduler head-of-line blocking, Sec. 4.2); the
+                                     stressor gave up so the victim could run */
+
+#define IFR_MAX_STRESSORS 16
+#define IFR_MAX_LEVELS 16
+#define IFR_MAX_SMS 256
+
+typedef struct ifr_ctx ifr_ctx;
+
+/* ---- context ------------------------------------------------------------ */
+typedef struct {
+    int32_t device, num_sms, cc_major, cc_minor;
+    int64_t l2_bytes;              /* cudaDevAttrL2CacheSize */
+    int32_t smem_per_sm;           /* bytes */
+    int32_t smem_per_block_optin;  /* bytes */
+    int32_t regs_per_sm, max_threads_per_sm, max_blocks_per_sm;
+    int32_t sm_clock_khz, mem_clock_khz, mem_bus_width_bits;
+    int64_t global_mem_bytes;
+    char name[128];
+} ifr_device_info;
+
+/* Create a context on CUDA device `device`: queries the device, creates the
+ * stressor / victim / control streams and allocates per-slot scratch.  The
+ * device must be sm_100-family (this build carries sm_103a code only).
+ * Errors: IFR_ERR_ARG (null out), IFR_ERR_CUDA, IFR_ERR_UNSUPPORTED (wrong arch). */
+int ifr_init(int device, ifr_ctx **out);
+/* Destroy a context; waits (bounded) for its streams.  NULL is a no-op. */
+void ifr_shutdown(ifr_ctx *ctx);
+/* Static string for a status code. */
+const char *ifr_strerror(int status);
+int ifr_abi_version(void);
+int ifr_device_query(ifr_ctx *ctx, ifr_device_info *out);
+/* Number of kernels this context has enqueued so far (each replay of a captured
+ * graph adds its kernel nodes).  Errors: IFR_ERR_ARG. */
+int ifr_launch_count(ifr_ctx *ctx, uint64_t *out);
+
+/* ---- stressors (Sec. 3, Sec. 4.2-4.4) ----------------------------------- */
+/* The paper's stressors: block-scheduler (sleep) kernel Sec. 4.2; compute kernel
+ * (independent fp32 multiplies, ILP knob) Sec. 3 and Sec. 4.4.2; copy kernel over
+ * an L2-sized or HBM-sized buffer Sec. 4.3; n-strided shared-memory copy Sec.
+ * 4.4.1.  The tensor-pipe stressor follows the pipe-utilisation metric of
+ * Sec. 2.2.  Each kernel folds what it touched into a checksum (see the oracle). */
+typedef enum {
+    IFR_S_SCHED = 0,    /* short blocks: block dispatch and SM block slots */
+    IFR_S_FMA = 1,      /* dependent fp32 FMA chains, ILP independent chains/thread */
+    IFR_S_TENSOR = 2,   /* BF16 tcgen05 MMA loop, 128x128x64 tiles, TMEM accumulator */
+    IFR_S_SMEM_CF = 3,  /* shared-memory ld/st, conflict-free (1 wavefront / request) */
+    IFR_S_SMEM_32W = 4, /* shared-memory ld/st, 32-way bank conflicts */
+    IFR_S_L2 = 5,       /* streaming XOR read of an L2-resident buffer */
+    IFR_S_HBM = 6,      /* streaming XOR read of an HBM-sized buffer */
+    IFR_S_COUNT = 7
+} ifr_stressor_kind;
+
+typedef struct {
+    int32_t kind;            /* ifr_stressor_kind */
+    int32_t sm_count;        /* SMs the stressor may occupy: 0 = none (harness-only
+                                launch, "intensity 0"), num_sms = all.  The SMs are
+                                spread evenly over the SM id range. */
+    int32_t blocks_per_sm;   /* persistent blocks per allowed SM (0 = kind default) */
+    int32_t block;           /* threads per block (0 = kind default) */
+    int32_t ilp;             /* FMA: independent chains per thread (1,2,4,8; 0 = 4) */
+    int32_t smem_ways;       /* SMEM: bank-conflict degree 1..32 power of 2 (0 = kind) */
+    float duty;              /* active fraction of each period, (0, 1]; 0 or 1 = always */
+    int32_t period_ns;       /* duty-cycle period (0 = 100000) */
+    int64_t working_set_bytes; /* L2/HBM: bytes of buf streamed; multiple of block*64 */
+    const void *buf;         /* L2/HBM: device buffer of >= working_set_bytes, 16-B aligned */
+    uint64_t seed;           /* private seed for FMA / SMEM / TENSOR / SCHED values */
+    int64_t max_rounds;      /* > 0: each block stops after this many rounds (fixed work);
+                                0: run until stopped or the deadline */
+    int32_t sched_blocks;    /* SCHED: blocks per launch (0 = 100000) */
+    int32_t sched_launches;  /* SCHED: launches enqueued (0 = 64) */
+    int32_t sched_cycles;    /* SCHED: busy cycles per block (0 = 100) */
+    int32_t mask_mode;       /* 0: shared SMs, %smid filter; 1: green-context partition */
+    uint64_t deadline_ns;    /* device-side limit on the run (0 = 2 s) */
+} ifr_stressor_cfg;
+
+typedef struct {
+    uint32_t checksum;       /* XOR of the per-block checksums (SCHED: of all blocks) */
+    int32_t status;          /* first error recorded by any block, or IFR_OK */
+    uint64_t rounds;         /* rounds summed over active blocks (SCHED: working blocks) */
+    uint64_t work;           /* kind units: chunks (L2/HBM), FMA steps/thread-chain,
+                                smem ld/st pairs/lane, tile MMAs, busy blocks (SCHED) */
+    uint64_t t_start_ns;     /* earliest active-block start (%globaltimer) */
+    uint64_t t_start_last_ns;/* latest active-block start */
+    uint64_t t_end_first_ns; /* earliest active-block end */
+    uint64_t t_end_ns;       /* latest active-block end */
+    int32_t blocks_launched; /* grid size (SCHED: blocks over all launches) */
+    int32_t blocks_active;   /* blocks that passed the SM filter and worked */
+    int32_t sms_used;        /* distinct SMs with an active block */
+    int32_t planned_active;  /* sm_count * blocks_per_sm (work-split stride) */
+    double elapsed_ms;       /* cudaEvent time from launch to completion */
+} ifr_stressor_result;
+
+typedef struct {
+    uint64_t t_start_ns, t_end_ns; /* %globaltimer at block entry / exit */
+    uint64_t rounds;               /* rounds this block completed */
+    uint64_t work;                 /* kind units this block completed */
+    uint32_t checksum;             /* per-block checksum (FMA: after round 0) */
+    uint32_t checksum2;            /* FMA: after the last round; else 0 */
+    uint32_t smid;
+    int32_t index;                 /* active-block index k (claim order) */
+    int32_t status;
+    uint32_t reserved;
+} ifr_block_log;
+
+/* Launch a stressor on `stream` (NULL = the context's stressor stream) and return
+ * a handle.  Non-blocking.  Persistent kinds launch num_sms * blocks_per_sm
+ * blocks; a block that lands on an SM outside the mask, or beyond blocks_per_sm
+ * on its SM, exits at once.  Runs until ifr_stressor_stop, max_rounds, or the
+ * deadline.  Errors: IFR_ERR_ARG, IFR_ERR_CAPACITY (no free slot), IFR_ERR_LAUNCH. */
+int ifr_stressor_launch(ifr_ctx *ctx, const ifr_stressor_cfg *cfg, void *stream, int *handle_out);
+/* Ask the stressor to stop.  stream != NULL: the stop is enqueued on that stream
+ * (it takes effect after the work queued there, e.g. the victim launches);
+ * stream == NULL: the stop is written at once from the host. */
+int ifr_stressor_stop(ifr_ctx *ctx, int handle, void *stream);
+/* Wait (host, bounded by timeout_ms; 0 = 10000) for the stressor to finish, then
+ * fill *out.  On host timeout the stop flag is set and IFR_ERR_TIMEOUT returned. */
+int ifr_stressor_wait(ifr_ctx *ctx, int handle, int timeout_ms, ifr_stressor_result *out);
+/* Copy the per-block logs of a finished stressor (active blocks, index order). */
+int ifr_stressor_block_logs(ifr_ctx *ctx, int handle, ifr_block_log *out, int cap, int *n_out);
+/* Free the slot of a finished stressor. */
+int ifr_stressor_release(ifr_ctx *ctx, int handle);
+
+/* ---- victims ------------------------------------------------------------ */
+/* Workloads whose slowdown is measured (Sec. 4: the paper uses LLM decode and
+ * torch.mm; this library uses kernels with textbook definitions). */
+typedef enum {
+    IFR_V_TRIAD = 0,     /* a[i] = b[i] + s*c[i]; fp32; n elements */
+    IFR_V_GEMM = 1,      /* C[m][n] = sum_k A[m][k] B[n][k]; A MxK, B NxK bf16; C fp32 */
+    IFR_V_GEMV = 2,      /* y[r] = sum_c A[r][c] x[c]; A m x k bf16 row-major; y fp32 */
+    IFR_V_LAYERNORM = 3, /* per row (m rows, n cols): (x-mean)/sqrt(var+eps); fp32 */
+    IFR_V_SOFTMAX = 4,   /* per row (m rows, n cols): exp(x-max)/sum; fp32 */
+    IFR_V_HIST = 5,      /* 256-bin histogram of key & 255; n int32 keys; u32 bins */
+    IFR_V_COUNT = 6
+} ifr_victim_kind;
+
+typedef struct {
+    int32_t kind;          /* ifr_victim_kind */
+    int32_t repeats;       /* K back-to-back launches per measurement (0 = 1) */
+    int64_t m, n, k;       /* shapes, see ifr_victim_kind */
+    float scalar;          /* TRIAD s */
+    float eps;             /* LAYERNORM eps (0 = 1e-5) */
+    const void *in0;       /* TRIAD b | GEMM A | GEMV A | LN/SOFTMAX x | HIST keys */
+    const void *in1;       /* TRIAD c | GEMM B | GEMV x */
+    void *out;             /* TRIAD a | GEMM C | GEMV y | LN/SOFTMAX y | HIST bins */
+    int32_t grid;          /* blocks (0 = kind default) */
+    int32_t block;         /* threads per block (0 = kind default) */
+} ifr_victim_cfg;
+
+typedef struct {
+    uint64_t t_start_ns;   /* earliest block entry over the K launches (%globaltimer) */
+    uint64_t t_end_ns;     /* latest block exit over the K launches */
+    double event_ms;       /* cudaEvent time around the K launches */
+    int32_t status;        /* IFR_OK, or IFR_ERR_NOT_RESIDENT from the residency wait */
+    int32_t sms_touched;   /* distinct SMs that ran a victim block */
+    int32_t blocks;        /* blocks executed over the K launches */
+    int32_t repeats;       /* K */
+} ifr_timing;
+
+/* Run K back-to-back launches of a victim on `stream` (NULL = context victim
+ * stream), wait for them and fill *out (may be NULL to skip timing read-back,
+ * then the call still synchronises).  Errors: IFR_ERR_ARG (shape, null or
+ * misaligned pointer), IFR_ERR_LAUNCH, IFR_ERR_CUDA. */
+int ifr_victim_launch(ifr_ctx *ctx, const ifr_victim_cfg *cfg, void *stream, ifr_timing *out);
+
+/* ---- sweep (Sec. 4.1 method) -------------------------------------------- */
+typedef struct {
+    int32_t n_victims;
+    const ifr_victim_cfg *victims;
+    int32_t n_stressors;
+    int32_t n_levels;                    /* levels 1..L per stressor (level 0 is added) */
+    const ifr_stressor_cfg *levels;      /* [n_stressors][n_levels] full configurations */
+    int32_t repeats;                     /* measurements per cell */
+    int32_t batched;                     /* 0: launch per cell; 1: one captured CUDA graph
+                                            per (stressor, level) over all victims */
+} ifr_sweep_plan;
+
+typedef struct {
+    int32_t victim, stressor, level, repeat; /* stressor -1 = solo; level 0 = zero-SM stressor */
+    ifr_timing timing;
+    ifr_stressor_result stress;               /* zeroed for solo cells */
+    int32_t valid;                            /* constant-interference rule met (Sec. 4.1) */
+    int32_t status;
+} ifr_cell_result;
+
+/* Run the plan: per repeat, solo runs of every victim, then for every stressor
+ * and level 0..L a colocated measurement of every victim.  Writes up to `cap`
+ * cells in that order and sets *n_out.  Errors: IFR_ERR_ARG, IFR_ERR_CAPACITY,
+ * IFR_ERR_CUDA.  A cell whose stressor timed out is recorded with valid = 0. */
+int ifr_sweep(ifr_ctx *ctx, const ifr_sweep_plan *plan, ifr_cell_result *cells, size_t cap, size_t *n_out);
+
+/* ---- sensitivity reduction (Sec. 4.3 slowdown; Sec. 5.1 estimator input) - */
+typedef struct {
+    int32_t n_stressors, n_levels;
+    double t0_ns;                                       /* median solo duration per launch */
+    double noise;                                       /* (max-min)/median of solo */
+    double slowdown[IFR_MAX_STRESSORS][IFR_MAX_LEVELS + 1]; /* NaN where no valid cell */
+    double S[IFR_MAX_STRESSORS];                        /* slowdown at level L minus 1 */
+    double auc[IFR_MAX_STRESSORS];                      /* trapezoid of slowdown-1 over x */
+    int32_t monotone[IFR_MAX_STRESSORS];
+    int32_t n_valid, n_invalid;
+} ifr_sensitivity_out;
+
+/* Pure host reduction of one victim's cells (see the oracle's reduction for the
+ * exact rule).  intensity: [n_stressors][n_levels] achieved fraction x_l of each
+ * level, or NULL for x_l = l / n_levels.  Errors: IFR_ERR_ARG. */
+int ifr_sensitivity(const ifr_cell_result *cells, size_t n, int victim, int n_stressors, int n_levels,
+                    const double *intensity, ifr_sensitivity_out *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IFR_H */

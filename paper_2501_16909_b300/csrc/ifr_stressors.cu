@@ -1,0 +1,669 @@
+// Resource stressors (Sec. 3 compute/copy kernels, Sec. 4.2 block-scheduler kernel,
+// Sec. 4.3 copy kernel over L2- and HBM-sized buffers, Sec. 4.4.1 strided
+// shared-memory copy, Sec. 4.4.2 compute kernel with an ILP knob).
+//
+// Persistent kinds share one skeleton:
+//   entry   thread 0 claims a slot on its SM (mask + blocks_per_sm); blocks that
+//           fail exit at once.  The claim order gives the active index k.
+//   rounds  thread 0 decides once per round (stop flag, max_rounds, deadline,
+//           duty-cycle off phase) and broadcasts through shared memory.
+//   exit    per-block log: %globaltimer entry/exit, rounds, work, checksums, %smid.
+// Every wait (duty-cycle sleep, residency wait) is bounded by the block's deadline
+// and an iteration cap; on expiry the block records IFR_ERR_TIMEOUT and returns.
+#include <stdio.h>
+#include <string.h>
+#include <time.h>
+
+#include "ifr_internal.cuh"
+
+namespace {
+
+constexpr int kStreamChunksPerRound = 4;  // L2/HBM: chunks per round
+constexpr int kFmaSteps = 4096;           // FMA: steps per chain per round
+constexpr int kSmemPasses = 8;            // SMEM: passes over the warp array per round
+constexpr int kSchedLcgSteps = 16;        // SCHED: LCG steps per block result
+constexpr uint32_t kMaxSpin = 1u << 22;   // iteration cap of every sleep loop
+
+struct BlockCtl {
+    int k;            // active index, -1 = not active
+    uint64_t t0;      // entry time
+    uint64_t deadline;
+    int status;
+};
+
+__device__ __forceinline__ bool sm_allowed(const StressParams &p, uint32_t sm) {
+    return sm < IFR_MAX_SMS && ((p.mask[sm >> 5] >> (sm & 31)) & 1u);
+}
+
+__global__ void stress_reset_kernel(DevStress *st) {
+    for (int i = threadIdx.x; i < IFR_MAX_SMS; i += blockDim.x) st->sm_claim[i] = 0u;
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+        st->sched_xor[i] = 0u;
+        st->sched_cnt[i] = 0u;
+    }
+    if (threadIdx.x == 0) {
+        st->stop = 0u;
+        st->arrived = 0u;
+        st->active = 0u;
+        st->status = 0;
+        st->t_origin = 0ull;
+        st->t_first_start = ~0ull;
+        st->t_last_end = 0ull;
+    }
+}
+
+// Thread 0 only.  Claims an SM slot; returns the active index or -1.
+__device__ int claim_slot(DevStress *st, const StressParams &p, uint32_t sm) {
+    int k = -1;
+    if (sm_allowed(p, sm)) {
+        uint32_t slot = atomicAdd(&st->sm_claim[sm], 1u);
+        if (slot < (uint32_t)p.bps) {
+            int kk = (int)atomicAdd(&st->active, 1u);
+            if (kk < p.planned) k = kk;
+        }
+    }
+    __threadfence();
+    atomicAdd(&st->arrived, 1u);
+    return k;
+}
+
+// Thread 0 only: should the block run round `round`?  Sleeps through the
+// off phase of the duty cycle.
+__device__ int round_decision(DevStress *st, const StressParams &p, int64_t round, BlockCtl &c) {
+    if (p.max_rounds > 0 && round >= p.max_rounds) return 0;
+    if (ifr_ld_volatile(&st->stop)) return 0;
+    uint64_t now = ifr_gtimer();
+    if (now >= c.deadline) {
+        c.status = IFR_ERR_TIMEOUT;
+        return 0;
+    }
+    if (p.progress) {
+        // head-of-line watch: a victim block must have entered or left within hol_ns
+        uint64_t last = *(const volatile uint64_t *)p.progress;
+        if (last < c.t0) last = c.t0;
+        if (now > last + p.hol_ns) {
+            c.status = IFR_ERR_HOL;
+            return 0;
+        }
+    }
+    if (p.duty > 0.f && p.duty < 1.f) {
+        const uint64_t per = p.period_ns ? p.period_ns : 100000u;
+        const uint64_t on = (uint64_t)((double)per * (double)p.duty);
+        uint64_t ph = now % per;
+        if (ph >= on) {
+            const uint64_t target = now - ph + per;
+            uint32_t it = 0;
+            while (now < target) {
+                if (now >= c.deadline) {
+                    c.status = IFR_ERR_TIMEOUT;
+                    return 0;
+                }
+                if (ifr_ld_volatile(&st->stop) || ++it > kMaxSpin) return 0;
+                uint64_t left = target - now;
+                __nanosleep((unsigned)(left > 20000u ? 20000u : left));
+                now = ifr_gtimer();
+            }
+        }
+    }
+    return 1;
+}
+
+__device__ void write_log(const StressParams &p, DevStress *st, const BlockCtl &c, int64_t rounds, uint64_t work,
+                          uint32_t cs, uint32_t cs2) {
+    ifr_block_log L;
+    L.t_start_ns = c.t0;
+    L.t_end_ns = ifr_gtimer();
+    L.rounds = (uint64_t)rounds;
+    L.work = work;
+    L.checksum = cs;
+    L.checksum2 = cs2;
+    L.smid = ifr_smid();
+    L.index = c.k;
+    L.status = c.status;
+    L.reserved = 0u;
+    p.logs[c.k] = L;
+    if (c.status != 0) atomicCAS(&st->status, 0, c.status);
+}
+
+// Common entry; returns false (whole block) when the block is not active.
+__device__ __forceinline__ bool block_enter(DevStress *st, const StressParams &p, BlockCtl &c, int *s_k,
+                                            uint64_t *s_t0) {
+    if (threadIdx.x == 0) {
+        uint64_t t = ifr_gtimer();
+        *s_k = claim_slot(st, p, ifr_smid());
+        *s_t0 = t;
+    }
+    __syncthreads();
+    c.k = *s_k;
+    c.t0 = *s_t0;
+    c.deadline = c.t0 + p.deadline_ns;
+    c.status = 0;
+    return c.k >= 0;
+}
+
+// ------------------------------------------------------------------ L2 / HBM
+__device__ __forceinline__ int4 ld_stream(const int4 *p) {
+    int4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.s32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+__global__ void __launch_bounds__(1024) stream_stress_kernel(DevStress *st, StressParams p) {
+    __shared__ int s_k;
+    __shared__ uint64_t s_t0;
+    __shared__ int s_go[2];
+    __shared__ uint32_t s_red[32];
+    BlockCtl c;
+    if (!block_enter(st, p, c, &s_k, &s_t0)) return;
+    const int64_t A = p.planned;
+    const int64_t k = c.k;
+    const int vpc = (int)blockDim.x * 4;  // int4 per chunk
+    int64_t cpos = k, pass = 0, done = 0;
+    uint32_t acc = 0u;
+    int64_t round = 0;
+    const bool has_work = k < p.n_chunks;
+    for (;; ++round) {
+        if (threadIdx.x == 0) s_go[round & 1] = has_work ? round_decision(st, p, round, c) : 0;
+        __syncthreads();
+        if (!s_go[round & 1]) break;
+        int4 v[kStreamChunksPerRound][4];
+        int64_t ps[kStreamChunksPerRound];
+#pragma unroll
+        for (int r = 0; r < kStreamChunksPerRound; ++r) {
+            const int4 *src = p.buf + cpos * vpc + threadIdx.x;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[r][u] = ld_stream(src + u * blockDim.x);
+            ps[r] = pass;
+            cpos += A;
+            if (cpos >= p.n_chunks) {
+                cpos = k;
+                ++pass;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < kStreamChunksPerRound; ++r) {
+            uint32_t x = 0u;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x ^= (uint32_t)(v[r][u].x ^ v[r][u].y ^ v[r][u].z ^ v[r][u].w);
+            acc ^= ifr_rotl(x, (uint32_t)ps[r]);
+        }
+        done += kStreamChunksPerRound;
+    }
+    uint32_t cs = ifr_block_xor(acc, s_red);
+    if (threadIdx.x == 0) write_log(p, st, c, round, (uint64_t)done, cs, 0u);
+}
+
+// ------------------------------------------------------------------ FP32 FMA
+template <int ILP>
+__global__ void __launch_bounds__(1024) fma_stress_kernel(DevStress *st, StressParams p) {
+    __shared__ int s_k;
+    __shared__ uint64_t s_t0;
+    __shared__ int s_go[2];
+    __shared__ uint32_t s_red[32];
+    BlockCtl c;
+    if (!block_enter(st, p, c, &s_k, &s_t0)) return;
+    const uint64_t s0 = p.seed << 32;
+    float x[ILP], a[ILP], b[ILP];
+#pragma unroll
+    for (int j = 0; j < ILP; ++j) {
+        const uint64_t g = ((uint64_t)c.k * blockDim.x + threadIdx.x) * ILP + j;
+        const uint64_t u0 = ifr_splitmix64(s0, 3ull * g);
+        const uint64_t u1 = ifr_splitmix64(s0, 3ull * g + 1ull);
+        const uint64_t u2 = ifr_splitmix64(s0, 3ull * g + 2ull);
+        x[j] = (float)((int)(u0 >> 40) - (1 << 23)) * 0x1p-23f;
+        a[j] = (1.0f - 0x1p-12f) - (float)(uint32_t)(u1 >> 53) * 0x1p-23f;
+        b[j] = (float)((int)(u2 >> 40) - (1 << 23)) * 0x1p-29f;
+    }
+    uint32_t r0 = 0u;
+    int64_t round = 0;
+    for (;; ++round) {
+        if (threadIdx.x == 0) s_go[round & 1] = round_decision(st, p, round, c);
+        __syncthreads();
+        if (!s_go[round & 1]) break;
+#pragma unroll 16
+        for (int s = 0; s < kFmaSteps; ++s) {
+#pragma unroll
+            for (int j = 0; j < ILP; ++j) x[j] = __fmaf_rn(x[j], a[j], b[j]);
+        }
+        if (round == 0) {
+#pragma unroll
+            for (int j = 0; j < ILP; ++j) r0 ^= __float_as_uint(x[j]);
+        }
+    }
+    uint32_t fin = 0u;
+#pragma unroll
+    for (int j = 0; j < ILP; ++j) fin ^= __float_as_uint(x[j]);
+    uint32_t cs = ifr_block_xor(r0, s_red);
+    uint32_t cs2 = ifr_block_xor(fin, s_red);
+    if (threadIdx.x == 0) write_log(p, st, c, round, (uint64_t)round * kFmaSteps, cs, cs2);
+}
+
+// ------------------------------------------------------------------ shared memory
+// Lane l = g*WAYS + r, iteration j: bank = g + (32/WAYS)*(j % WAYS),
+// row = r + WAYS*(j / WAYS), word = 32*row + bank.  For a fixed j the WAYS lanes
+// of a group hit one bank at WAYS distinct rows (WAYS-way conflict); over the 32
+// iterations every lane visits its own 32 words once.
+template <int WAYS>
+__device__ __forceinline__ int smem_off(int j) {
+    return 32 * WAYS * (j / WAYS) + (32 / WAYS) * (j % WAYS);
+}
+
+template <int WAYS>
+__global__ void __launch_bounds__(1024) smem_stress_kernel(DevStress *st, StressParams p) {
+    extern __shared__ uint32_t s_arr[];
+    __shared__ int s_k;
+    __shared__ uint64_t s_t0;
+    __shared__ int s_go[2];
+    __shared__ uint32_t s_red[32];
+    BlockCtl c;
+    if (!block_enter(st, p, c, &s_k, &s_t0)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
+    volatile uint32_t *arr = s_arr + warp * 1024;
+    const uint64_t s0 = p.seed << 32;
+    for (int q = lane; q < 1024; q += 32)
+        arr[q] = (uint32_t)ifr_splitmix64(s0, ((uint64_t)c.k * warps + warp) * 1024ull + q);
+    __syncwarp();
+    volatile uint32_t *mine = arr + 32 * (lane % WAYS) + lane / WAYS;
+    int64_t round = 0;
+    for (;; ++round) {
+        if (threadIdx.x == 0) s_go[round & 1] = round_decision(st, p, round, c);
+        __syncthreads();
+        if (!s_go[round & 1]) break;
+#pragma unroll 1
+        for (int pass = 0; pass < kSmemPasses; ++pass) {
+#pragma unroll
+            for (int jb = 0; jb < 32; jb += 8) {
+                uint32_t v[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) v[i] = mine[smem_off<WAYS>(jb + i)];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) mine[smem_off<WAYS>(jb + i)] = v[i] * 1664525u + 1013904223u;
+            }
+        }
+    }
+    __syncwarp();
+    uint32_t acc = 0u;
+    for (int q = lane; q < 1024; q += 32) acc ^= arr[q];
+    uint32_t cs = ifr_block_xor(acc, s_red);
+    if (threadIdx.x == 0) write_log(p, st, c, round, (uint64_t)round * kSmemPasses * 32, cs, 0u);
+}
+
+// ------------------------------------------------------------------ block scheduler
+// Many short blocks of one warp.  Every block folds LCG^16(q ^ seed) into one of
+// 64 XOR slots (q = launch * blocks + blockIdx); blocks on allowed SMs that see no
+// stop request also stay resident for `sched_cycles` cycles.
+__global__ void __launch_bounds__(32) sched_stress_kernel(DevStress *st, StressParams p, int launch_idx) {
+    const uint64_t q = (uint64_t)launch_idx * (uint64_t)p.sched_blocks + blockIdx.x;
+    int work = 0;
+    if (threadIdx.x == 0) {
+        const uint64_t now = ifr_gtimer();
+        if (q == 0) {
+            atomicExch((unsigned long long *)&st->t_origin, (unsigned long long)now);
+            atomicAdd(&st->arrived, 1u);
+        }
+        uint32_t y = (uint32_t)q ^ (uint32_t)p.seed;
+#pragma unroll
+        for (int s = 0; s < kSchedLcgSteps; ++s) y = y * 1664525u + 1013904223u;
+        atomicXor(&st->sched_xor[q & 63], y);
+        uint64_t origin = *(volatile uint64_t *)&st->t_origin;
+        if (origin == 0ull) origin = now;
+        if (now > origin + p.deadline_ns) {
+            atomicCAS(&st->status, 0, IFR_ERR_TIMEOUT);
+        } else if (!ifr_ld_volatile(&st->stop) && sm_allowed(p, ifr_smid())) {
+            work = 1;
+            if ((q & 255) == 0) atomicMin((unsigned long long *)&st->t_first_start, (unsigned long long)now);
+        }
+    }
+    work = __shfl_sync(0xffffffffu, work, 0);
+    if (!work) return;
+    const long long t = clock64();
+    uint32_t it = 0;
+    while (clock64() - t < (long long)p.sched_cycles && ++it < kMaxSpin) {
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(&st->sched_cnt[q & 63], 1u);
+        if ((q & 255) == 0) atomicMax((unsigned long long *)&st->t_last_end, (unsigned long long)ifr_gtimer());
+    }
+}
+
+__global__ void wait_resident_kernel(DevStress *st, uint32_t expected, uint64_t timeout_ns, DevTiming *tm) {
+    if (threadIdx.x != 0) return;
+    const uint64_t t0 = ifr_gtimer();
+    uint32_t it = 0;
+    while (ifr_ld_volatile(&st->arrived) < expected) {
+        if (ifr_gtimer() - t0 > timeout_ns || ++it > kMaxSpin) {
+            if (tm) tm->status = IFR_ERR_NOT_RESIDENT;
+            break;
+        }
+        __nanosleep(256);
+    }
+}
+
+int kind_default_block(int kind) {
+    switch (kind) {
+        case IFR_S_SCHED: return 32;
+        case IFR_S_FMA: return 128;
+        case IFR_S_TENSOR: return 128;
+        case IFR_S_SMEM_CF:
+        case IFR_S_SMEM_32W: return 256;
+        case IFR_S_L2:
+        case IFR_S_HBM: return 512;
+        default: return 128;
+    }
+}
+
+int kind_default_bps(int kind) {
+    switch (kind) {
+        case IFR_S_FMA: return 2;
+        case IFR_S_TENSOR: return 1;
+        case IFR_S_SMEM_CF:
+        case IFR_S_SMEM_32W: return 2;
+        case IFR_S_L2:
+        case IFR_S_HBM: return 2;
+        default: return 1;
+    }
+}
+
+template <int W>
+int launch_smem(dim3 g, dim3 b, size_t sh, cudaStream_t s, DevStress *st, const StressParams &p) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(smem_stress_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024 + 1024);
+        attr = true;
+    }
+    ifr_carveout((const void *)smem_stress_kernel<W>);
+    smem_stress_kernel<W><<<g, b, sh, s>>>(st, p);
+    return IFR_OK;
+}
+
+}  // namespace
+
+int ifr_stressor_expected_arrivals(const Slot &s) {
+    return s.cfg.kind == IFR_S_SCHED ? 1 : s.grid;
+}
+
+static int validate_cfg(ifr_ctx *ctx, const ifr_stressor_cfg *c) {
+    if (!c || c->kind < 0 || c->kind >= IFR_S_COUNT) return IFR_ERR_ARG;
+    if (c->sm_count < 0 || c->sm_count > ctx->info.num_sms) return IFR_ERR_ARG;
+    if (c->blocks_per_sm < 0 || c->blocks_per_sm > IFR_MAX_BPS) return IFR_ERR_ARG;
+    if (c->block < 0 || c->block > 1024 || (c->block % 32) != 0) return IFR_ERR_ARG;
+    if (c->duty < 0.f || c->duty > 1.f) return IFR_ERR_ARG;
+    if (c->max_rounds < 0) return IFR_ERR_ARG;
+    if (c->kind == IFR_S_FMA && !(c->ilp == 0 || c->ilp == 1 || c->ilp == 2 || c->ilp == 4 || c->ilp == 8))
+        return IFR_ERR_ARG;
+    if (c->kind == IFR_S_SMEM_CF || c->kind == IFR_S_SMEM_32W) {
+        int w = c->smem_ways;
+        if (!(w == 0 || w == 1 || w == 2 || w == 4 || w == 8 || w == 16 || w == 32)) return IFR_ERR_ARG;
+        int blk = c->block ? c->block : kind_default_block(c->kind);
+        if (blk > 512) return IFR_ERR_ARG;  // 4 KiB per warp, at most 64 KiB per block
+    }
+    if (c->kind == IFR_S_L2 || c->kind == IFR_S_HBM) {
+        int blk = c->block ? c->block : kind_default_block(c->kind);
+        int64_t chunk = (int64_t)blk * 64;
+        if (!c->buf || ((uintptr_t)c->buf & 15u)) return IFR_ERR_ARG;
+        if (c->working_set_bytes < chunk || c->working_set_bytes % chunk) return IFR_ERR_ARG;
+    }
+    if (c->kind == IFR_S_TENSOR && c->block != 0 && c->block != 128) return IFR_ERR_ARG;
+    if (c->kind == IFR_S_SCHED && (c->sched_blocks < 0 || c->sched_launches < 0 || c->sched_cycles < 0))
+        return IFR_ERR_ARG;
+    if (c->mask_mode != 0) return IFR_ERR_UNSUPPORTED;
+    return IFR_OK;
+}
+
+int ifr_stressor_enqueue(ifr_ctx *ctx, const ifr_stressor_cfg *cfg, cudaStream_t stream, int slot, int record_events) {
+    int rc = validate_cfg(ctx, cfg);
+    if (rc != IFR_OK) return rc;
+    rc = ifr_slot_prepare(ctx, slot);
+    if (rc != IFR_OK) return rc;
+    Slot &s = ctx->slots[slot];
+    s.cfg = *cfg;
+    const int num_sms = ctx->info.num_sms;
+    const int kind = cfg->kind;
+    StressParams p;
+    memset(&p, 0, sizeof p);
+    p.kind = kind;
+    p.bps = cfg->blocks_per_sm ? cfg->blocks_per_sm : kind_default_bps(kind);
+    ifr_compute_mask(num_sms, cfg->sm_count, p.mask);
+    p.planned = cfg->sm_count * p.bps;
+    p.seed = cfg->seed;
+    p.max_rounds = cfg->max_rounds;
+    p.deadline_ns = cfg->deadline_ns ? cfg->deadline_ns : 2000000000ull;
+    p.duty = cfg->duty;
+    p.period_ns = cfg->period_ns > 0 ? (uint32_t)cfg->period_ns : 100000u;
+    p.ilp = cfg->ilp ? cfg->ilp : 4;
+    p.logs = s.d_logs;
+    if (s.watch) {
+        p.progress = ctx->d_progress;
+        p.hol_ns = IFR_HOL_NS;
+    }
+    const int block = cfg->block ? cfg->block : kind_default_block(kind);
+    s.block = block;
+    s.planned = p.planned;
+    s.grid = num_sms * p.bps;
+    s.launches = 1;
+    ifr_carveout((const void *)stress_reset_kernel);
+    stress_reset_kernel<<<1, 256, 0, stream>>>(s.d_state);
+    IFR_CUDA(cudaGetLastError());
+    IFR_CUDA(cudaEventRecord(s.ev_reset, stream));
+    ctx->kernel_launches += (kind == IFR_S_SCHED) ? 1 : 2;
+    if (record_events) IFR_CUDA(cudaEventRecord(s.ev_start, stream));
+    const dim3 grid(s.grid), blk(block);
+    switch (kind) {
+        case IFR_S_L2:
+        case IFR_S_HBM:
+            p.buf = (const int4 *)cfg->buf;
+            p.n_chunks = cfg->working_set_bytes / ((int64_t)block * 64);
+            ifr_carveout((const void *)stream_stress_kernel);
+            stream_stress_kernel<<<grid, blk, 0, stream>>>(s.d_state, p);
+            break;
+        case IFR_S_FMA:
+            switch (p.ilp) {
+                case 1:
+                    ifr_carveout((const void *)fma_stress_kernel<1>);
+                    fma_stress_kernel<1><<<grid, blk, 0, stream>>>(s.d_state, p);
+                    break;
+                case 2:
+                    ifr_carveout((const void *)fma_stress_kernel<2>);
+                    fma_stress_kernel<2><<<grid, blk, 0, stream>>>(s.d_state, p);
+                    break;
+                case 4:
+                    ifr_carveout((const void *)fma_stress_kernel<4>);
+                    fma_stress_kernel<4><<<grid, blk, 0, stream>>>(s.d_state, p);
+                    break;
+                default:
+                    ifr_carveout((const void *)fma_stress_kernel<8>);
+                    fma_stress_kernel<8><<<grid, blk, 0, stream>>>(s.d_state, p);
+                    break;
+            }
+            break;
+        case IFR_S_SMEM_CF:
+        case IFR_S_SMEM_32W: {
+            int w = cfg->smem_ways ? cfg->smem_ways : (kind == IFR_S_SMEM_CF ? 1 : 32);
+            p.ways = w;
+            size_t sh = (size_t)(block / 32) * 4096;
+            switch (w) {
+                case 1: launch_smem<1>(grid, blk, sh, stream, s.d_state, p); break;
+                case 2: launch_smem<2>(grid, blk, sh, stream, s.d_state, p); break;
+                case 4: launch_smem<4>(grid, blk, sh, stream, s.d_state, p); break;
+                case 8: launch_smem<8>(grid, blk, sh, stream, s.d_state, p); break;
+                case 16: launch_smem<16>(grid, blk, sh, stream, s.d_state, p); break;
+                default: launch_smem<32>(grid, blk, sh, stream, s.d_state, p); break;
+            }
+            break;
+        }
+        case IFR_S_TENSOR:
+            rc = ifr_tensor_stressor_launch(p, s.d_state, s.grid, 128, stream);
+            if (rc != IFR_OK) return rc;
+            break;
+        case IFR_S_SCHED: {
+            p.sched_blocks = cfg->sched_blocks ? cfg->sched_blocks : 100000;
+            p.sched_cycles = cfg->sched_cycles ? cfg->sched_cycles : 100;
+            s.launches = cfg->sched_launches ? cfg->sched_launches : 64;
+            s.grid = p.sched_blocks;
+            s.block = 32;
+            s.planned = p.sched_blocks;
+            ifr_carveout((const void *)sched_stress_kernel);
+            for (int l = 0; l < s.launches; ++l) sched_stress_kernel<<<p.sched_blocks, 32, 0, stream>>>(s.d_state, p, l);
+            ctx->kernel_launches += (uint64_t)s.launches;
+            break;
+        }
+        default: return IFR_ERR_ARG;
+    }
+    IFR_CUDA(cudaGetLastError());
+    if (record_events) IFR_CUDA(cudaEventRecord(s.ev_end, stream));
+    s.stream = stream;
+    s.in_use = 1;
+    s.finished = 0;
+    return IFR_OK;
+}
+
+int ifr_enqueue_wait_resident(ifr_ctx *ctx, int slot, cudaStream_t stream, DevTiming *tm, uint64_t timeout_ns) {
+    Slot &s = ctx->slots[slot];
+    // the wait must not start before the stressor's state reset (cross-stream edge)
+    IFR_CUDA(cudaStreamWaitEvent(stream, s.ev_reset, 0));
+    ifr_carveout((const void *)wait_resident_kernel);
+    wait_resident_kernel<<<1, 32, 0, stream>>>(s.d_state, (uint32_t)ifr_stressor_expected_arrivals(s), timeout_ns, tm);
+    IFR_CUDA(cudaGetLastError());
+    ctx->kernel_launches += 1;
+    return IFR_OK;
+}
+
+int ifr_enqueue_stop(ifr_ctx *ctx, int slot, cudaStream_t stream) {
+    Slot &s = ctx->slots[slot];
+    IFR_CUDA(cudaMemcpyAsync(&s.d_state->stop, ctx->h_one, sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
+    return IFR_OK;
+}
+
+int ifr_stressor_collect(ifr_ctx *ctx, int slot) {
+    Slot &s = ctx->slots[slot];
+    DevStress h;
+    IFR_CUDA(cudaMemcpy(&h, s.d_state, sizeof h, cudaMemcpyDeviceToHost));
+    ifr_stressor_result &r = s.result;
+    memset(&r, 0, sizeof r);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, s.ev_start, s.ev_end) != cudaSuccess) {
+        ms = 0.f;
+        cudaGetLastError();
+    }
+    r.elapsed_ms = ms;
+    r.status = h.status;
+    r.planned_active = s.planned;
+    if (s.cfg.kind == IFR_S_SCHED) {
+        uint32_t x = 0u;
+        uint64_t cnt = 0;
+        for (int i = 0; i < 64; ++i) {
+            x ^= h.sched_xor[i];
+            cnt += h.sched_cnt[i];
+        }
+        r.checksum = x;
+        r.work = cnt;
+        r.rounds = cnt;
+        r.blocks_launched = s.grid * s.launches;
+        r.blocks_active = cnt > 0x7fffffffull ? 0x7fffffff : (int32_t)cnt;
+        r.sms_used = 0;
+        if (cnt > 0) {
+            r.t_start_ns = r.t_start_last_ns = h.t_first_start;
+            r.t_end_ns = r.t_end_first_ns = h.t_last_end;
+        }
+        s.h_nlogs = 0;
+        s.finished = 1;
+        return IFR_OK;
+    }
+    int n = (int)(h.active < (uint32_t)s.planned ? h.active : (uint32_t)s.planned);
+    if (n > s.log_cap) n = s.log_cap;
+    if (n > 0) IFR_CUDA(cudaMemcpy(s.h_logs, s.d_logs, sizeof(ifr_block_log) * (size_t)n, cudaMemcpyDeviceToHost));
+    s.h_nlogs = n;
+    r.blocks_launched = s.grid;
+    r.blocks_active = n;
+    uint32_t used[IFR_MAX_SMS / 32] = {0};
+    if (n > 0) {
+        r.t_start_ns = ~0ull;
+        r.t_end_first_ns = ~0ull;
+    }
+    for (int i = 0; i < n; ++i) {
+        const ifr_block_log &L = s.h_logs[i];
+        r.checksum ^= L.checksum;
+        r.rounds += L.rounds;
+        r.work += L.work;
+        if (L.t_start_ns < r.t_start_ns) r.t_start_ns = L.t_start_ns;
+        if (L.t_start_ns > r.t_start_last_ns) r.t_start_last_ns = L.t_start_ns;
+        if (L.t_end_ns < r.t_end_first_ns) r.t_end_first_ns = L.t_end_ns;
+        if (L.t_end_ns > r.t_end_ns) r.t_end_ns = L.t_end_ns;
+        if (L.smid < IFR_MAX_SMS) used[L.smid >> 5] |= 1u << (L.smid & 31);
+        if (L.status != 0 && r.status == 0) r.status = L.status;
+    }
+    for (int i = 0; i < IFR_MAX_SMS / 32; ++i) r.sms_used += __builtin_popcount(used[i]);
+    s.finished = 1;
+    return IFR_OK;
+}
+
+// ------------------------------------------------------------------ public API
+extern "C" int ifr_stressor_launch(ifr_ctx *ctx, const ifr_stressor_cfg *cfg, void *stream, int *handle_out) {
+    if (!ctx || !cfg || !handle_out) return IFR_ERR_ARG;
+    int slot = ifr_slot_alloc(ctx);
+    if (slot < 0) return slot;
+    ctx->slots[slot].watch = 0;
+    int rc = ifr_stressor_enqueue(ctx, cfg, stream ? (cudaStream_t)stream : ctx->s_stress, slot);
+    if (rc != IFR_OK) return rc;
+    *handle_out = slot;
+    return IFR_OK;
+}
+
+static bool valid_handle(ifr_ctx *ctx, int h) { return ctx && h >= 0 && h < IFR_SLOTS && ctx->slots[h].in_use; }
+
+extern "C" int ifr_stressor_stop(ifr_ctx *ctx, int handle, void *stream) {
+    if (!valid_handle(ctx, handle)) return IFR_ERR_ARG;
+    return ifr_enqueue_stop(ctx, handle, stream ? (cudaStream_t)stream : ctx->s_ctrl);
+}
+
+extern "C" int ifr_stressor_wait(ifr_ctx *ctx, int handle, int timeout_ms, ifr_stressor_result *out) {
+    if (!valid_handle(ctx, handle)) return IFR_ERR_ARG;
+    Slot &s = ctx->slots[handle];
+    if (!s.finished) {
+        const int limit = timeout_ms > 0 ? timeout_ms : 10000;
+        cudaEvent_t ev = s.ev_end;
+        int waited_us = 0;
+        cudaError_t q;
+        while ((q = cudaEventQuery(ev)) == cudaErrorNotReady) {
+            if (waited_us >= limit * 1000) {
+                ifr_enqueue_stop(ctx, handle, ctx->s_ctrl);
+                cudaEventSynchronize(ev);  // the kernels' own deadlines bound this wait
+                int rc = ifr_stressor_collect(ctx, handle);
+                if (out) *out = s.result;
+                return rc != IFR_OK ? rc : IFR_ERR_TIMEOUT;
+            }
+            struct timespec ts = {0, 50000};
+            nanosleep(&ts, nullptr);
+            waited_us += 50;
+        }
+        if (q != cudaSuccess) return ifr_cuda_fail(q, "cudaEventQuery(stressor end)", __FILE__, __LINE__);
+        int rc = ifr_stressor_collect(ctx, handle);
+        if (rc != IFR_OK) return rc;
+    }
+    if (out) *out = s.result;
+    return IFR_OK;
+}
+
+extern "C" int ifr_stressor_block_logs(ifr_ctx *ctx, int handle, ifr_block_log *out, int cap, int *n_out) {
+    if (!valid_handle(ctx, handle) || !n_out || (cap > 0 && !out)) return IFR_ERR_ARG;
+    Slot &s = ctx->slots[handle];
+    if (!s.finished) return IFR_ERR_ARG;
+    *n_out = s.h_nlogs;
+    if (cap < s.h_nlogs) return IFR_ERR_CAPACITY;
+    memcpy(out, s.h_logs, sizeof(ifr_block_log) * (size_t)s.h_nlogs);
+    return IFR_OK;
+}
+
+extern "C" int ifr_stressor_release(ifr_ctx *ctx, int handle) {
+    if (!valid_handle(ctx, handle)) return IFR_ERR_ARG;
+    Slot &s = ctx->slots[handle];
+    if (!s.finished) {
+        ifr_stressor_result r;
+        int rc = ifr_stressor_wait(ctx, handle, 0, &r);
+        if (rc != IFR_OK && rc != IFR_ERR_TIMEOUT) return rc;
+    }
+    s.in_use = 0;
+    return IFR_OK;
+}

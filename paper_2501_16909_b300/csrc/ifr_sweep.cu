@@ -1,0 +1,286 @@
+// Colocation sweep (Sec. 4.1): a stressor holding a constant interference level on
+// one stream, victims on another, slowdown against isolated runs.
+//
+// Plain mode, per colocated cell:
+//   stressor stream:  reset state -> stressor kernels
+//   victim stream:    reset timing -> bounded residency wait -> K victim launches
+//                     -> stop flag (copy-engine write, so it needs no SM slot)
+// Batched mode, per (stressor, level): the same sequence with all victims
+// back to back under one stressor run, captured once into a CUDA graph and
+// replayed for every repeat; per-victim timings land in separate slots.
+#include <math.h>
+#include <string.h>
+#include <time.h>
+
+#include <vector>
+
+#include "ifr_internal.cuh"
+
+namespace {
+
+constexpr uint64_t kResidencyTimeoutNs = 200000000ull;  // 200 ms
+
+int wait_event_bounded(cudaEvent_t ev, int timeout_ms) {
+    int waited_us = 0;
+    cudaError_t q;
+    while ((q = cudaEventQuery(ev)) == cudaErrorNotReady) {
+        if (waited_us >= timeout_ms * 1000) return IFR_ERR_TIMEOUT;
+        struct timespec ts = {0, 20000};
+        nanosleep(&ts, nullptr);
+        waited_us += 20;
+    }
+    if (q != cudaSuccess) return ifr_cuda_fail(q, "cudaEventQuery", __FILE__, __LINE__);
+    return IFR_OK;
+}
+
+void fill_validity(ifr_cell_result &c) {
+    const ifr_timing &t = c.timing;
+    const ifr_stressor_result &s = c.stress;
+    int ok = t.status == IFR_OK && t.t_end_ns > t.t_start_ns;
+    if (ok && c.stressor >= 0) {
+        ok = s.status == IFR_OK;
+        if (ok && c.level > 0)
+            ok = s.blocks_active > 0 && s.t_start_last_ns <= t.t_start_ns && s.t_end_first_ns >= t.t_end_ns;
+    }
+    c.valid = ok;
+    c.status = ok ? IFR_OK : (t.status != IFR_OK ? t.status : (s.status != IFR_OK ? s.status : IFR_ERR_INVALID_CELL));
+}
+
+ifr_stressor_cfg level_cfg(const ifr_sweep_plan *p, int r, int l) {
+    ifr_stressor_cfg c = p->levels[(size_t)r * p->n_levels + (l > 0 ? l - 1 : 0)];
+    if (l == 0) c.sm_count = 0;  // level 0: the harness runs, nothing interferes
+    return c;
+}
+
+int measure_solo_plain(ifr_ctx *ctx, const ifr_victim_cfg *v, ifr_timing *out) {
+    DevTiming *tm = ctx->d_timing;
+    cudaStream_t sv = ctx->s_victim;
+    int rc = ifr_timing_reset(tm, 1, sv, nullptr);
+    if (rc) return rc;
+    ctx->kernel_launches += 1;
+    IFR_CUDA(cudaEventRecord(ctx->ev_a, sv));
+    rc = ifr_victim_enqueue(ctx, v, sv, tm);
+    if (rc) return rc;
+    IFR_CUDA(cudaEventRecord(ctx->ev_b, sv));
+    rc = wait_event_bounded(ctx->ev_b, 60000);
+    if (rc) return rc;
+    DevTiming h;
+    IFR_CUDA(cudaMemcpy(&h, tm, sizeof h, cudaMemcpyDeviceToHost));
+    ifr_timing_to_host(h, v->repeats > 0 ? v->repeats : 1, out);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev_a, ctx->ev_b);
+    out->event_ms = ms;
+    return IFR_OK;
+}
+
+int measure_cell_plain(ifr_ctx *ctx, const ifr_victim_cfg *v, const ifr_stressor_cfg *scfg, ifr_cell_result *cell) {
+    int slot = ifr_slot_alloc(ctx);
+    if (slot < 0) return slot;
+    cudaStream_t ss = ctx->s_stress, sv = ctx->s_victim;
+    DevTiming *tm = ctx->d_timing;
+    ctx->slots[slot].watch = 1;
+    int rc = ifr_stressor_enqueue(ctx, scfg, ss, slot);
+    if (rc) return rc;
+    rc = ifr_timing_reset(tm, 1, sv, ctx->d_progress);
+    ctx->kernel_launches += 1;
+    if (!rc) rc = ifr_enqueue_wait_resident(ctx, slot, sv, tm, kResidencyTimeoutNs);
+    if (!rc) {
+        cudaEventRecord(ctx->ev_a, sv);
+        rc = ifr_victim_enqueue(ctx, v, sv, tm);
+        cudaEventRecord(ctx->ev_b, sv);
+    }
+    int rc_stop = ifr_enqueue_stop(ctx, slot, sv);
+    if (!rc) rc = rc_stop;
+    int rc_w = wait_event_bounded(ctx->ev_b, 60000);
+    ifr_stressor_result sres;
+    int rc_s = ifr_stressor_wait(ctx, slot, 60000, &sres);
+    ctx->slots[slot].in_use = 0;
+    if (rc) return rc;
+    if (rc_w) return rc_w;
+    DevTiming h;
+    IFR_CUDA(cudaMemcpy(&h, tm, sizeof h, cudaMemcpyDeviceToHost));
+    ifr_timing_to_host(h, v->repeats > 0 ? v->repeats : 1, &cell->timing);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev_a, ctx->ev_b);
+    cell->timing.event_ms = ms;
+    cell->stress = sres;
+    if (rc_s == IFR_ERR_TIMEOUT && cell->stress.status == IFR_OK) cell->stress.status = IFR_ERR_TIMEOUT;
+    else if (rc_s) return rc_s;
+    return IFR_OK;
+}
+
+// Capture one graph: optional stressor + all victims back to back.
+int capture_batch(ifr_ctx *ctx, const ifr_sweep_plan *p, const ifr_stressor_cfg *scfg, int slot,
+                  cudaGraphExec_t *exec, uint64_t *kernels) {
+    const uint64_t before = ctx->kernel_launches;
+    cudaStream_t sv = ctx->s_victim, ss = ctx->s_stress;
+    cudaGraph_t g = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    IFR_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    IFR_CUDA(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+    int rc = IFR_OK;
+    IFR_CUDA(cudaStreamBeginCapture(sv, cudaStreamCaptureModeRelaxed));
+    rc = ifr_timing_reset(ctx->d_timing, p->n_victims, sv, scfg ? ctx->d_progress : nullptr);
+    ctx->kernel_launches += 1;
+    if (!rc && scfg) {
+        cudaEventRecord(fork, sv);
+        cudaStreamWaitEvent(ss, fork, 0);
+        rc = ifr_stressor_enqueue(ctx, scfg, ss, slot, 0);
+        if (!rc) rc = ifr_enqueue_wait_resident(ctx, slot, sv, ctx->d_timing, kResidencyTimeoutNs);
+    }
+    for (int v = 0; !rc && v < p->n_victims; ++v) rc = ifr_victim_enqueue(ctx, &p->victims[v], sv, ctx->d_timing + v);
+    if (!rc && scfg) {
+        rc = ifr_enqueue_stop(ctx, slot, sv);
+        cudaEventRecord(join, ss);
+        cudaStreamWaitEvent(sv, join, 0);
+    }
+    cudaError_t e = cudaStreamEndCapture(sv, &g);
+    if (!rc && e != cudaSuccess) rc = ifr_cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+    if (!rc) {
+        e = cudaGraphInstantiate(exec, g, 0);
+        if (e != cudaSuccess) rc = ifr_cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaEventDestroy(fork);
+    cudaEventDestroy(join);
+    *kernels = ctx->kernel_launches - before;
+    ctx->kernel_launches = before;  // counted again at every replay
+    return rc;
+}
+
+}  // namespace
+
+extern "C" int ifr_sweep(ifr_ctx *ctx, const ifr_sweep_plan *p, ifr_cell_result *cells, size_t cap, size_t *n_out) {
+    if (!ctx || !p || !n_out || p->n_victims <= 0 || !p->victims || p->n_stressors < 0 ||
+        p->n_stressors > IFR_MAX_STRESSORS || p->n_levels < 0 || p->n_levels > IFR_MAX_LEVELS || p->repeats <= 0)
+        return IFR_ERR_ARG;
+    if (p->n_stressors > 0 && (p->n_levels <= 0 || !p->levels)) return IFR_ERR_ARG;
+    *n_out = 0;
+    for (int v = 0; v < p->n_victims; ++v) {
+        int rc = ifr_victim_validate(ctx, &p->victims[v]);
+        if (rc) return rc;
+    }
+    const size_t need = (size_t)p->repeats * p->n_victims * (1 + (size_t)p->n_stressors * (p->n_levels + 1));
+    if (!cells || cap < need) return IFR_ERR_CAPACITY;
+    int rc = ifr_ensure_timing(ctx, p->n_victims);
+    if (rc) return rc;
+    IFR_CUDA(cudaDeviceSynchronize());
+    size_t n = 0;
+    if (!p->batched) {
+        for (int rep = 0; rep < p->repeats; ++rep) {
+            for (int v = 0; v < p->n_victims; ++v) {
+                ifr_cell_result &c = cells[n++];
+                memset(&c, 0, sizeof c);
+                c.victim = v;
+                c.stressor = -1;
+                c.repeat = rep;
+                rc = measure_solo_plain(ctx, &p->victims[v], &c.timing);
+                if (rc) return rc;
+                fill_validity(c);
+            }
+            for (int r = 0; r < p->n_stressors; ++r)
+                for (int l = 0; l <= p->n_levels; ++l) {
+                    ifr_stressor_cfg sc = level_cfg(p, r, l);
+                    for (int v = 0; v < p->n_victims; ++v) {
+                        ifr_cell_result &c = cells[n++];
+                        memset(&c, 0, sizeof c);
+                        c.victim = v;
+                        c.stressor = r;
+                        c.level = l;
+                        c.repeat = rep;
+                        rc = measure_cell_plain(ctx, &p->victims[v], &sc, &c);
+                        if (rc) return rc;
+                        fill_validity(c);
+                    }
+                }
+        }
+        *n_out = n;
+        return IFR_OK;
+    }
+    // batched: one graph per (stressor, level) plus one for the solo runs
+    const int n_graphs = 1 + p->n_stressors * (p->n_levels + 1);
+    std::vector<cudaGraphExec_t> execs((size_t)n_graphs, nullptr);
+    int slot = ifr_slot_alloc(ctx);
+    if (slot < 0) return slot;
+    rc = ifr_slot_prepare(ctx, slot);
+    if (rc) return rc;
+    ctx->slots[slot].watch = 1;
+    std::vector<ifr_stressor_cfg> cfgs((size_t)n_graphs);
+    struct Shape {
+        int grid, block, planned, launches;
+    };
+    std::vector<Shape> shapes((size_t)n_graphs);
+    std::vector<uint64_t> nodes((size_t)n_graphs, 0);
+    for (int gi = 0; gi < n_graphs && !rc; ++gi) {
+        if (gi == 0) {
+            rc = capture_batch(ctx, p, nullptr, slot, &execs[0], &nodes[0]);
+        } else {
+            const int r = (gi - 1) / (p->n_levels + 1), l = (gi - 1) % (p->n_levels + 1);
+            cfgs[gi] = level_cfg(p, r, l);
+            rc = capture_batch(ctx, p, &cfgs[gi], slot, &execs[gi], &nodes[gi]);
+            const Slot &s = ctx->slots[slot];
+            shapes[gi] = Shape{s.grid, s.block, s.planned, s.launches};
+        }
+    }
+    ctx->slots[slot].in_use = 1;
+    std::vector<DevTiming> ht((size_t)p->n_victims);
+    for (int rep = 0; rep < p->repeats && !rc; ++rep) {
+        for (int gi = 0; gi < n_graphs && !rc; ++gi) {
+            Slot &s = ctx->slots[slot];
+            if (gi > 0) {
+                s.cfg = cfgs[gi];
+                s.grid = shapes[gi].grid;
+                s.block = shapes[gi].block;
+                s.planned = shapes[gi].planned;
+                s.launches = shapes[gi].launches;
+                s.in_use = 1;
+                s.finished = 0;
+            }
+            cudaError_t e = cudaGraphLaunch(execs[gi], ctx->s_victim);
+            ctx->kernel_launches += nodes[gi];
+            if (e != cudaSuccess) {
+                rc = ifr_cuda_fail(e, "cudaGraphLaunch", __FILE__, __LINE__);
+                break;
+            }
+            IFR_CUDA(cudaEventRecord(ctx->ev_b, ctx->s_victim));
+            rc = wait_event_bounded(ctx->ev_b, 120000);
+            if (rc) break;
+            e = cudaMemcpy(ht.data(), ctx->d_timing, sizeof(DevTiming) * (size_t)p->n_victims, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) {
+                rc = ifr_cuda_fail(e, "cudaMemcpy timings", __FILE__, __LINE__);
+                break;
+            }
+            ifr_stressor_result sres;
+            memset(&sres, 0, sizeof sres);
+            if (gi > 0) {
+                rc = ifr_stressor_collect(ctx, slot);
+                if (rc) break;
+                sres = s.result;
+                sres.elapsed_ms = 0.0;  // events are not recorded inside graphs
+            }
+            const int r = gi == 0 ? -1 : (gi - 1) / (p->n_levels + 1);
+            const int l = gi == 0 ? 0 : (gi - 1) % (p->n_levels + 1);
+            for (int v = 0; v < p->n_victims; ++v) {
+                ifr_cell_result &c = cells[n++];
+                memset(&c, 0, sizeof c);
+                c.victim = v;
+                c.stressor = r;
+                c.level = l;
+                c.repeat = rep;
+                ifr_timing_to_host(ht[v], p->victims[v].repeats > 0 ? p->victims[v].repeats : 1, &c.timing);
+                c.timing.event_ms = 0.0;
+                if (gi > 0) {
+                    c.stress = sres;
+                    // the residency wait stamps its status into victim 0's slot only
+                    if (v > 0 && ht[0].status != IFR_OK) c.timing.status = ht[0].status;
+                }
+                fill_validity(c);
+            }
+        }
+    }
+    ctx->slots[slot].in_use = 0;
+    for (auto &e : execs)
+        if (e) cudaGraphExecDestroy(e);
+    *n_out = n;
+    return rc;
+}

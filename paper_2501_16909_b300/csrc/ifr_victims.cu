@@ -1,0 +1,491 @@
+// Victim kernels: the workloads whose slowdown the method measures (Sec. 4).
+// Every block stamps %globaltimer at entry (atomicMin) and exit (atomicMax) into
+// the measurement's DevTiming, plus its %smid bit, so a measurement spans
+// [first block entry, last block exit] over K back-to-back launches.
+#include <cuda_bf16.h>
+#include <string.h>
+
+#include "ifr_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ void v_enter(DevTiming *tm) {
+    if (threadIdx.x == 0) {
+        const unsigned long long t = ifr_gtimer();
+        atomicMin((unsigned long long *)&tm->t_min, t);
+        if (tm->progress) atomicMax((unsigned long long *)tm->progress, t);
+    }
+}
+__device__ __forceinline__ void v_exit(DevTiming *tm) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long t = ifr_gtimer();
+        atomicMax((unsigned long long *)&tm->t_max, t);
+        if (tm->progress) atomicMax((unsigned long long *)tm->progress, t);
+        atomicAdd(&tm->blocks, 1u);
+        const uint32_t s = ifr_smid();
+        if (s < IFR_MAX_SMS) atomicOr(&tm->sm_bits[s >> 5], 1u << (s & 31));
+    }
+}
+
+__global__ void timing_reset_kernel(DevTiming *tm, int n, uint64_t *progress) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        tm[i].progress = progress;
+        tm[i].t_min = ~0ull;
+        tm[i].t_max = 0ull;
+        tm[i].blocks = 0u;
+        tm[i].status = 0;
+        for (int j = 0; j < IFR_MAX_SMS / 32; ++j) tm[i].sm_bits[j] = 0u;
+    }
+}
+
+__device__ __forceinline__ float4 ld_f4_stream(const float4 *p) {
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
+}
+__device__ __forceinline__ void st_f4_stream(float4 *p, float4 v) {
+    asm volatile("st.global.cs.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
+// ------------------------------------------------------------------ triad
+// a[i] = b[i] + s * c[i] (STREAM triad).  Grid-stride over float4 with 4
+// independent float4 per thread per step; scalar tail.
+__global__ void __launch_bounds__(256) triad_kernel(float *__restrict__ a, const float *__restrict__ b,
+                                                    const float *__restrict__ c, float s, int64_t n,
+                                                    DevTiming *tm) {
+    v_enter(tm);
+    const int64_t n4 = n >> 2;
+    const float4 *b4 = (const float4 *)b;
+    const float4 *c4 = (const float4 *)c;
+    float4 *a4 = (float4 *)a;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n4; i += 4 * stride) {
+        float4 bv[4], cv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            bv[u] = ld_f4_stream(b4 + i + u * stride);
+            cv[u] = ld_f4_stream(c4 + i + u * stride);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            float4 r;
+            r.x = bv[u].x + s * cv[u].x;
+            r.y = bv[u].y + s * cv[u].y;
+            r.z = bv[u].z + s * cv[u].z;
+            r.w = bv[u].w + s * cv[u].w;
+            st_f4_stream(a4 + i + u * stride, r);
+        }
+    }
+    for (; i < n4; i += stride) {
+        float4 bv = ld_f4_stream(b4 + i), cv = ld_f4_stream(c4 + i), r;
+        r.x = bv.x + s * cv.x;
+        r.y = bv.y + s * cv.y;
+        r.z = bv.z + s * cv.z;
+        r.w = bv.w + s * cv.w;
+        st_f4_stream(a4 + i, r);
+    }
+    const int64_t t = (n4 << 2) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) a[t] = b[t] + s * c[t];
+    v_exit(tm);
+}
+
+// ------------------------------------------------------------------ row kernels
+// Block-wide sum; every thread gets the result.
+template <int NT>
+__device__ __forceinline__ float block_sum(float v, float *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    float r = lane < NT / 32 ? red[lane] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    return r;
+}
+template <int NT>
+__device__ __forceinline__ float block_max(float v, float *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    float r = lane < NT / 32 ? red[lane] : -INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+    return r;
+}
+
+// LayerNorm, no affine, biased variance, two passes over the register-held row.
+// NT threads, VPT float4 per thread: cols <= NT*VPT*4, cols % 4 == 0.
+template <int NT, int VPT>
+__global__ void __launch_bounds__(NT) layernorm_kernel(const float *__restrict__ x, float *__restrict__ y,
+                                                       int64_t rows, int cols, float eps, DevTiming *tm) {
+    __shared__ float red[32];
+    v_enter(tm);
+    const int c4 = cols >> 2;
+    const float inv_n = 1.0f / (float)cols;
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+        const float4 *xr = (const float4 *)(x + r * cols);
+        float4 v[VPT];
+        float s = 0.f;
+#pragma unroll
+        for (int u = 0; u < VPT; ++u) {
+            const int j = threadIdx.x + u * NT;
+            v[u] = j < c4 ? ld_f4_stream(xr + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+            s += (v[u].x + v[u].y) + (v[u].z + v[u].w);
+        }
+        const float mean = block_sum<NT>(s, red) * inv_n;
+        float q = 0.f;
+#pragma unroll
+        for (int u = 0; u < VPT; ++u) {
+            const int j = threadIdx.x + u * NT;
+            if (j < c4) {
+                const float a = v[u].x - mean, b = v[u].y - mean, c = v[u].z - mean, d = v[u].w - mean;
+                q += (a * a + b * b) + (c * c + d * d);
+            }
+        }
+        const float var = block_sum<NT>(q, red) * inv_n;
+        const float inv = 1.0f / sqrtf(var + eps);
+        float4 *yr = (float4 *)(y + r * cols);
+#pragma unroll
+        for (int u = 0; u < VPT; ++u) {
+            const int j = threadIdx.x + u * NT;
+            if (j < c4) {
+                float4 o;
+                o.x = (v[u].x - mean) * inv;
+                o.y = (v[u].y - mean) * inv;
+                o.z = (v[u].z - mean) * inv;
+                o.w = (v[u].w - mean) * inv;
+                st_f4_stream(yr + j, o);
+            }
+        }
+    }
+    v_exit(tm);
+}
+
+// Row softmax: max, sum of exp(x - max), divide.  Same layout as layernorm.
+template <int NT, int VPT>
+__global__ void __launch_bounds__(NT) softmax_kernel(const float *__restrict__ x, float *__restrict__ y,
+                                                     int64_t rows, int cols, DevTiming *tm) {
+    __shared__ float red[32];
+    v_enter(tm);
+    const int c4 = cols >> 2;
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+        const float4 *xr = (const float4 *)(x + r * cols);
+        float4 v[VPT];
+        float m = -INFINITY;
+#pragma unroll
+        for (int u = 0; u < VPT; ++u) {
+            const int j = threadIdx.x + u * NT;
+            if (j < c4) {
+                v[u] = ld_f4_stream(xr + j);
+                m = fmaxf(m, fmaxf(fmaxf(v[u].x, v[u].y), fmaxf(v[u].z, v[u].w)));
+            }
+        }
+        const float mx = block_max<NT>(m, red);
+        float s = 0.f;
+#pragma unroll
+        for (int u = 0; u < VPT; ++u) {
+            const int j = threadIdx.x + u * NT;
+            if (j < c4) {
+                v[u].x = expf(v[u].x - mx);
+                v[u].y = expf(v[u].y - mx);
+                v[u].z = expf(v[u].z - mx);
+                v[u].w = expf(v[u].w - mx);
+                s += (v[u].x + v[u].y) + (v[u].z + v[u].w);
+            }
+        }
+        const float inv = 1.0f / block_sum<NT>(s, red);
+        float4 *yr = (float4 *)(y + r * cols);
+#pragma unroll
+        for (int u = 0; u < VPT; ++u) {
+            const int j = threadIdx.x + u * NT;
+            if (j < c4) {
+                float4 o;
+                o.x = v[u].x * inv;
+                o.y = v[u].y * inv;
+                o.z = v[u].z * inv;
+                o.w = v[u].w * inv;
+                st_f4_stream(yr + j, o);
+            }
+        }
+    }
+    v_exit(tm);
+}
+
+// ------------------------------------------------------------------ GEMV
+// y[r] = sum_c A[r][c] x[c], bf16 inputs, fp32 accumulate.  One warp per row,
+// 16-byte loads (8 bf16), x staged in shared memory; cols % 8 == 0.
+__global__ void __launch_bounds__(256) gemv_kernel(const __nv_bfloat16 *__restrict__ A,
+                                                  const __nv_bfloat16 *__restrict__ x, float *__restrict__ y,
+                                                  int64_t rows, int cols, DevTiming *tm) {
+    extern __shared__ uint4 xs[];
+    v_enter(tm);
+    const int c8 = cols >> 3;
+    for (int i = threadIdx.x; i < c8; i += blockDim.x) xs[i] = ((const uint4 *)x)[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    for (int64_t r = (int64_t)blockIdx.x * wpb + warp; r < rows; r += (int64_t)gridDim.x * wpb) {
+        const uint4 *ar = (const uint4 *)(A + r * cols);
+        float acc = 0.f;
+        int j = lane;
+        for (; j + 96 < c8; j += 128) {
+            uint4 av[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                int4 t;
+                asm volatile("ld.global.nc.L1::no_allocate.v4.s32 {%0,%1,%2,%3}, [%4];"
+                             : "=r"(t.x), "=r"(t.y), "=r"(t.z), "=r"(t.w)
+                             : "l"(ar + j + 32 * u));
+                av[u] = make_uint4((uint32_t)t.x, (uint32_t)t.y, (uint32_t)t.z, (uint32_t)t.w);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint4 xv = xs[j + 32 * u];
+                const __nv_bfloat162 *a2 = (const __nv_bfloat162 *)&av[u];
+                const __nv_bfloat162 *x2 = (const __nv_bfloat162 *)&xv;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float2 af = __bfloat1622float2(a2[e]);
+                    const float2 xf = __bfloat1622float2(x2[e]);
+                    acc = fmaf(af.x, xf.x, acc);
+                    acc = fmaf(af.y, xf.y, acc);
+                }
+            }
+        }
+        for (; j < c8; j += 32) {
+            const uint4 av = ar[j];
+            const uint4 xv = xs[j];
+            const __nv_bfloat162 *a2 = (const __nv_bfloat162 *)&av;
+            const __nv_bfloat162 *x2 = (const __nv_bfloat162 *)&xv;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float2 af = __bfloat1622float2(a2[e]);
+                const float2 xf = __bfloat1622float2(x2[e]);
+                acc = fmaf(af.x, xf.x, acc);
+                acc = fmaf(af.y, xf.y, acc);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) y[r] = acc;
+    }
+    v_exit(tm);
+}
+
+// ------------------------------------------------------------------ histogram
+// 256 bins of key & 255; one privatised shared-memory histogram per warp,
+// merged into the block's and then atomically into the global bins (which the
+// launch sequence zeroes first).
+__global__ void __launch_bounds__(256) hist_kernel(const int32_t *__restrict__ keys, int64_t n,
+                                                   uint32_t *__restrict__ bins, DevTiming *tm) {
+    __shared__ uint32_t h[8][256];
+    v_enter(tm);
+    const int warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) (&h[0][0])[i] = 0u;
+    __syncthreads();
+    uint32_t *hw = h[warp & 7];
+    const int64_t n4 = n >> 2;
+    const int4 *k4 = (const int4 *)keys;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n4; i += 4 * stride) {
+        int4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            asm volatile("ld.global.nc.L1::no_allocate.v4.s32 {%0,%1,%2,%3}, [%4];"
+                         : "=r"(v[u].x), "=r"(v[u].y), "=r"(v[u].z), "=r"(v[u].w)
+                         : "l"(k4 + i + u * stride));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            atomicAdd(&hw[v[u].x & 255], 1u);
+            atomicAdd(&hw[v[u].y & 255], 1u);
+            atomicAdd(&hw[v[u].z & 255], 1u);
+            atomicAdd(&hw[v[u].w & 255], 1u);
+        }
+    }
+    for (; i < n4; i += stride) {
+        const int4 v = k4[i];
+        atomicAdd(&hw[v.x & 255], 1u);
+        atomicAdd(&hw[v.y & 255], 1u);
+        atomicAdd(&hw[v.z & 255], 1u);
+        atomicAdd(&hw[v.w & 255], 1u);
+    }
+    const int64_t t = (n4 << 2) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) atomicAdd(&hw[keys[t] & 255], 1u);
+    __syncthreads();
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) {
+        uint32_t s = 0u;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) s += h[w][b];
+        if (s) atomicAdd(&bins[b], s);
+    }
+    v_exit(tm);
+}
+
+inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+template <int NT, int VPT>
+void launch_ln(int grid, cudaStream_t st, const ifr_victim_cfg *c, DevTiming *tm) {
+    ifr_carveout((const void *)layernorm_kernel<NT, VPT>);
+    layernorm_kernel<NT, VPT><<<grid, NT, 0, st>>>((const float *)c->in0, (float *)c->out, c->m, (int)c->n,
+                                                   c->eps > 0.f ? c->eps : 1e-5f, tm);
+}
+template <int NT, int VPT>
+void launch_sm(int grid, cudaStream_t st, const ifr_victim_cfg *c, DevTiming *tm) {
+    ifr_carveout((const void *)softmax_kernel<NT, VPT>);
+    softmax_kernel<NT, VPT><<<grid, NT, 0, st>>>((const float *)c->in0, (float *)c->out, c->m, (int)c->n, tm);
+}
+
+}  // namespace
+
+int ifr_timing_reset(DevTiming *tm, int n, cudaStream_t stream, uint64_t *progress) {
+    ifr_carveout((const void *)timing_reset_kernel);
+    timing_reset_kernel<<<(n + 127) / 128, 128, 0, stream>>>(tm, n, progress);
+    IFR_CUDA(cudaGetLastError());
+    return IFR_OK;
+}
+
+void ifr_timing_to_host(const DevTiming &d, int repeats, ifr_timing *out) {
+    memset(out, 0, sizeof *out);
+    out->t_start_ns = d.t_min == ~0ull ? 0ull : d.t_min;
+    out->t_end_ns = d.t_max;
+    out->status = d.status;
+    out->blocks = (int32_t)d.blocks;
+    out->repeats = repeats;
+    int n = 0;
+    for (int i = 0; i < IFR_MAX_SMS / 32; ++i) n += __builtin_popcount(d.sm_bits[i]);
+    out->sms_touched = n;
+}
+
+int ifr_victim_validate(ifr_ctx *ctx, const ifr_victim_cfg *c) {
+    if (!c || c->kind < 0 || c->kind >= IFR_V_COUNT || c->repeats < 0 || c->grid < 0 || c->block < 0) return IFR_ERR_ARG;
+    if (!c->in0 || !c->out) return IFR_ERR_ARG;
+    switch (c->kind) {
+        case IFR_V_TRIAD:
+            if (!c->in1 || c->n <= 0 || !aligned16(c->in0) || !aligned16(c->in1) || !aligned16(c->out)) return IFR_ERR_ARG;
+            return IFR_OK;
+        case IFR_V_LAYERNORM:
+        case IFR_V_SOFTMAX:
+            if (c->m <= 0 || c->n <= 0 || c->n % 4 || c->n > 32768) return IFR_ERR_ARG;
+            if (!aligned16(c->in0) || !aligned16(c->out)) return IFR_ERR_ARG;
+            return IFR_OK;
+        case IFR_V_GEMV:
+            if (!c->in1 || c->m <= 0 || c->k <= 0 || c->k % 8 || c->k > 24576) return IFR_ERR_ARG;
+            if (!aligned16(c->in0) || !aligned16(c->in1)) return IFR_ERR_ARG;
+            return IFR_OK;
+        case IFR_V_HIST:
+            if (c->n <= 0 || !aligned16(c->in0)) return IFR_ERR_ARG;
+            return IFR_OK;
+        case IFR_V_GEMM:
+            if (!c->in1 || c->m <= 0 || c->n <= 0 || c->k <= 0) return IFR_ERR_ARG;
+            if (c->m % 128 || c->n % 128 || c->k % 64) return IFR_ERR_ARG;
+            if (!aligned16(c->in0) || !aligned16(c->in1) || !aligned16(c->out)) return IFR_ERR_ARG;
+            return IFR_OK;
+        default: return IFR_ERR_ARG;
+    }
+    (void)ctx;
+}
+
+// Enqueue K launches of a victim on `stream`, all stamping into *tm (already reset).
+int ifr_victim_enqueue(ifr_ctx *ctx, const ifr_victim_cfg *c, cudaStream_t stream, DevTiming *tm) {
+    const int K = c->repeats > 0 ? c->repeats : 1;
+    const int sms = ctx->info.num_sms;
+    for (int rep = 0; rep < K; ++rep) {
+        switch (c->kind) {
+            case IFR_V_TRIAD: {
+                const int grid = c->grid ? c->grid : sms * 8;
+                ifr_carveout((const void *)triad_kernel);
+                triad_kernel<<<grid, 256, 0, stream>>>((float *)c->out, (const float *)c->in0, (const float *)c->in1,
+                                                       c->scalar, c->n, tm);
+                break;
+            }
+            case IFR_V_LAYERNORM:
+            case IFR_V_SOFTMAX: {
+                const int64_t rows = c->m;
+                const int cols = (int)c->n;
+                const int c4 = cols / 4;
+                const bool ln = c->kind == IFR_V_LAYERNORM;
+                int grid = c->grid ? c->grid : (int)(rows < (int64_t)sms * 8 ? rows : (int64_t)sms * 8);
+                if (c4 <= 256 * 4) {
+                    grid = c->grid ? c->grid : (int)(rows < (int64_t)sms * 8 ? rows : (int64_t)sms * 8);
+                    if (ln) launch_ln<256, 4>(grid, stream, c, tm); else launch_sm<256, 4>(grid, stream, c, tm);
+                } else if (c4 <= 256 * 8) {
+                    if (ln) launch_ln<256, 8>(grid, stream, c, tm); else launch_sm<256, 8>(grid, stream, c, tm);
+                } else {
+                    grid = c->grid ? c->grid : (int)(rows < (int64_t)sms * 2 ? rows : (int64_t)sms * 2);
+                    if (ln) launch_ln<1024, 8>(grid, stream, c, tm); else launch_sm<1024, 8>(grid, stream, c, tm);
+                }
+                break;
+            }
+            case IFR_V_GEMV: {
+                const int64_t rows = c->m;
+                int grid = c->grid ? c->grid : sms * 8;
+                if ((int64_t)grid * 8 > rows) grid = (int)((rows + 7) / 8);
+                const size_t sh = (size_t)c->k * 2;
+                if (sh > 48 * 1024)
+                    cudaFuncSetAttribute(gemv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+                ifr_carveout((const void *)gemv_kernel);
+                gemv_kernel<<<grid, 256, sh, stream>>>((const __nv_bfloat16 *)c->in0, (const __nv_bfloat16 *)c->in1,
+                                                       (float *)c->out, rows, (int)c->k, tm);
+                break;
+            }
+            case IFR_V_HIST: {
+                IFR_CUDA(cudaMemsetAsync(c->out, 0, 256 * sizeof(uint32_t), stream));
+                int grid = c->grid ? c->grid : sms * 8;
+                ifr_carveout((const void *)hist_kernel);
+                hist_kernel<<<grid, 256, 0, stream>>>((const int32_t *)c->in0, c->n, (uint32_t *)c->out, tm);
+                break;
+            }
+            case IFR_V_GEMM: {
+                int rc = ifr_gemm_enqueue(ctx, c, stream, tm);
+                if (rc != IFR_OK) return rc;
+                break;
+            }
+            default: return IFR_ERR_ARG;
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return ifr_cuda_fail(e, "victim launch", __FILE__, __LINE__);
+        ctx->kernel_launches += 1;
+    }
+    return IFR_OK;
+}
+
+extern "C" int ifr_victim_launch(ifr_ctx *ctx, const ifr_victim_cfg *cfg, void *stream, ifr_timing *out) {
+    if (!ctx) return IFR_ERR_ARG;
+    int rc = ifr_victim_validate(ctx, cfg);
+    if (rc != IFR_OK) return rc;
+    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->s_victim;
+    DevTiming *tm = ctx->d_timing;
+    rc = ifr_timing_reset(tm, 1, st, nullptr);
+    if (rc != IFR_OK) return rc;
+    ctx->kernel_launches += 1;
+    IFR_CUDA(cudaEventRecord(ctx->ev_a, st));
+    rc = ifr_victim_enqueue(ctx, cfg, st, tm);
+    if (rc != IFR_OK) return rc;
+    IFR_CUDA(cudaEventRecord(ctx->ev_b, st));
+    IFR_CUDA(cudaEventSynchronize(ctx->ev_b));
+    if (out) {
+        DevTiming h;
+        IFR_CUDA(cudaMemcpy(&h, tm, sizeof h, cudaMemcpyDeviceToHost));
+        ifr_timing_to_host(h, cfg->repeats > 0 ? cfg->repeats : 1, out);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ctx->ev_a, ctx->ev_b);
+        out->event_ms = ms;
+    }
+    return IFR_OK;
+}
+
+extern "C" int ifr_launch_count(ifr_ctx *ctx, uint64_t *out) {
+    if (!ctx || !out) return IFR_ERR_ARG;
+    *out = ctx->kernel_launches;
+    return IFR_OK;
+}

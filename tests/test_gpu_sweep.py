@@ -1,0 +1,71 @@
+"""GPU sweep (plain and graph-batched) on the smallest configuration: FP32 triad
+victim, HBM stream stressor at 0/25/50/100 % of SMs; the library's reduction must
+equal the oracle's recomputation from the same raw timestamps."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import ifr_inputs as I
+from oracle import reduction as R
+import paper_2501_16909_b300 as ifr
+from paper_2501_16909_b300 import _abi as A
+from tests.gpu_common import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    need_gpu()
+    ctx = ifr.Context(0)
+    S = ctx.info["num_sms"]
+    n = 1 << 22
+    b = I.torch_uniform_pm1(0, n, "cuda")
+    c = I.torch_uniform_pm1(0, n, "cuda", start=n)
+    a = torch.empty(n, device="cuda")
+    buf = I.torch_u32_as_i32(1, (256 << 20) // 4, "cuda")
+    victims = [ifr.victim_cfg(A.IFR_V_TRIAD, b, c, a, n=n, scalar=1.5, repeats=8)]
+    fr = [0.25, 0.5, 1.0]
+    levels = [[ifr.stressor_cfg(A.IFR_S_HBM, sm_count=max(1, round(f * S)), blocks_per_sm=2, block=512,
+                                working_set_bytes=256 << 20, buf=buf, seed=1) for f in fr]]
+    yield ctx, victims, levels, (b, c, a, buf)
+    ctx.close()
+
+
+def _check(cells, n_levels, repeats):
+    assert len(cells) == repeats * (1 + (n_levels + 1))
+    d = ifr.cells_to_dicts(cells)
+    valid = [x for x in d if x["valid"]]
+    assert len(valid) >= 0.8 * len(d)
+    for x in d:
+        assert x["valid"] == (1 if R.cell_valid(x) else 0)
+    got = ifr.ifr_sensitivity(cells, 0, 1, n_levels)
+    want = R.sensitivity(d, 0, 1, n_levels)
+    assert got["t0"] == want["t0"]
+    for l in range(n_levels + 1):
+        assert ifr.isclose_nan(got["slowdown"][0][l], want["slowdown"][0][l])
+    assert got["monotone"] == want["monotone"]
+    return got
+
+
+def test_plain_sweep_config1(setup):
+    ctx, victims, levels, _ = setup
+    cells = ctx.sweep(victims, levels, repeats=3, batched=False)
+    got = _check(cells, 3, 3)
+    sd = got["slowdown"][0]
+    # harness-only launch (level 0) does not slow the victim; the full HBM stressor does
+    assert abs(sd[0] - 1.0) <= 3 * got["noise"] + 0.1
+    assert sd[3] > 1.2
+    # every colocated cell recorded a running stressor
+    for c in cells:
+        if c.stressor >= 0 and c.level > 0:
+            assert c.stress.blocks_active > 0 and c.stress.work > 0
+
+
+def test_batched_sweep_config1(setup):
+    ctx, victims, levels, _ = setup
+    cells = ctx.sweep(victims, levels, repeats=3, batched=True)
+    got = _check(cells, 3, 3)
+    assert got["slowdown"][0][3] > 1.2
