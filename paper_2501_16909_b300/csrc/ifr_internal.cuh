@@ -155,8 +155,6 @@ void ifr_compute_mask(int num_sms, int sm_count, uint32_t *mask);
 int ifr_enqueue_wait_resident(ifr_ctx *ctx, int slot, cudaStream_t stream, DevTiming *tm, uint64_t timeout_ns);
 int ifr_enqueue_stop(ifr_ctx *ctx, int slot, cudaStream_t stream);
 
-// tcgen05 tensor stressor (ifr_tensor.cu)
-int ifr_tensor_stressor_launch(const StressParams &p, DevStress *st, int grid, int block, cudaStream_t stream);
 
 // victims (ifr_victims.cu)
 int ifr_victim_validate(ifr_ctx *ctx, const ifr_victim_cfg *cfg);

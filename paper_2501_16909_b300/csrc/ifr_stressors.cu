@@ -14,7 +14,10 @@
 #include <string.h>
 #include <time.h>
 
+#include <cuda_bf16.h>
+
 #include "ifr_internal.cuh"
+#include "ifr_tcgen05.cuh"
 
 namespace {
 
@@ -64,6 +67,15 @@ __device__ int claim_slot(DevStress *st, const StressParams &p, uint32_t sm) {
     }
     __threadfence();
     atomicAdd(&st->arrived, 1u);
+    if (k < 0 && p.planned > 0) {
+        // A surplus block stays resident (bounded) until every planned slot is
+        // claimed: the grid equals the GPU's block capacity, so while nobody
+        // leaves, each allowed SM holds enough blocks to fill its slots.
+        const uint64_t t_end = ifr_gtimer() + 200000ull;
+        uint32_t it = 0;
+        while (ifr_ld_volatile(&st->active) < (uint32_t)p.planned && ifr_gtimer() < t_end && ++it < kMaxSpin)
+            __nanosleep(256);
+    }
     return k;
 }
 
@@ -290,6 +302,97 @@ __global__ void __launch_bounds__(1024) smem_stress_kernel(DevStress *st, Stress
     if (threadIdx.x == 0) write_log(p, st, c, round, (uint64_t)round * kSmemPasses * 32, cs, 0u);
 }
 
+// ------------------------------------------------------------------ BF16 tensor pipe
+// One 128-thread block per allowed SM holds A (128x64) and B (128x64, K-major)
+// bf16 tiles of small integers in shared memory (128-byte swizzle) and a
+// 128x128 fp32 accumulator in TMEM.  Thread 0 issues, per round, kTensorGroup
+// tile products (4 tcgen05.mma of K = 16 each) into the zeroed accumulator, then
+// commits and waits (bounded) on an mbarrier.  The accumulator ends as
+// kTensorGroup * A B^T, exact in fp32; its XOR is the block checksum.
+constexpr int kTensorGroup = 64;
+
+__global__ void __launch_bounds__(128, 1) tensor_stress_kernel(DevStress *st, StressParams p) {
+    extern __shared__ uint8_t t_smem_raw[];
+    __shared__ int s_k;
+    __shared__ uint64_t s_t0;
+    __shared__ int s_go[2];
+    __shared__ uint32_t s_red[32];
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_fail;
+    BlockCtl c;
+    if (!block_enter(st, p, c, &s_k, &s_t0)) return;
+    uint8_t *base = (uint8_t *)(((uintptr_t)t_smem_raw + 1023u) & ~(uintptr_t)1023u);
+    uint8_t *sA = base, *sB = base + 16384;
+    const int warp = threadIdx.x >> 5;
+    if (warp == 0) {
+        tc::tmem_alloc(&s_tmem, 128);
+        tc::tmem_relinquish();
+    }
+    const uint64_t s0 = p.seed << 32;
+    for (int e = threadIdx.x; e < 8192; e += blockDim.x) {
+        const uint32_t row = (uint32_t)e >> 6, col = (uint32_t)e & 63u;
+        const uint64_t ua = ifr_splitmix64(s0, (uint64_t)c.k * 16384ull + (uint64_t)e);
+        const uint64_t ub = ifr_splitmix64(s0, (uint64_t)c.k * 16384ull + 8192ull + (uint64_t)e);
+        *(__nv_bfloat16 *)(sA + tc::sw128_offset(row, col)) = __int2bfloat16_rn((int)((ua >> 32) % 5u) - 2);
+        *(__nv_bfloat16 *)(sB + tc::sw128_offset(row, col)) = __int2bfloat16_rn((int)((ub >> 32) % 5u) - 2);
+    }
+    tc::fence_proxy_async_smem();
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&s_bar, 1);
+        tc::fence_mbar_init();
+        s_fail = 0;
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = s_tmem;
+    const uint64_t adesc = tc::desc_sw128(tc::smem_u32(sA));
+    const uint64_t bdesc = tc::desc_sw128(tc::smem_u32(sB));
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 128);
+    int64_t round = 0;
+    for (;; ++round) {
+        if (threadIdx.x == 0) {
+            int go = round_decision(st, p, round, c);
+            if (go) {
+                for (int g = 0; g < kTensorGroup; ++g)
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        tc::mma_bf16(tmem, adesc + 2ull * kk, bdesc + 2ull * kk, idesc, (uint32_t)((g | kk) != 0));
+                tc::mma_commit(&s_bar);
+                if (!tc::mbar_wait(&s_bar, (uint32_t)(round & 1), c.deadline + 100000000ull)) {
+                    c.status = IFR_ERR_TIMEOUT;
+                    s_fail = 1;
+                    go = 0;
+                }
+            }
+            s_go[round & 1] = go;
+        }
+        __syncthreads();
+        if (!s_go[round & 1]) break;
+    }
+    tc::fence_after();
+    uint32_t acc = 0u;
+    if (round > 0 && !s_fail) {
+#pragma unroll 1
+        for (int cc = 0; cc < 128; cc += 32) {
+            uint32_t r[32];
+            tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc, r);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 32; ++j) acc ^= r[j];
+        }
+    }
+    const uint32_t cs = ifr_block_xor(acc, s_red);
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after();
+        tc::tmem_dealloc(tmem, 128);
+    }
+    if (threadIdx.x == 0) write_log(p, st, c, round, (uint64_t)round * kTensorGroup, cs, 0u);
+}
+
 // ------------------------------------------------------------------ block scheduler
 // Many short blocks of one warp.  Every block folds LCG^16(q ^ seed) into one of
 // 64 XOR slots (q = launch * blocks + blockIdx); blocks on allowed SMs that see no
@@ -367,15 +470,24 @@ int kind_default_bps(int kind) {
 }
 
 template <int W>
-int launch_smem(dim3 g, dim3 b, size_t sh, cudaStream_t s, DevStress *st, const StressParams &p) {
+const void *smem_fn() {
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(smem_stress_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024 + 1024);
         attr = true;
     }
-    ifr_carveout((const void *)smem_stress_kernel<W>);
-    smem_stress_kernel<W><<<g, b, sh, s>>>(st, p);
-    return IFR_OK;
+    return (const void *)smem_stress_kernel<W>;
+}
+
+const void *smem_kernel_for(int ways) {
+    switch (ways) {
+        case 1: return smem_fn<1>();
+        case 2: return smem_fn<2>();
+        case 4: return smem_fn<4>();
+        case 8: return smem_fn<8>();
+        case 16: return smem_fn<16>();
+        default: return smem_fn<32>();
+    }
 }
 
 }  // namespace
@@ -405,7 +517,9 @@ static int validate_cfg(ifr_ctx *ctx, const ifr_stressor_cfg *c) {
         if (!c->buf || ((uintptr_t)c->buf & 15u)) return IFR_ERR_ARG;
         if (c->working_set_bytes < chunk || c->working_set_bytes % chunk) return IFR_ERR_ARG;
     }
-    if (c->kind == IFR_S_TENSOR && c->block != 0 && c->block != 128) return IFR_ERR_ARG;
+    // one 128-thread block holds 128 TMEM columns; at most 2 per SM leave 256 of the
+    // 512 columns for a GEMM victim block (so a TMEM allocation never waits long)
+    if (c->kind == IFR_S_TENSOR && ((c->block != 0 && c->block != 128) || c->blocks_per_sm > 2)) return IFR_ERR_ARG;
     if (c->kind == IFR_S_SCHED && (c->sched_blocks < 0 || c->sched_launches < 0 || c->sched_cycles < 0))
         return IFR_ERR_ARG;
     if (c->mask_mode != 0) return IFR_ERR_UNSUPPORTED;
@@ -441,8 +555,46 @@ int ifr_stressor_enqueue(ifr_ctx *ctx, const ifr_stressor_cfg *cfg, cudaStream_t
     const int block = cfg->block ? cfg->block : kind_default_block(kind);
     s.block = block;
     s.planned = p.planned;
-    s.grid = num_sms * p.bps;
     s.launches = 1;
+    // kernel and dynamic shared memory of this kind
+    const void *fn = nullptr;
+    size_t sh = 0;
+    int ways = 0;
+    switch (kind) {
+        case IFR_S_L2:
+        case IFR_S_HBM: fn = (const void *)stream_stress_kernel; break;
+        case IFR_S_FMA:
+            fn = p.ilp == 1 ? (const void *)fma_stress_kernel<1>
+               : p.ilp == 2 ? (const void *)fma_stress_kernel<2>
+               : p.ilp == 4 ? (const void *)fma_stress_kernel<4>
+                            : (const void *)fma_stress_kernel<8>;
+            break;
+        case IFR_S_SMEM_CF:
+        case IFR_S_SMEM_32W:
+            ways = cfg->smem_ways ? cfg->smem_ways : (kind == IFR_S_SMEM_CF ? 1 : 32);
+            fn = smem_kernel_for(ways);
+            sh = (size_t)(block / 32) * 4096;
+            break;
+        case IFR_S_TENSOR:
+            fn = (const void *)tensor_stress_kernel;
+            sh = 32768 + 1024;
+            break;
+        default: break;
+    }
+    // Launch enough blocks to fill every SM in the first wave (num_sms x occupancy):
+    // each allowed SM then receives at least blocks_per_sm blocks to claim its
+    // slots; the surplus blocks exit at once.
+    if (fn) {
+        ifr_carveout(fn);
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kind == IFR_S_TENSOR ? 128 : block, sh) !=
+            cudaSuccess)
+            occ = 0;
+        if (occ > IFR_MAX_BPS) occ = IFR_MAX_BPS;
+        s.grid = num_sms * (occ > p.bps ? occ : p.bps);
+    } else {
+        s.grid = num_sms * p.bps;
+    }
     ifr_carveout((const void *)stress_reset_kernel);
     stress_reset_kernel<<<1, 256, 0, stream>>>(s.d_state);
     IFR_CUDA(cudaGetLastError());
@@ -455,47 +607,31 @@ int ifr_stressor_enqueue(ifr_ctx *ctx, const ifr_stressor_cfg *cfg, cudaStream_t
         case IFR_S_HBM:
             p.buf = (const int4 *)cfg->buf;
             p.n_chunks = cfg->working_set_bytes / ((int64_t)block * 64);
-            ifr_carveout((const void *)stream_stress_kernel);
             stream_stress_kernel<<<grid, blk, 0, stream>>>(s.d_state, p);
             break;
         case IFR_S_FMA:
             switch (p.ilp) {
-                case 1:
-                    ifr_carveout((const void *)fma_stress_kernel<1>);
-                    fma_stress_kernel<1><<<grid, blk, 0, stream>>>(s.d_state, p);
-                    break;
-                case 2:
-                    ifr_carveout((const void *)fma_stress_kernel<2>);
-                    fma_stress_kernel<2><<<grid, blk, 0, stream>>>(s.d_state, p);
-                    break;
-                case 4:
-                    ifr_carveout((const void *)fma_stress_kernel<4>);
-                    fma_stress_kernel<4><<<grid, blk, 0, stream>>>(s.d_state, p);
-                    break;
-                default:
-                    ifr_carveout((const void *)fma_stress_kernel<8>);
-                    fma_stress_kernel<8><<<grid, blk, 0, stream>>>(s.d_state, p);
-                    break;
+                case 1: fma_stress_kernel<1><<<grid, blk, 0, stream>>>(s.d_state, p); break;
+                case 2: fma_stress_kernel<2><<<grid, blk, 0, stream>>>(s.d_state, p); break;
+                case 4: fma_stress_kernel<4><<<grid, blk, 0, stream>>>(s.d_state, p); break;
+                default: fma_stress_kernel<8><<<grid, blk, 0, stream>>>(s.d_state, p); break;
             }
             break;
         case IFR_S_SMEM_CF:
-        case IFR_S_SMEM_32W: {
-            int w = cfg->smem_ways ? cfg->smem_ways : (kind == IFR_S_SMEM_CF ? 1 : 32);
-            p.ways = w;
-            size_t sh = (size_t)(block / 32) * 4096;
-            switch (w) {
-                case 1: launch_smem<1>(grid, blk, sh, stream, s.d_state, p); break;
-                case 2: launch_smem<2>(grid, blk, sh, stream, s.d_state, p); break;
-                case 4: launch_smem<4>(grid, blk, sh, stream, s.d_state, p); break;
-                case 8: launch_smem<8>(grid, blk, sh, stream, s.d_state, p); break;
-                case 16: launch_smem<16>(grid, blk, sh, stream, s.d_state, p); break;
-                default: launch_smem<32>(grid, blk, sh, stream, s.d_state, p); break;
+        case IFR_S_SMEM_32W:
+            p.ways = ways;
+            switch (ways) {
+                case 1: smem_stress_kernel<1><<<grid, blk, sh, stream>>>(s.d_state, p); break;
+                case 2: smem_stress_kernel<2><<<grid, blk, sh, stream>>>(s.d_state, p); break;
+                case 4: smem_stress_kernel<4><<<grid, blk, sh, stream>>>(s.d_state, p); break;
+                case 8: smem_stress_kernel<8><<<grid, blk, sh, stream>>>(s.d_state, p); break;
+                case 16: smem_stress_kernel<16><<<grid, blk, sh, stream>>>(s.d_state, p); break;
+                default: smem_stress_kernel<32><<<grid, blk, sh, stream>>>(s.d_state, p); break;
             }
             break;
-        }
         case IFR_S_TENSOR:
-            rc = ifr_tensor_stressor_launch(p, s.d_state, s.grid, 128, stream);
-            if (rc != IFR_OK) return rc;
+            s.block = 128;
+            tensor_stress_kernel<<<grid, 128, sh, stream>>>(s.d_state, p);
             break;
         case IFR_S_SCHED: {
             p.sched_blocks = cfg->sched_blocks ? cfg->sched_blocks : 100000;

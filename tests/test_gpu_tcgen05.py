@@ -1,0 +1,92 @@
+"""GPU parity of the tcgen05 kernels: the BF16 tensor-pipe stressor (bit-exact
+small-integer tiles) and the BF16 GEMM victim (fp64 oracle, 2e-2 relative)."""
+import numpy as np
+import pytest
+import torch
+
+import ifr_inputs as I
+import oracle
+import paper_2501_16909_b300 as ifr
+from paper_2501_16909_b300 import _abi as A
+from tests.gpu_common import BF16_TOL, need_gpu, spread_mask
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    need_gpu()
+    c = ifr.Context(0)
+    yield c
+    c.close()
+
+
+def _gemm(ctx, M, N, K, seed=11, repeats=1):
+    Ab = I.torch_normal_bf16(seed, M * K, "cuda").view(M, K)
+    Bb = I.torch_normal_bf16(seed + 1, N * K, "cuda").view(N, K)
+    C = torch.full((M, N), float("nan"), device="cuda")
+    t = ctx.victim_launch(ifr.victim_cfg(A.IFR_V_GEMM, Ab, Bb, C, m=M, n=N, k=K, repeats=repeats))
+    return Ab, Bb, C, t
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (128, 256, 128), (256, 384, 192), (384, 512, 1024)])
+def test_gemm_small_all_entries(ctx, M, N, K):
+    Ab, Bb, C, t = _gemm(ctx, M, N, K)
+    assert t["status"] == 0
+    ref = Ab.double().cpu() @ Bb.double().cpu().T
+    got = C.double().cpu()
+    assert torch.isfinite(got).all()
+    rms = float(ref.pow(2).mean().sqrt())
+    err = (got - ref).abs()
+    assert bool((err <= BF16_TOL * torch.maximum(ref.abs(), torch.tensor(rms))).all())
+    assert float(torch.linalg.norm(got - ref) / torch.linalg.norm(ref)) <= 1e-5
+
+
+def test_gemm_full_size_sampled_vs_oracle(ctx):
+    M = N = K = 4096
+    Ab, Bb, C, t = _gemm(ctx, M, N, K, seed=21, repeats=2)
+    assert t["status"] == 0 and t["sms_touched"] > 100
+    rng = np.random.default_rng(0)
+    ij = np.stack([rng.integers(0, M, 400), rng.integers(0, N, 400)], axis=1)
+    ij = np.concatenate([ij, [[0, 0], [M - 1, N - 1], [127, 255], [128, 256]]])
+    A_np = oracle.f32_bits_to_bf16_bits(I.np_normal_bf16(21, np.arange(M * K))).reshape(M, K)
+    B_np = oracle.f32_bits_to_bf16_bits(I.np_normal_bf16(22, np.arange(N * K))).reshape(N, K)
+    ref = oracle.gemm_entries(A_np, B_np, ij)
+    got = C.cpu().numpy()[ij[:, 0], ij[:, 1]].astype(np.float64)
+    rms = np.sqrt(np.mean(ref * ref))
+    assert np.all(np.abs(got - ref) <= BF16_TOL * np.maximum(np.abs(ref), rms))
+    assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref)
+    assert torch.isfinite(C).all()
+
+
+def test_gemm_rejects_bad_shapes(ctx):
+    import ctypes as C
+
+    L = A.load()
+    x = torch.empty(1 << 16, device="cuda")
+    t = A.ifr_timing()
+    for m, n, k in [(100, 128, 64), (128, 100, 64), (128, 128, 32), (0, 128, 64)]:
+        cfg = ifr.victim_cfg(A.IFR_V_GEMM, x, x, x, m=m, n=n, k=k)
+        assert L.ifr_victim_launch(ctx._h, C.byref(cfg), None, C.byref(t)) == A.IFR_ERR_ARG
+
+
+@pytest.mark.parametrize("sm_frac,bps,rounds", [(1.0, 1, 3), (0.5, 2, 2)])
+def test_tensor_stressor_bit_exact(ctx, sm_frac, bps, rounds):
+    S = ctx.info["num_sms"]
+    n_sm = max(1, int(S * sm_frac))
+    cfg = ifr.stressor_cfg(A.IFR_S_TENSOR, sm_count=n_sm, blocks_per_sm=bps, max_rounds=rounds, seed=12)
+    r, logs = ctx.run_stressor(cfg, 20000)
+    assert r["status"] == 0 and len(logs) == n_sm * bps
+    assert {L["smid"] for L in logs} <= spread_mask(S, n_sm)
+    for L in logs[:: max(1, len(logs) // 8)]:
+        assert L["rounds"] == rounds and L["work"] == rounds * 64
+        assert L["checksum"] == oracle.tensor_block(12, L["index"], 64), L
+
+
+def test_tensor_stressor_rejects_too_many_blocks(ctx):
+    import ctypes as C
+
+    L = A.load()
+    h = C.c_int()
+    cfg = ifr.stressor_cfg(A.IFR_S_TENSOR, sm_count=1, blocks_per_sm=3)
+    assert L.ifr_stressor_launch(ctx._h, C.byref(cfg), None, C.byref(h)) == A.IFR_ERR_ARG
