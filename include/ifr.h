@@ -175,6 +175,32 @@ int ifr_stressor_block_logs(ifr_ctx *ctx, int handle, ifr_block_log *out, int ca
 /* Free the slot of a finished stressor. */
 int ifr_stressor_release(ifr_ctx *ctx, int handle);
 
+/* Allocation-free fixed-work run of the L2/HBM stream stressor (the paper has no
+ * counterpart: this is a convenience of the library).  Some callers cannot call
+ * cudaMalloc: code running while a stream is being captured into a CUDA graph in a
+ * mode that rejects allocation calls, latency-critical loops that must not block
+ * on the device allocator (cudaMalloc can synchronise the device), and hosts that
+ * own a fixed device-memory budget and so never create an ifr_ctx (ifr_init
+ * allocates).  This entry point needs no context and allocates nothing: its
+ * control state (stop flag, counters, per-SM claim table) is a 4 KiB file-scope
+ * device array that every GPU loading the library keeps until the process exits.
+ * Arguments: kind IFR_S_L2 or IFR_S_HBM; buf / working_set_bytes / block as in
+ * ifr_stressor_cfg; sm_count SMs (spread as in ifr_stressor_cfg) with
+ * blocks_per_sm blocks each; max_rounds > 0 rounds per block (fixed work, no stop
+ * request exists); deadline_ns as in ifr_stressor_cfg (0 = 2 s); stream a
+ * cudaStream_t (NULL = legacy default stream); logs_out a caller-owned device
+ * array of logs_cap >= sm_count * blocks_per_sm records, written in active-index
+ * order (unclaimed slots keep index -1).  Asynchronous: synchronise `stream`
+ * before reading logs_out.  The first call on a device looks up the array's
+ * device address with that device current, so make it before any stream capture.
+ * All calls share the array, which keeps the last call's contents (the call
+ * clears it on the stream first): calls whose kernels overlap on the GPU race.
+ * Errors: IFR_ERR_ARG (kind, pointer, alignment, size, rounds), IFR_ERR_CAPACITY
+ * (logs_cap too small, or a device with more than IFR_MAX_SMS SMs), IFR_ERR_CUDA. */
+int ifr_stream_stressor_noalloc(int kind, const void *buf, int64_t working_set_bytes, int sm_count,
+                                int blocks_per_sm, int block, int64_t max_rounds, uint64_t deadline_ns,
+                                void *stream, ifr_block_log *logs_out, int logs_cap);
+
 /* ---- victims ------------------------------------------------------------ */
 /* Workloads whose slowdown is measured (Sec. 4: the paper uses LLM decode and
  * torch.mm; this library uses kernels with textbook definitions). */

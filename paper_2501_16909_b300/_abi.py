@@ -142,6 +142,8 @@ def load():
         "ifr_stressor_wait": (i32, [vp, i32, i32, P(ifr_stressor_result)]),
         "ifr_stressor_block_logs": (i32, [vp, i32, P(ifr_block_log), i32, P(i32)]),
         "ifr_stressor_release": (i32, [vp, i32]),
+        "ifr_stream_stressor_noalloc": (i32, [i32, vp, C.c_int64, i32, i32, i32, C.c_int64, C.c_uint64, vp,
+                                               vp, i32]),
         "ifr_victim_launch": (i32, [vp, P(ifr_victim_cfg), vp, P(ifr_timing)]),
         "ifr_sweep": (i32, [vp, P(ifr_sweep_plan), P(ifr_cell_result), C.c_size_t, P(C.c_size_t)]),
         "ifr_sensitivity": (i32, [P(ifr_cell_result), C.c_size_t, i32, i32, i32, P(C.c_double),

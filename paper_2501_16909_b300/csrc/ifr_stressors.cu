@@ -14,6 +14,8 @@
 #include <string.h>
 #include <time.h>
 
+#include <mutex>
+
 #include <cuda_bf16.h>
 
 #include "ifr_internal.cuh"
@@ -801,5 +803,86 @@ extern "C" int ifr_stressor_release(ifr_ctx *ctx, int handle) {
         if (rc != IFR_OK && rc != IFR_ERR_TIMEOUT) return rc;
     }
     s.in_use = 0;
+    return IFR_OK;
+}
+
+// ------------------------------------------------------------------ allocation-free variant
+// Control state (stop flag, counters, per-SM claims) of ifr_stream_stressor_noalloc.
+// It lives in this file-scope device array, so the entry point needs no
+// cudaMalloc; every GPU that loads the library keeps these bytes until exit.
+// All calls share the array: calls whose kernels overlap on the GPU race on it.
+#define IFR_NOALLOC_SCRATCH_BYTES 4096
+static __device__ __align__(256) unsigned char g_noalloc_scratch[IFR_NOALLOC_SCRATCH_BYTES];
+static_assert(sizeof(DevStress) <= IFR_NOALLOC_SCRATCH_BYTES, "scratch array too small for DevStress");
+
+namespace {
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kNoallocMaxDevices];  // device address of the array, per device (host cache)
+
+__global__ void noalloc_logs_clear_kernel(ifr_block_log *logs, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        ifr_block_log L;
+        memset(&L, 0, sizeof L);
+        L.index = -1;
+        logs[i] = L;
+    }
+}
+}  // namespace
+
+extern "C" int ifr_stream_stressor_noalloc(int kind, const void *buf, int64_t working_set_bytes, int sm_count,
+                                           int blocks_per_sm, int block, int64_t max_rounds, uint64_t deadline_ns,
+                                           void *stream, ifr_block_log *logs_out, int logs_cap) {
+    if (kind != IFR_S_L2 && kind != IFR_S_HBM) return IFR_ERR_ARG;
+    if (!buf || ((uintptr_t)buf & 15u) || !logs_out || ((uintptr_t)logs_out & 7u)) return IFR_ERR_ARG;
+    if (block <= 0 || block > 1024 || block % 32) return IFR_ERR_ARG;
+    const int64_t chunk = (int64_t)block * 64;
+    if (working_set_bytes < chunk || working_set_bytes % chunk) return IFR_ERR_ARG;
+    if (max_rounds <= 0 || blocks_per_sm <= 0 || blocks_per_sm > IFR_MAX_BPS) return IFR_ERR_ARG;
+    int dev = 0, num_sms = 0;
+    IFR_CUDA(cudaGetDevice(&dev));
+    IFR_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+    // the array holds per-SM claim counters for at most IFR_MAX_SMS SMs
+    if (num_sms > IFR_MAX_SMS || dev >= kNoallocMaxDevices) return IFR_ERR_CAPACITY;
+    if (sm_count <= 0 || sm_count > num_sms) return IFR_ERR_ARG;
+    if ((int64_t)sm_count * blocks_per_sm > logs_cap) return IFR_ERR_CAPACITY;
+    void *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> g(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            // first call on this device: look up the array's device address with
+            // the device current (host code cannot use the symbol itself)
+            void *ptr = nullptr;
+            IFR_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+            g_noalloc_addr[dev] = ptr;
+        }
+        scratch = g_noalloc_addr[dev];
+    }
+    DevStress *st = (DevStress *)scratch;
+    cudaStream_t s = (cudaStream_t)stream;
+    StressParams p;
+    memset(&p, 0, sizeof p);
+    p.kind = kind;
+    p.bps = blocks_per_sm;
+    ifr_compute_mask(num_sms, sm_count, p.mask);
+    p.planned = sm_count * blocks_per_sm;
+    p.max_rounds = max_rounds;
+    p.deadline_ns = deadline_ns ? deadline_ns : 2000000000ull;
+    p.duty = 1.f;
+    p.period_ns = 100000u;
+    p.logs = logs_out;
+    p.buf = (const int4 *)buf;
+    p.n_chunks = working_set_bytes / chunk;
+    ifr_carveout((const void *)stream_stress_kernel);
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)stream_stress_kernel, block, 0) != cudaSuccess)
+        occ = 0;
+    if (occ > IFR_MAX_BPS) occ = IFR_MAX_BPS;
+    const int grid = num_sms * (occ > blocks_per_sm ? occ : blocks_per_sm);
+    // the previous call's counters and claims are still in the array: clear them
+    stress_reset_kernel<<<1, 256, 0, s>>>(st);
+    noalloc_logs_clear_kernel<<<(p.planned + 127) / 128, 128, 0, s>>>(logs_out, p.planned);
+    stream_stress_kernel<<<grid, block, 0, s>>>(st, p);
+    IFR_CUDA(cudaGetLastError());
     return IFR_OK;
 }
