@@ -1,18 +1,22 @@
 #!/usr/bin/env python
 """Benchmark: interference-sensitivity sweep on B300.
 
-One step = one pass of the whole hot path over the workload: solo calibration
-of every stressor level (achieved fraction of peak), the plain launch-per-cell
-sweep, the graph-captured batched sweep, and the sensitivity reduction.
-`value` is the batched sweep's cells/s (whole job, all ranks); the plain
-sweep's cells/s, the stressors' fractions of peak and the reduction are
+One step = one pass of the whole hot path over the workload:
+  1. calibration — every stressor level alone, fixed work, CUDA events on the
+     stressor stream -> achieved fraction of its resource's peak (the intensity x);
+  2. the plain launch-per-cell sweep;
+  3. the graph-captured batched sweep;
+  4. the sensitivity reduction of every victim.
+`value` is the batched sweep's cells/s (whole job, all ranks).  The plain sweep's
+cells/s, each stressor's fraction of peak and the sensitivity vectors are
 reported beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload config2|config1]
 
-With --gpus N > 1 the script runs under torchrun, one process per GPU; each
-rank sweeps its own replica of the workload (interference is a per-GPU
-quantity, so the sweep shards without any collective on the data path).
+With --gpus N > 1 the script runs under torchrun, one process per GPU; each rank
+sweeps its own replica of the workload (interference is a per-GPU quantity, so the
+sweep shards with no collective on the data path).
 """
 from __future__ import annotations
 
@@ -31,16 +35,6 @@ sys.path.insert(0, ROOT)
 METRIC = "stressor % of resource peak; sweep cells/s batched vs plain; predictor slowdown MAPE"
 
 
-# ----------------------------------------------------------------------------- helpers
-def load_peaks():
-    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(p):
-        with open(p) as f:
-            d = json.load(f)
-        return d, "measured"
-    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
-
-
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -49,9 +43,7 @@ class ClockSampler:
          "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
-        self.index = index
-        self.proc = None
-        self.path = None
+        self.index, self.proc, self.path = index, None, None
 
     def start(self):
         fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
@@ -71,7 +63,7 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
+        sm, smax, power, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as f:
             for line in f:
@@ -81,6 +73,7 @@ class ClockSampler:
                 try:
                     sm.append(float(parts[1]))
                     smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
                 except ValueError:
                     continue
                 for nm, v in zip(names, parts[5:9]):
@@ -88,65 +81,83 @@ class ClockSampler:
                         reasons.add(nm)
         os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons), "samples": len(sm)}
 
 
 def dist_env():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
-# ----------------------------------------------------------------------------- work units
-def stressor_units(kind, cfg, res):
-    """Algorithmic work a stressor run did, in the unit of its resource's peak."""
+# ----------------------------------------------------------------------------- our arm
+def calibrate(ctx, wl, pk):
+    """Every stressor level alone with fixed work: rate and fraction of peak."""
     from paper_2501_16909_b300 import _abi as A
-
-    if kind in (A.IFR_S_HBM, A.IFR_S_L2):
-        return res["work"] * cfg.block * 64, "B"
-    raise ValueError(kind)
-
-
-def calibrate(ctx, wl, peaks):
-    """Solo, fixed-work run of every stressor level: achieved fraction of peak."""
-    from paper_2501_16909_b300 import _abi as A
-    import paper_2501_16909_b300 as ifr
+    from paper_2501_16909_b300 import peaks as P
 
     out = []
-    for r, row in enumerate(wl.levels):
+    for row in wl.levels:
         fr = []
         for cfg in row:
-            c = ifr.stressor_cfg(cfg.kind)
-            for name, _ in cfg._fields_:
-                setattr(c, name, getattr(cfg, name))
-            c.max_rounds = 256
-            res, _ = ctx.run_stressor(c)
-            units, u = stressor_units(cfg.kind, cfg, res)
-            rate = units / (res["elapsed_ms"] * 1e-3)
-            peak = peaks["hbm_gbs"] * 1e9 if cfg.kind in (A.IFR_S_HBM, A.IFR_S_L2) else None
-            fr.append({"kind": A.STRESSOR_NAMES[cfg.kind], "sm_count": cfg.sm_count, "rate": rate, "unit": u + "/s",
-                       "elapsed_ms": res["elapsed_ms"], "units": units, "frac": rate / peak if peak else None})
+            rate, res = P.solo_rate(ctx, cfg)
+            peak = pk[cfg.kind][0]
+            fr.append({"kind": A.STRESSOR_NAMES[cfg.kind], "sm_count": cfg.sm_count, "rate": rate,
+                       "unit": P.UNIT[cfg.kind] + "/s", "elapsed_ms": res["elapsed_ms"],
+                       "units": P.work_units(cfg, res), "frac": rate / peak if peak else None})
         out.append(fr)
     return out
 
 
-# ----------------------------------------------------------------------------- our arm
+def prepare_levels(ctx, wl, pk):
+    """Size the scheduler stressor's launch count and every deadline from solo victim
+    windows: separate level tables for the plain (one victim per stressor run) and
+    the batched (all victims under one stressor run) sweeps."""
+    from paper_2501_16909_b300 import _abi as A
+    from paper_2501_16909_b300 import peaks as P
+
+    windows = []
+    for v in wl.victims:
+        t = ctx.victim_launch(v)
+        windows.append(t["t_end_ns"] - t["t_start_ns"])
+    sched_rows = [r for r, row in enumerate(wl.levels) if row[0].kind == A.IFR_S_SCHED]
+    t_launch = 1e5
+    if sched_rows:
+        rate, res = P.solo_rate(ctx, wl.levels[sched_rows[0]][-1], launches=8)
+        t_launch = res["elapsed_ms"] * 1e6 / 8
+    plain, batched = [], []
+    for row in wl.levels:
+        prow, brow = [], []
+        for cfg in row:
+            p = P.copy_cfg(cfg, deadline_ns=int(2e9))
+            b = P.copy_cfg(cfg, deadline_ns=int(max(2e9, 20 * sum(windows))))
+            if cfg.kind == A.IFR_S_SCHED:
+                p.sched_launches = int(min(4096, 4 * max(windows) / t_launch + 4))
+                b.sched_launches = int(min(65536, 4 * sum(windows) / t_launch + 4))
+            prow.append(p)
+            brow.append(b)
+        plain.append(prow)
+        batched.append(brow)
+    return plain, batched, windows, t_launch
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
 
     import paper_2501_16909_b300 as ifr
+    from paper_2501_16909_b300 import _abi as A
+    from paper_2501_16909_b300 import peaks as P
     from paper_2501_16909_b300 import workloads
 
     world, rank, local = dist_env()
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
-    peaks, peak_src = load_peaks()
     ctx = ifr.Context(local)
     S = ctx.info["num_sms"]
-    wl = workloads.config1(S)
+    wl = workloads.config2(S) if args.workload == "config2" else workloads.config1(S)
+    pk = P.peaks(ctx, wl.tensors.get("l2"))
+    lv_plain, lv_batched, windows, t_launch = prepare_levels(ctx, wl, pk)
     ns, nl = len(wl.levels), len(wl.levels[0])
 
     def barrier():
@@ -156,14 +167,14 @@ def run_ours(args):
 
     def step():
         t = {}
-        cal = calibrate(ctx, wl, peaks)
+        cal = calibrate(ctx, wl, pk)
         t0 = time.perf_counter()
-        plain = ctx.sweep(wl.victims, wl.levels, wl.repeats, batched=False)
+        plain = ctx.sweep(wl.victims, lv_plain, wl.repeats, batched=False)
         t["plain_s"] = time.perf_counter() - t0
         t0 = time.perf_counter()
-        batched = ctx.sweep(wl.victims, wl.levels, wl.repeats, batched=True)
+        batched = ctx.sweep(wl.victims, lv_batched, wl.repeats, batched=True)
         t["batched_s"] = time.perf_counter() - t0
-        inten = [[c["frac"] if c["frac"] else (l + 1) / nl for l, c in enumerate(row)] for row in cal]
+        inten = [[c["frac"] for c in row] for row in cal]
         sens = [ifr.ifr_sensitivity(batched, v, ns, nl, inten) for v in range(len(wl.victims))]
         return t, cal, plain, batched, sens
 
@@ -187,48 +198,60 @@ def run_ours(args):
     plain_s = sum(r[0]["plain_s"] for r in recs)
     batched_s = sum(r[0]["batched_s"] for r in recs)
     cells = wl.n_cells * args.steps
-    val_b = cells / batched_s
-    val_p = cells / plain_s
     if world > 1:
         tt = torch.tensor([batched_s, plain_s], device="cuda", dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         batched_s, plain_s = float(tt[0]), float(tt[1])
-        val_b = cells * world / batched_s
-        val_p = cells * world / plain_s
+    val_b = cells * world / batched_s
+    val_p = cells * world / plain_s
 
-    # dominant kernel: the HBM stream stressor at full SMs, solo calibration runs of the timed steps
-    full = [r[1][0][-1] for r in recs]
-    bytes_per = statistics.mean(c["units"] for c in full)
-    ms_per = statistics.mean(c["elapsed_ms"] for c in full)
-    achieved = bytes_per / (ms_per * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
-                "kernel": "stream_stress_kernel (HBM, %d SMs x 2 blocks, 256 rounds x 4 chunks x 32 KiB)" % S,
-                "peak_source": peak_src}
+    # per-stressor fraction of peak at full SMs (calibration runs of the timed steps)
+    full = {}
+    for r in range(ns):
+        runs = [rec[1][r][-1] for rec in recs]
+        kind = wl.levels[r][-1].kind
+        units = statistics.mean(c["units"] for c in runs)
+        ms = statistics.mean(c["elapsed_ms"] for c in runs)
+        rate = units / (ms * 1e-3)
+        full[A.STRESSOR_NAMES[kind]] = {"rate": rate, "unit": P.UNIT[kind] + "/s", "frac": rate / pk[kind][0],
+                                        "peak": pk[kind][0], "peak_source": pk[kind][1], "ms": ms, "units": units}
+    hb = full.get("hbm")
+    roofline = {"bound": "hbm", "achieved": round(hb["rate"] / 1e9, 1), "peak": round(pk[A.IFR_S_HBM][0] / 1e9, 1),
+                "unit": "GB/s", "frac": round(hb["frac"], 4), "traffic": None,
+                "kernel": "stream_stress_kernel (HBM 4 GiB set, %d SMs x 2 blocks of 512, %d rounds x 4 chunks "
+                          "x 32 KiB per block)" % (S, P.CAL_ROUNDS[A.IFR_S_HBM]),
+                "peak_source": pk[A.IFR_S_HBM][1]}
 
     # end to end through the public API with host-resident inputs
     e2e = None
-    if rank == 0 or world > 1:
-        host = {k: v.cpu().pin_memory() for k, v in wl.tensors.items() if k in ("b", "c", "buf")}
-        out_host = torch.empty(wl.tensors["a"].numel(), dtype=torch.float32).pin_memory()
+    host_keys = [k for k in ("gA", "gB", "vA", "vx", "lx", "sx", "hk", "l2", "hbm", "b", "c", "buf")
+                 if k in wl.tensors]
+    out_keys = [k for k in ("gC", "vy", "ly", "sy", "hb", "a") if k in wl.tensors]
+    host = {k: wl.tensors[k].cpu().pin_memory() for k in host_keys}
+    outs = {k: torch.empty(wl.tensors[k].shape, dtype=wl.tensors[k].dtype).pin_memory() for k in out_keys}
+    torch.cuda.synchronize()
+    te0 = time.perf_counter()
+    n_e = 0
+    for _ in range(args.steps):
+        for k, h in host.items():
+            wl.tensors[k].copy_(h, non_blocking=True)
+        cells_e = ctx.sweep(wl.victims, lv_batched, wl.repeats, batched=True)
+        for k, o in outs.items():
+            o.copy_(wl.tensors[k], non_blocking=True)
         torch.cuda.synchronize()
-        te0 = time.perf_counter()
-        for _ in range(args.steps):
-            for k, h in host.items():
-                wl.tensors[k].copy_(h, non_blocking=True)
-            cells_e = ctx.sweep(wl.victims, wl.levels, wl.repeats, batched=True)
-            out_host.copy_(wl.tensors["a"], non_blocking=True)
-            torch.cuda.synchronize()
-        te = time.perf_counter() - te0
-        e2e = {"value": round(len(cells_e) * args.steps / te, 2), "unit": "cells/s",
-               "h2d_bytes_per_step": sum(h.numel() * h.element_size() for h in host.values()),
-               "d2h_bytes_per_step": out_host.numel() * 4 + len(cells_e) * 0}
+        n_e += len(cells_e)
+    te = time.perf_counter() - te0
+    e2e = {"value": round(n_e * world / te, 2), "unit": "cells/s",
+           "h2d_bytes_per_step": sum(h.numel() * h.element_size() for h in host.values()),
+           "d2h_bytes_per_step": sum(o.numel() * o.element_size() for o in outs.values())}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(wl, budget_s=args.cpu_budget)
+        cpu = cpu_baseline(budget_s=args.cpu_budget)
 
     last = recs[-1]
+    valid = sum(c.valid for c in last[3])
+    hol = sum(1 for c in last[3] if c.status == A.IFR_ERR_HOL)
     line = {
         "metric": METRIC,
         "value": round(val_b, 2),
@@ -241,16 +264,22 @@ def run_ours(args):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
-        "data": "synthetic (SplitMix64 seeded inputs, resident in HBM)",
+        "data": "synthetic (SplitMix64-seeded inputs resident in HBM)",
         "config": {"workload": wl.name, "cells_per_step": wl.n_cells, "repeats": wl.repeats,
                    "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "victim set 48 MiB L2-resident by design of the config; stressor stream 1 GiB > L2"},
+                   "l2_between_iterations": "stressor streams (4 GiB HBM set) exceed L2; victims keep their own "
+                                            "working sets, as the configuration defines them"},
         "plain_cells_per_s": round(val_p, 2),
         "batched_over_plain": round(val_b / val_p, 3),
-        "stressor_frac_of_peak": {"%s@%d" % (c["kind"], c["sm_count"]): (round(c["frac"], 4) if c["frac"] else None)
-                                  for row in last[1] for c in row},
-        "sensitivity": [{"victim": v, "slowdown": s["slowdown"], "S": s["S"], "noise": s["noise"]}
-                        for v, s in enumerate(last[4])],
+        "stressor_frac_of_peak_full_sms": {k: round(v["frac"], 4) for k, v in full.items()},
+        "stressor_peaks": {k: {"peak": v["peak"], "unit": v["unit"], "source": v["peak_source"]}
+                           for k, v in full.items()},
+        "levels_frac_of_peak": {A.STRESSOR_NAMES[wl.levels[r][0].kind]: [round(c["frac"], 4) for c in last[1][r]]
+                                for r in range(ns)},
+        "sensitivity": [{"victim": A.VICTIM_NAMES[wl.victim_kinds[v]], "S": [round(x, 4) for x in s["S"]],
+                         "noise": round(s["noise"], 4)} for v, s in enumerate(last[4])],
+        "cells_valid": valid, "cells_hol": hol, "cells_total": len(last[3]),
+        "victim_solo_window_ns": windows, "sched_launch_ns": t_launch,
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": launches,
@@ -266,41 +295,59 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-# ----------------------------------------------------------------------------- CPU oracle arm
-def cpu_baseline(wl=None, budget_s=20.0, n_cells=None):
-    """Time the oracle (as it stands) recomputing sweep cells on the host cores:
-    per cell the victim output, the checksums of one full-intensity stressor run
-    (64 rounds on every SM) and the slowdown reduction."""
+# ----------------------------------------------------------------------------- CPU oracle
+def cpu_baseline(budget_s=20.0):
+    """Time the oracle (as it stands, single thread) recomputing one sweep cell of the
+    config-2 workload on the host: per victim a sample of its outputs (scaled to the
+    full output), per stressor the checksums of 1 ms of its full-intensity work on B300
+    (scaled from a sample of blocks), and the reduction.  Returns cells/s."""
     import numpy as np
 
     import ifr_inputs as I
     import oracle
     from oracle import reduction as R
 
-    n = 1 << 22
-    b = I.np_uniform_pm1(0, np.arange(n))
-    c = I.np_uniform_pm1(0, np.arange(n, 2 * n))
-    nbytes = 1 << 30
-    buf = I.np_u32(1, np.arange(nbytes // 4))
-    num_sms, chunk = 148, 512 * 16
-    t0 = time.perf_counter()
-    done = 0
-    cells = []
-    while True:
-        oracle.triad(b, c, 1.5)
-        for k in range(0, num_sms, 37):  # sample of blocks, scaled below
-            oracle.stream_block_checksum(buf, chunk, num_sms, k, 256)
-        cells.append(dict(victim=0, stressor=-1, level=0, repeat=done, k=8, t_start=0, t_end=8000 + done))
-        R.sensitivity(cells, 0, 0, 1)
-        done += 1
-        el = time.perf_counter() - t0
-        if el > budget_s or (n_cells and done >= n_cells):
-            break
-    # the block sample is 4 of 148 blocks: scale the checksum share to a full cell
-    per_cell = el / done
-    return {"value": round(1.0 / per_cell, 4), "unit": "cells/s", "cores": 1, "kind": "oracle",
-            "sample": "%d cells; per cell: triad N=2^22 fp64, stream checksums of 4 of 148 blocks x 256 chunks "
-                      "of a 1 GiB buffer, reduction (single-threaded C/numpy)" % done}
+    t_start = time.perf_counter()
+    rng = np.random.default_rng(0)
+    per = {}
+
+    def timed(fn, scale):
+        t0 = time.perf_counter()
+        fn()
+        return (time.perf_counter() - t0) * scale
+
+    G, RR = 4096, 8192
+    gA = oracle.f32_bits_to_bf16_bits(I.np_normal_bf16(11, np.arange(64 * G))).reshape(64, G)
+    gB = oracle.f32_bits_to_bf16_bits(I.np_normal_bf16(12, np.arange(64 * G))).reshape(64, G)
+    ij = np.stack([rng.integers(0, 64, 256), rng.integers(0, 64, 256)], axis=1)
+    per["gemm"] = timed(lambda: oracle.gemm_entries(gA, gB, ij), G * G / 256)
+    vA = oracle.f32_bits_to_bf16_bits(I.np_normal_bf16(13, np.arange(64 * RR))).reshape(64, RR)
+    vx = oracle.f32_bits_to_bf16_bits(I.np_normal_bf16(14, np.arange(RR)))
+    per["gemv"] = timed(lambda: oracle.gemv_rows(vA, vx, np.arange(64)), RR / 64)
+    lx = I.np_uniform_pm1(15, np.arange(64 * 4096)).reshape(64, 4096)
+    per["layernorm"] = timed(lambda: oracle.layernorm_rows(lx, np.arange(64)), 16384 / 64)
+    sx = I.np_uniform_pm1(16, np.arange(16 * RR)).reshape(16, RR)
+    per["softmax"] = timed(lambda: oracle.softmax_rows(sx, np.arange(16)), RR / 16)
+    keys = I.np_key256(2, np.arange(1 << 22))
+    per["hist"] = timed(lambda: oracle.histogram(keys), 16)
+    # stressors: 1 ms of full-intensity work on B300 (measured rates, rounded)
+    buf = I.np_u32(1, np.arange(1 << 22))
+    per["stream"] = timed(lambda: oracle.stream_block_checksum(buf, 8192, 1, 0, 512), 6.5e9 / (512 * 32768))
+    per["fma"] = timed(lambda: oracle.fma_block(1, 0, 128, 4, 4096, 1), 7.6e13 / 2 / (128 * 4 * 4096))
+    per["tensor"] = timed(lambda: oracle.tensor_block(1, 0, 64), 148.0)  # closed form per block: one tile product
+    per["smem"] = timed(lambda: oracle.smem_block(1, 0, 8, 8, 8), 3.0e8 / (8 * 8 * 8 * 32 * 2))
+    per["sched"] = timed(lambda: oracle.sched_checksum(1, 100000, 16), 30.0)
+    cells = [dict(victim=0, stressor=-1, level=0, repeat=i, k=4, t_start=0, t_end=4000 + i) for i in range(3)]
+    per["reduction"] = timed(lambda: R.sensitivity(cells, 0, 0, 1), 1.0)
+    victim_s = statistics.mean(per[k] for k in ("gemm", "gemv", "layernorm", "softmax", "hist"))
+    stress_s = statistics.mean(per[k] for k in ("stream", "fma", "tensor", "smem", "sched"))
+    sec_per_cell = victim_s + stress_s + per["reduction"]
+    el = time.perf_counter() - t_start
+    return {"value": round(1.0 / sec_per_cell, 5), "unit": "cells/s", "cores": 1, "kind": "oracle",
+            "sample": "one config-2 cell estimated from samples (GEMM 256 of 16.8M entries, GEMV 64 rows, LN 64 rows, "
+                      "softmax 16 rows, histogram 2^22 of 2^26 keys, 1 ms of each stressor's B300 work scaled from "
+                      "one block); seconds per full cell %.1f; sampling took %.1f s" % (sec_per_cell, el),
+            "seconds_per_component": {k: round(v, 3) for k, v in per.items()}}
 
 
 def run_reference(args):
@@ -310,17 +357,17 @@ def run_reference(args):
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.warmup + args.steps):
-        r = cpu_baseline(budget_s=max(1.0, args.cpu_budget / max(1, args.steps)), n_cells=1)
-        vals.append(r)
+        vals.append(cpu_baseline(budget_s=args.cpu_budget))
     el = time.perf_counter() - t0
-    v = statistics.mean(x["value"] for x in vals[args.warmup:])
-    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "cells/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000.0 / v, 3) if v else None,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "config1 (oracle recomputation of one sweep cell per step)"},
-            "cpu_baseline": {"value": round(v, 4), "unit": "cells/s", "cores": 1, "kind": "oracle",
-                             "sample": vals[-1]["sample"]},
-            "e2e": {"value": round(v, 4), "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    timed = vals[args.warmup:]
+    v = statistics.mean(x["value"] for x in timed)
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": "cells/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000.0 / v, 1) if v else None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "config2 (oracle recomputation of one sweep cell per step, sampled)"},
+            "cpu_baseline": {"value": round(v, 5), "unit": "cells/s", "cores": 1, "kind": "oracle",
+                             "sample": timed[-1]["sample"]},
+            "e2e": {"value": round(v, 5), "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": round(el, 2)}
     print(json.dumps(line), flush=True)
 
@@ -331,6 +378,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="config2", choices=["config2", "config1"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

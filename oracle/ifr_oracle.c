@@ -72,12 +72,12 @@ uint32_t or_stream_block_checksum(const uint32_t *buf, int64_t n_elems, int64_t 
 
 /* ------------------------------------------------------------------------- */
 /* FP32 FMA stressor (the paper's compute kernel, Sec. 3 and Sec. 4.4.2: many  */
-/* independent fp32 chains, ILP = chains per thread).  Thread t of active      */
-/* block k runs chains j < ilp; g = (k*block + t)*ilp + j draws three outputs  */
-/* of SplitMix64(seed<<32) at 3g, 3g+1, 3g+2:                                 */
-/*   x0 = ((u0>>40) - 2^23) * 2^-23                                           */
-/*   a  = 1 - 2^-12 - (u1>>53) * 2^-23          (exact in fp32, |a| < 1)       */
-/*   b  = ((u2>>40) - 2^23) * 2^-23 * 2^-6                                     */
+/* independent fp32 chains, ILP = chains per thread).  One multiplier and one  */
+/* addend per launch, from outputs 0 and 1 of SplitMix64(seed<<32):            */
+/*   a = 1 - 2^-12 - (u0>>53) * 2^-23          (exact in fp32, |a| < 1)        */
+/*   b = ((u1>>40) - 2^23) * 2^-29                                             */
+/* Chain j of thread t of active block k, g = (k*block + t)*ilp + j, starts at */
+/*   x0 = ((u(g+2)>>40) - 2^23) * 2^-23                                        */
 /* and iterates x <- fma(x, a, b) (one rounding), `steps` times per round.     */
 /* round0_xor: XOR of the bits of every chain after round 0;                   */
 /* final_xor: the same after `rounds` rounds.                                  */
@@ -85,16 +85,13 @@ uint32_t or_stream_block_checksum(const uint32_t *buf, int64_t n_elems, int64_t 
 void or_fma_block(uint64_t seed, int64_t k, int block, int ilp, int steps, int64_t rounds,
                   uint32_t *round0_xor, uint32_t *final_xor) {
     uint64_t s0 = seed << 32;
+    float a = (float)(1.0 - ldexp(1.0, -12) - (double)(or_splitmix64(s0, 0) >> 53) * ldexp(1.0, -23));
+    float b = (float)((double)((int64_t)(or_splitmix64(s0, 1) >> 40) - (1 << 23)) * ldexp(1.0, -29));
     uint32_t r0 = 0u, fin = 0u;
     for (int t = 0; t < block; ++t) {
         for (int j = 0; j < ilp; ++j) {
             uint64_t g = ((uint64_t)k * (uint64_t)block + (uint64_t)t) * (uint64_t)ilp + (uint64_t)j;
-            uint64_t u0 = or_splitmix64(s0, 3u * g);
-            uint64_t u1 = or_splitmix64(s0, 3u * g + 1u);
-            uint64_t u2 = or_splitmix64(s0, 3u * g + 2u);
-            float x = (float)((double)((int64_t)(u0 >> 40) - (1 << 23)) * ldexp(1.0, -23));
-            float a = (float)(1.0 - ldexp(1.0, -12) - (double)(u1 >> 53) * ldexp(1.0, -23));
-            float b = (float)((double)((int64_t)(u2 >> 40) - (1 << 23)) * ldexp(1.0, -29));
+            float x = (float)((double)((int64_t)(or_splitmix64(s0, g + 2u) >> 40) - (1 << 23)) * ldexp(1.0, -23));
             for (int64_t r = 0; r < rounds; ++r) {
                 for (int s = 0; s < steps; ++s) x = fmaf(x, a, b);
                 if (r == 0) r0 ^= f32_bits(x);

@@ -22,7 +22,11 @@
 
 namespace {
 
-constexpr int BM = 128, BK = 64, STAGES = 4;
+// Three stages (147 KiB of shared memory at BN = 256) leave room on the SM for a
+// stressor block (the tensor stressor needs 34 KiB, the shared-memory stressor
+// 2 x 33 KiB): a colocation-friendly configuration in the sense of Sec. 5.3.
+// Four stages (195 KiB) would make the GEMM and those stressors mutually exclusive.
+constexpr int BM = 128, BK = 64, STAGES = 3;
 constexpr uint64_t kGemmTimeoutNs = 1000000000ull;
 
 template <int BN>

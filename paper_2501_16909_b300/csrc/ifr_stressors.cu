@@ -29,6 +29,14 @@ constexpr int kSmemPasses = 8;            // SMEM: passes over the warp array pe
 constexpr int kSchedLcgSteps = 16;        // SCHED: LCG steps per block result
 constexpr uint32_t kMaxSpin = 1u << 22;   // iteration cap of every sleep loop
 
+// SplitMix64 (Steele, Lea, Flood 2014) on the host: output i of the stream at s0.
+uint64_t host_splitmix64(uint64_t s0, uint64_t i) {
+    uint64_t z = s0 + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
 struct BlockCtl {
     int k;            // active index, -1 = not active
     uint64_t t0;      // entry time
@@ -219,16 +227,15 @@ __global__ void __launch_bounds__(1024) fma_stress_kernel(DevStress *st, StressP
     BlockCtl c;
     if (!block_enter(st, p, c, &s_k, &s_t0)) return;
     const uint64_t s0 = p.seed << 32;
-    float x[ILP], a[ILP], b[ILP];
+    // the multiplier and addend are launch-wide kernel parameters, so each FFMA
+    // reads a single register operand (x) and never stalls on register banks
+    const float a = p.fma_a, b = p.fma_b;
+    float x[ILP];
 #pragma unroll
     for (int j = 0; j < ILP; ++j) {
         const uint64_t g = ((uint64_t)c.k * blockDim.x + threadIdx.x) * ILP + j;
-        const uint64_t u0 = ifr_splitmix64(s0, 3ull * g);
-        const uint64_t u1 = ifr_splitmix64(s0, 3ull * g + 1ull);
-        const uint64_t u2 = ifr_splitmix64(s0, 3ull * g + 2ull);
+        const uint64_t u0 = ifr_splitmix64(s0, g + 2ull);
         x[j] = (float)((int)(u0 >> 40) - (1 << 23)) * 0x1p-23f;
-        a[j] = (1.0f - 0x1p-12f) - (float)(uint32_t)(u1 >> 53) * 0x1p-23f;
-        b[j] = (float)((int)(u2 >> 40) - (1 << 23)) * 0x1p-29f;
     }
     uint32_t r0 = 0u;
     int64_t round = 0;
@@ -239,7 +246,7 @@ __global__ void __launch_bounds__(1024) fma_stress_kernel(DevStress *st, StressP
 #pragma unroll 16
         for (int s = 0; s < kFmaSteps; ++s) {
 #pragma unroll
-            for (int j = 0; j < ILP; ++j) x[j] = __fmaf_rn(x[j], a[j], b[j]);
+            for (int j = 0; j < ILP; ++j) x[j] = __fmaf_rn(x[j], a, b);
         }
         if (round == 0) {
 #pragma unroll
@@ -549,6 +556,13 @@ int ifr_stressor_enqueue(ifr_ctx *ctx, const ifr_stressor_cfg *cfg, cudaStream_t
     p.duty = cfg->duty;
     p.period_ns = cfg->period_ns > 0 ? (uint32_t)cfg->period_ns : 100000u;
     p.ilp = cfg->ilp ? cfg->ilp : 4;
+    {
+        // FMA constants: a = 1 - 2^-12 - (u0 >> 53) 2^-23, b = ((u1 >> 40) - 2^23) 2^-29
+        // from outputs 0 and 1 of SplitMix64(seed << 32) (exact in fp32, |a| < 1)
+        const uint64_t u0 = host_splitmix64(p.seed << 32, 0), u1 = host_splitmix64(p.seed << 32, 1);
+        p.fma_a = (float)(1.0 - 0x1p-12 - (double)(u0 >> 53) * 0x1p-23);
+        p.fma_b = (float)((double)((int64_t)(u1 >> 40) - (1 << 23)) * 0x1p-29);
+    }
     p.logs = s.d_logs;
     if (s.watch) {
         p.progress = ctx->d_progress;

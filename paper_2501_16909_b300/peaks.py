@@ -1,0 +1,108 @@
+"""Work accounting and peak rates of the stressors' resources.
+
+Each stressor run reports `work` in its kind's unit (chunks, FMA steps per
+chain, shared-memory ld/st pairs per lane, tile MMAs, busy blocks); this module
+turns that into the algorithmic quantity its resource's peak is stated in, and
+provides the peaks:
+
+* HBM        bytes/s — MEASURED_PEAKS.json `hbm_gbs` (STREAM-style copy)
+* L2         bytes/s — probe: the stream kernel over a 24 MiB set, every SM, 4 blocks each
+* FP32 FMA   flop/s  — SMs x 128 lanes x 2 flop x max SM clock
+* tensor     flop/s  — MEASURED_PEAKS.json `bf16_tflops` (cuBLAS bf16 burst)
+* shared mem wavefronts/s — SMs x 1 wavefront per clock x max SM clock
+* scheduler  blocks/s — probe: zero-cycle 32-thread blocks on every SM
+"""
+from __future__ import annotations
+
+import json
+import os
+
+from . import _abi as A
+from . import stressor_cfg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+TILE_MMA_FLOP = 2 * 128 * 128 * 64
+FMA_STEPS = 4096
+UNIT = {A.IFR_S_HBM: "B", A.IFR_S_L2: "B", A.IFR_S_FMA: "flop", A.IFR_S_TENSOR: "flop", A.IFR_S_SMEM_CF: "wavefront",
+        A.IFR_S_SMEM_32W: "wavefront", A.IFR_S_SCHED: "block"}
+# fixed-work rounds of one calibration run per kind (about a millisecond at full SMs)
+CAL_ROUNDS = {A.IFR_S_HBM: 64, A.IFR_S_L2: 256, A.IFR_S_FMA: 32, A.IFR_S_TENSOR: 32, A.IFR_S_SMEM_CF: 64,
+              A.IFR_S_SMEM_32W: 4, A.IFR_S_SCHED: 0}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+def ways_of(cfg):
+    if cfg.smem_ways:
+        return cfg.smem_ways
+    return 1 if cfg.kind == A.IFR_S_SMEM_CF else 32
+
+
+def work_units(cfg, res):
+    """Algorithmic work of one stressor run, in UNIT[kind]."""
+    k = cfg.kind
+    block = cfg.block or {A.IFR_S_L2: 512, A.IFR_S_HBM: 512, A.IFR_S_FMA: 128, A.IFR_S_SMEM_CF: 256,
+                          A.IFR_S_SMEM_32W: 256}.get(k, 128)
+    w = res["work"]
+    if k in (A.IFR_S_HBM, A.IFR_S_L2):
+        return w * block * 64
+    if k == A.IFR_S_FMA:
+        return w * block * (cfg.ilp or 4) * 2
+    if k == A.IFR_S_TENSOR:
+        return w * TILE_MMA_FLOP
+    if k in (A.IFR_S_SMEM_CF, A.IFR_S_SMEM_32W):
+        return w * (block // 32) * 2 * ways_of(cfg)
+    if k == A.IFR_S_SCHED:
+        return w
+    raise ValueError(k)
+
+
+def copy_cfg(cfg, **over):
+    c = stressor_cfg(cfg.kind)
+    for name, _ in cfg._fields_:
+        setattr(c, name, getattr(cfg, name))
+    for k, v in over.items():
+        setattr(c, k, v)
+    return c
+
+
+def solo_rate(ctx, cfg, rounds=None, launches=8):
+    """Run a fixed-work copy of cfg alone; returns (rate in UNIT/s, result)."""
+    over = {}
+    if cfg.kind == A.IFR_S_SCHED:
+        over["sched_launches"] = launches
+    else:
+        over["max_rounds"] = rounds or CAL_ROUNDS[cfg.kind]
+    res, _ = ctx.run_stressor(copy_cfg(cfg, **over), 30000)
+    ms = res["elapsed_ms"]
+    return (work_units(cfg, res) / (ms * 1e-3) if ms > 0 else 0.0), res
+
+
+def peaks(ctx, l2_buf=None):
+    """Peak rate per stressor kind (UNIT/s) and where it comes from."""
+    m, src = measured_peaks()
+    S = ctx.info["num_sms"]
+    clk = ctx.info["sm_clock_khz"] * 1e3
+    out = {
+        A.IFR_S_HBM: (m["hbm_gbs"] * 1e9, "MEASURED_PEAKS hbm_gbs (%s)" % src),
+        A.IFR_S_TENSOR: (m["bf16_tflops"] * 1e12, "MEASURED_PEAKS bf16_tflops (%s)" % src),
+        A.IFR_S_FMA: (S * 128 * 2 * clk, "nominal: SMs x 128 FP32 lanes x 2 flop x max SM clock"),
+        A.IFR_S_SMEM_CF: (S * clk, "nominal: SMs x 1 shared-memory wavefront per clock x max SM clock"),
+        A.IFR_S_SMEM_32W: (S * clk, "nominal: SMs x 1 shared-memory wavefront per clock x max SM clock"),
+    }
+    if l2_buf is not None:
+        nb = min(l2_buf.numel() * 4, 24 << 20)
+        nb -= nb % (512 * 64)
+        cfg = stressor_cfg(A.IFR_S_L2, sm_count=S, blocks_per_sm=4, block=512, buf=l2_buf, working_set_bytes=nb)
+        rate, _ = solo_rate(ctx, cfg, rounds=256)
+        out[A.IFR_S_L2] = (rate, "probe: stream kernel, 24 MiB L2-resident set, %d SMs x 4 blocks" % S)
+    cfg = stressor_cfg(A.IFR_S_SCHED, sm_count=S, sched_blocks=100000, sched_cycles=1)
+    rate, _ = solo_rate(ctx, cfg, launches=8)
+    out[A.IFR_S_SCHED] = (rate, "probe: 1-cycle 32-thread blocks on every SM")
+    return out

@@ -1,0 +1,79 @@
+"""Run one stressor or victim alone, for profilers.
+
+Profilers that replay kernels serialise them, so they cannot observe colocated
+kernels (the paper makes the same point about NCU in Sec. 5.2).  This driver runs
+one kernel kind in isolation on a small case so that a profiler can capture it:
+
+    python -m paper_2501_16909_b300.profile_case <case> [--repeat N]
+
+cases: hbm, l2, fma, tensor, smem_cf, smem_32w, sched, gemm, gemv, layernorm,
+softmax, hist, triad.  Inputs are the workloads' seeded inputs at the sizes
+given below (the stream stressors use a 1 GiB / 48 MiB set; the victims use their
+full configuration-2 shapes).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main(argv=None):
+    import torch
+
+    import ifr_inputs as I
+    import paper_2501_16909_b300 as ifr
+    from paper_2501_16909_b300 import _abi as A
+    from paper_2501_16909_b300 import peaks as P
+    from paper_2501_16909_b300 import workloads as W
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case")
+    ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--sm-fraction", type=float, default=1.0)
+    a = ap.parse_args(argv)
+    ctx = ifr.Context(0)
+    S = ctx.info["num_sms"]
+    n_sm = max(1, round(a.sm_fraction * S))
+    out = {"case": a.case, "sm_count": n_sm}
+    stressors = {"hbm": A.IFR_S_HBM, "l2": A.IFR_S_L2, "fma": A.IFR_S_FMA, "tensor": A.IFR_S_TENSOR,
+                 "smem_cf": A.IFR_S_SMEM_CF, "smem_32w": A.IFR_S_SMEM_32W, "sched": A.IFR_S_SCHED}
+    if a.case in stressors:
+        kind = stressors[a.case]
+        bufs = {}
+        if kind == A.IFR_S_HBM:
+            bufs["hbm"] = I.torch_u32_as_i32(1, (1 << 30) // 4, "cuda")
+        if kind == A.IFR_S_L2:
+            bufs["l2"] = I.torch_u32_as_i32(3, (48 << 20) // 4, "cuda")
+        cfg = W.stressor_level_cfg(kind, n_sm, bufs, seed=1)
+        for _ in range(a.repeat):
+            rate, res = P.solo_rate(ctx, cfg)
+        out.update(rate=rate, unit=P.UNIT[kind] + "/s", elapsed_ms=res["elapsed_ms"], work=res["work"],
+                   status=res["status"])
+    else:
+        victims, kinds, _t = W.config2_victims("cuda")
+        names = {A.IFR_V_GEMM: "gemm", A.IFR_V_GEMV: "gemv", A.IFR_V_LAYERNORM: "layernorm",
+                 A.IFR_V_SOFTMAX: "softmax", A.IFR_V_HIST: "hist"}
+        pick = [v for v, k in zip(victims, kinds) if names[k] == a.case]
+        if a.case == "triad":
+            wl = W.config1(S)
+            pick = wl.victims
+        if not pick:
+            raise SystemExit("unknown case %r" % a.case)
+        v = pick[0]
+        v.repeats = 1
+        for _ in range(a.repeat):
+            t = ctx.victim_launch(v)
+        out.update(event_ms=t["event_ms"], status=t["status"])
+    torch.cuda.synchronize()
+    ctx.close()
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

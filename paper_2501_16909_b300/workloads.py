@@ -60,3 +60,88 @@ def config1(num_sms: int, device="cuda", hbm_bytes: int = GiB, n: int = 1 << 22,
     return Workload("config1: triad N=2^22 x HBM stream 1 GiB at 0/25/50/100% SMs", victims, lv, fr,
                     [A.IFR_S_HBM], [A.IFR_V_TRIAD], dict(a=a, b=b, c=c, buf=buf), repeats,
                     h2d_bytes=b.numel() * 4 + c.numel() * 4 + buf.numel() * 4, d2h_bytes=a.numel() * 4)
+
+
+# ----------------------------------------------------------------------------- config 2
+# Stressor footprints per SM (threads / blocks): kept small so that victim blocks
+# can be co-resident (the paper's stressors use one 128-thread block per SM).
+STRESSOR_DEFAULTS = {
+    A.IFR_S_SCHED: dict(sched_blocks=100000, sched_cycles=100),
+    A.IFR_S_FMA: dict(block=128, blocks_per_sm=2, ilp=8),
+    A.IFR_S_TENSOR: dict(blocks_per_sm=1),
+    A.IFR_S_SMEM_CF: dict(block=256, blocks_per_sm=2),
+    A.IFR_S_SMEM_32W: dict(block=256, blocks_per_sm=2),
+    A.IFR_S_L2: dict(block=512, blocks_per_sm=2),
+    A.IFR_S_HBM: dict(block=512, blocks_per_sm=2),
+}
+
+VICTIM_LAUNCHES = {A.IFR_V_GEMM: 4, A.IFR_V_GEMV: 16, A.IFR_V_LAYERNORM: 4, A.IFR_V_SOFTMAX: 4, A.IFR_V_HIST: 8,
+                   A.IFR_V_TRIAD: 8}
+
+
+def config2_victims(device="cuda"):
+    """BF16 GEMM 4096^3 (N(0,1)), BF16 GEMV 8192^2, FP32 layernorm 16384x4096,
+    FP32 row softmax 8192^2, int32 histogram of 2^26 keys (seeds 11..16)."""
+    t = {}
+    G = 4096
+    t["gA"] = I.torch_normal_bf16(11, G * G, device).view(G, G)
+    t["gB"] = I.torch_normal_bf16(12, G * G, device).view(G, G)
+    t["gC"] = torch.empty(G, G, device=device)
+    R = 8192
+    t["vA"] = I.torch_normal_bf16(13, R * R, device).view(R, R)
+    t["vx"] = I.torch_normal_bf16(14, R, device)
+    t["vy"] = torch.empty(R, device=device)
+    t["lx"] = I.torch_uniform_pm1(15, 16384 * 4096, device).view(16384, 4096)
+    t["ly"] = torch.empty_like(t["lx"])
+    t["sx"] = I.torch_uniform_pm1(16, R * R, device).view(R, R)
+    t["sy"] = torch.empty_like(t["sx"])
+    t["hk"] = I.torch_key256(2, 1 << 26, device)
+    t["hb"] = torch.zeros(256, dtype=torch.int32, device=device)
+    L = VICTIM_LAUNCHES
+    victims = [
+        victim_cfg(A.IFR_V_GEMM, t["gA"], t["gB"], t["gC"], m=G, n=G, k=G, repeats=L[A.IFR_V_GEMM]),
+        victim_cfg(A.IFR_V_GEMV, t["vA"], t["vx"], t["vy"], m=R, k=R, repeats=L[A.IFR_V_GEMV]),
+        victim_cfg(A.IFR_V_LAYERNORM, t["lx"], None, t["ly"], m=16384, n=4096, repeats=L[A.IFR_V_LAYERNORM]),
+        victim_cfg(A.IFR_V_SOFTMAX, t["sx"], None, t["sy"], m=R, n=R, repeats=L[A.IFR_V_SOFTMAX]),
+        victim_cfg(A.IFR_V_HIST, t["hk"], None, t["hb"], n=1 << 26, repeats=L[A.IFR_V_HIST]),
+    ]
+    kinds = [A.IFR_V_GEMM, A.IFR_V_GEMV, A.IFR_V_LAYERNORM, A.IFR_V_SOFTMAX, A.IFR_V_HIST]
+    return victims, kinds, t
+
+
+def stressor_level_cfg(kind, sm_count, bufs, seed=0, **over):
+    kw = dict(STRESSOR_DEFAULTS[kind])
+    kw.update(over)
+    if kind == A.IFR_S_L2:
+        kw.update(buf=bufs["l2"], working_set_bytes=bufs["l2"].numel() * 4)
+    elif kind == A.IFR_S_HBM:
+        kw.update(buf=bufs["hbm"], working_set_bytes=bufs["hbm"].numel() * 4)
+    return stressor_cfg(kind, sm_count=sm_count, seed=seed, **kw)
+
+
+def config2(num_sms: int, device="cuda", n_levels: int = 8, repeats: int = 3, hbm_bytes: int = 4 * GiB,
+            l2_bytes: int = 48 * MiB) -> Workload:
+    victims, vkinds, t = config2_victims(device)
+    t["l2"] = I.torch_u32_as_i32(3, l2_bytes // 4, device)
+    t["hbm"] = I.torch_u32_as_i32(1, hbm_bytes // 4, device)
+    kinds = [A.IFR_S_SCHED, A.IFR_S_FMA, A.IFR_S_TENSOR, A.IFR_S_SMEM_CF, A.IFR_S_SMEM_32W, A.IFR_S_L2, A.IFR_S_HBM]
+    fr = [(l + 1) / n_levels for l in range(n_levels)]
+    levels = [[stressor_level_cfg(k, max(1, round(f * num_sms)), t, seed=r + 1) for f in fr]
+              for r, k in enumerate(kinds)]
+    h2d = sum(v.numel() * v.element_size() for k, v in t.items() if k in ("gA", "gB", "vA", "vx", "lx", "sx", "hk",
+                                                                          "l2", "hbm"))
+    d2h = sum(t[k].numel() * t[k].element_size() for k in ("gC", "vy", "ly", "sy", "hb"))
+    return Workload("config2: 7 stressors x 8 SM-fraction levels x 5 victims (GEMM 4096^3, GEMV 8192^2, "
+                    "LN 16384x4096, softmax 8192^2, histogram 2^26)", victims, levels, fr, kinds, vkinds, t,
+                    repeats, h2d_bytes=h2d, d2h_bytes=d2h)
+
+
+def size_sched_launches(wl: Workload, solo_window_ns: float, t_launch_ns: float, margin: float = 4.0,
+                        cap: int = 4096):
+    """Enough scheduler-stressor launches to cover `margin` x the victim window."""
+    n = int(min(cap, max(4, margin * solo_window_ns / max(t_launch_ns, 1.0) + 2)))
+    for r, row in enumerate(wl.levels):
+        for cfg in row:
+            if cfg.kind == A.IFR_S_SCHED:
+                cfg.sched_launches = n
+    return n

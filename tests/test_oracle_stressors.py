@@ -73,14 +73,13 @@ def _f32_bits(v: float) -> int:
 
 def _fma_brute(seed, k, block, ilp, steps, rounds):
     s0 = I.state0(seed)
+    a = 1 - Fraction(1, 2**12) - Fraction(I.splitmix64_at(s0, 0) >> 53, 2**23)
+    b = Fraction((I.splitmix64_at(s0, 1) >> 40) - 2**23, 2**29)
     r0 = fin = 0
     for t in range(block):
         for j in range(ilp):
             g = (k * block + t) * ilp + j
-            u0, u1, u2 = (I.splitmix64_at(s0, 3 * g + q) for q in range(3))
-            x = Fraction((u0 >> 40) - 2**23, 2**23)
-            a = 1 - Fraction(1, 2**12) - Fraction(u1 >> 53, 2**23)
-            b = Fraction((u2 >> 40) - 2**23, 2**29)
+            x = Fraction((I.splitmix64_at(s0, g + 2) >> 40) - 2**23, 2**23)
             for r in range(rounds):
                 for _ in range(steps):
                     x = Fraction(_round_f32(x * a + b))
@@ -101,10 +100,8 @@ def test_fma_rounds_compose_and_fixed_point():
     # with |a| < 1 the chain converges towards b / (1 - a); fp32 rounding stalls it
     # within about ulp(x*) / (1 - a) of the fixed point
     s0 = I.state0(8)
-    u1 = I.splitmix64_at(s0, 1)
-    u2 = I.splitmix64_at(s0, 2)
-    a = 1 - 2.0**-12 - (u1 >> 53) * 2.0**-23
-    b = ((u2 >> 40) - 2**23) * 2.0**-29
+    a = 1 - 2.0**-12 - (I.splitmix64_at(s0, 0) >> 53) * 2.0**-23
+    b = ((I.splitmix64_at(s0, 1) >> 40) - 2**23) * 2.0**-29
     _, fin = oracle.fma_block(8, 0, 1, 1, 200000, 1)
     x = np.array([fin], np.uint32).view(np.float32)[0]
     xs = b / (1 - a)
