@@ -109,34 +109,14 @@ def calibrate(ctx, wl, pk):
 
 
 def prepare_levels(ctx, wl, pk):
-    """Size the scheduler stressor's launch count and every deadline from solo victim
-    windows: separate level tables for the plain (one victim per stressor run) and
-    the batched (all victims under one stressor run) sweeps."""
-    from paper_2501_16909_b300 import _abi as A
-    from paper_2501_16909_b300 import peaks as P
+    """Scheduler launch counts and deadlines sized from solo victim windows: separate
+    level tables for the plain (one victim per stressor run) and the batched (all
+    victims under one stressor run) sweeps."""
+    from paper_2501_16909_b300 import plan
 
-    windows = []
-    for v in wl.victims:
-        t = ctx.victim_launch(v)
-        windows.append(t["t_end_ns"] - t["t_start_ns"])
-    sched_rows = [r for r, row in enumerate(wl.levels) if row[0].kind == A.IFR_S_SCHED]
-    t_launch = 1e5
-    if sched_rows:
-        rate, res = P.solo_rate(ctx, wl.levels[sched_rows[0]][-1], launches=8)
-        t_launch = res["elapsed_ms"] * 1e6 / 8
-    plain, batched = [], []
-    for row in wl.levels:
-        prow, brow = [], []
-        for cfg in row:
-            p = P.copy_cfg(cfg, deadline_ns=int(2e9))
-            b = P.copy_cfg(cfg, deadline_ns=int(max(2e9, 20 * sum(windows))))
-            if cfg.kind == A.IFR_S_SCHED:
-                p.sched_launches = int(min(4096, 4 * max(windows) / t_launch + 4))
-                b.sched_launches = int(min(65536, 4 * sum(windows) / t_launch + 4))
-            prow.append(p)
-            brow.append(b)
-        plain.append(prow)
-        batched.append(brow)
+    windows = plan.solo_windows(ctx, wl.victims)
+    t_launch = plan.sched_launch_ns(ctx, wl.levels)
+    plain, batched = plan.mode_levels(wl.levels, windows, t_launch)
     return plain, batched, windows, t_launch
 
 

@@ -24,8 +24,10 @@
 namespace {
 
 constexpr int kStreamChunksPerRound = 4;  // L2/HBM: chunks per round
-constexpr int kFmaSteps = 4096;           // FMA: steps per chain per round
-constexpr int kSmemPasses = 8;            // SMEM: passes over the warp array per round
+// FMA: steps per chain per round = kFmaWork / ILP (16384 FMAs per thread per round)
+constexpr int kFmaWork = 16384;
+// SMEM: passes over the warp array per round = max(1, 8 / WAYS)
+constexpr int kSmemPassesCF = 8;
 constexpr int kSchedLcgSteps = 16;        // SCHED: LCG steps per block result
 constexpr uint32_t kMaxSpin = 1u << 22;   // iteration cap of every sleep loop
 
@@ -244,7 +246,7 @@ __global__ void __launch_bounds__(1024) fma_stress_kernel(DevStress *st, StressP
         __syncthreads();
         if (!s_go[round & 1]) break;
 #pragma unroll 16
-        for (int s = 0; s < kFmaSteps; ++s) {
+        for (int s = 0; s < kFmaWork / ILP; ++s) {
 #pragma unroll
             for (int j = 0; j < ILP; ++j) x[j] = __fmaf_rn(x[j], a, b);
         }
@@ -258,7 +260,7 @@ __global__ void __launch_bounds__(1024) fma_stress_kernel(DevStress *st, StressP
     for (int j = 0; j < ILP; ++j) fin ^= __float_as_uint(x[j]);
     uint32_t cs = ifr_block_xor(r0, s_red);
     uint32_t cs2 = ifr_block_xor(fin, s_red);
-    if (threadIdx.x == 0) write_log(p, st, c, round, (uint64_t)round * kFmaSteps, cs, cs2);
+    if (threadIdx.x == 0) write_log(p, st, c, round, (uint64_t)round * (kFmaWork / ILP), cs, cs2);
 }
 
 // ------------------------------------------------------------------ shared memory
@@ -293,7 +295,7 @@ __global__ void __launch_bounds__(1024) smem_stress_kernel(DevStress *st, Stress
         __syncthreads();
         if (!s_go[round & 1]) break;
 #pragma unroll 1
-        for (int pass = 0; pass < kSmemPasses; ++pass) {
+        for (int pass = 0; pass < (WAYS >= kSmemPassesCF ? 1 : kSmemPassesCF / WAYS); ++pass) {
 #pragma unroll
             for (int jb = 0; jb < 32; jb += 8) {
                 uint32_t v[8];
@@ -308,7 +310,8 @@ __global__ void __launch_bounds__(1024) smem_stress_kernel(DevStress *st, Stress
     uint32_t acc = 0u;
     for (int q = lane; q < 1024; q += 32) acc ^= arr[q];
     uint32_t cs = ifr_block_xor(acc, s_red);
-    if (threadIdx.x == 0) write_log(p, st, c, round, (uint64_t)round * kSmemPasses * 32, cs, 0u);
+    if (threadIdx.x == 0)
+        write_log(p, st, c, round, (uint64_t)round * (WAYS >= kSmemPassesCF ? 1 : kSmemPassesCF / WAYS) * 32, cs, 0u);
 }
 
 // ------------------------------------------------------------------ BF16 tensor pipe

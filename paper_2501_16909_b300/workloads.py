@@ -10,8 +10,10 @@ on zero SMs) is added by the sweep itself.  Input generation uses ifr_inputs
 """
 from __future__ import annotations
 
+import math
 from dataclasses import dataclass, field
 
+import numpy as np
 import torch
 
 import ifr_inputs as I
@@ -134,6 +136,73 @@ def config2(num_sms: int, device="cuda", n_levels: int = 8, repeats: int = 3, hb
     return Workload("config2: 7 stressors x 8 SM-fraction levels x 5 victims (GEMM 4096^3, GEMV 8192^2, "
                     "LN 16384x4096, softmax 8192^2, histogram 2^26)", victims, levels, fr, kinds, vkinds, t,
                     repeats, h2d_bytes=h2d, d2h_bytes=d2h)
+
+
+# ----------------------------------------------------------------------------- config 3
+def _loguniform(u64: int, lo: int, hi: int, mult: int) -> int:
+    """Log-uniform draw in [lo, hi] from one generator output, rounded to a multiple of mult."""
+    u01 = (int(u64) >> 11) * 2.0 ** -53
+    v = math.exp(math.log(lo) + u01 * (math.log(hi) - math.log(lo)))
+    r = mult * int(round(v / mult))
+    return int(min(hi - hi % mult, max(lo, r)))
+
+
+def config3_shapes(seed: int = 3):
+    """64 uneven victims: 16 GEMMs (M, N, K log-uniform in [256, 8192], multiples of
+    128), 16 GEMVs (rows log-uniform in [1024, 16384], width 4096), 16 softmax and 16
+    layernorm (rows log-uniform in [512, 32768], width 4096).  Draw i of the seed's
+    SplitMix64 stream feeds the i-th dimension in that order."""
+    u = I.np_u64(seed, np.arange(96))
+    shapes = []
+    for g in range(16):
+        M, N, K = (_loguniform(u[3 * g + j], 256, 8192, 128) for j in range(3))
+        shapes.append(("gemm", M, N, K))
+    for g in range(16):
+        shapes.append(("gemv", _loguniform(u[48 + g], 1024, 16384, 1), 0, 4096))
+    for g in range(16):
+        shapes.append(("softmax", _loguniform(u[64 + g], 512, 32768, 1), 4096, 0))
+    for g in range(16):
+        shapes.append(("layernorm", _loguniform(u[80 + g], 512, 32768, 1), 4096, 0))
+    return shapes
+
+
+def config3_victims(device="cuda", seed: int = 3, launches: int = 1):
+    """Allocate and fill the 64 config-3 victims (inputs seeded per victim index)."""
+    t, victims, kinds = {}, [], []
+    for i, (kind, a, b, c) in enumerate(config3_shapes(seed)):
+        s = 100 + 4 * i
+        if kind == "gemm":
+            M, N, K = a, b, c
+            A_ = I.torch_normal_bf16(s, M * K, device).view(M, K)
+            B_ = I.torch_normal_bf16(s + 1, N * K, device).view(N, K)
+            C_ = torch.empty(M, N, device=device)
+            t[i] = (A_, B_, C_)
+            victims.append(victim_cfg(A.IFR_V_GEMM, A_, B_, C_, m=M, n=N, k=K, repeats=launches))
+            kinds.append(A.IFR_V_GEMM)
+        elif kind == "gemv":
+            R, W = a, c
+            A_ = I.torch_normal_bf16(s, R * W, device).view(R, W)
+            x = I.torch_normal_bf16(s + 1, W, device)
+            y = torch.empty(R, device=device)
+            t[i] = (A_, x, y)
+            victims.append(victim_cfg(A.IFR_V_GEMV, A_, x, y, m=R, k=W, repeats=launches))
+            kinds.append(A.IFR_V_GEMV)
+        else:
+            R, W = a, b
+            x = I.torch_uniform_pm1(s, R * W, device).view(R, W)
+            y = torch.empty_like(x)
+            t[i] = (x, y)
+            k = A.IFR_V_SOFTMAX if kind == "softmax" else A.IFR_V_LAYERNORM
+            victims.append(victim_cfg(k, x, None, y, m=R, n=W, repeats=launches))
+            kinds.append(k)
+    return victims, kinds, t
+
+
+def config3_base_stressors(num_sms: int, bufs, kinds=None):
+    """Full-intensity configuration of every stressor kind (the autotuner's start)."""
+    kinds = kinds or [A.IFR_S_SCHED, A.IFR_S_FMA, A.IFR_S_TENSOR, A.IFR_S_SMEM_CF, A.IFR_S_SMEM_32W, A.IFR_S_L2,
+                      A.IFR_S_HBM]
+    return [stressor_level_cfg(k, num_sms, bufs, seed=r + 1) for r, k in enumerate(kinds)]
 
 
 def size_sched_launches(wl: Workload, solo_window_ns: float, t_launch_ns: float, margin: float = 4.0,
