@@ -243,6 +243,72 @@ typedef struct {
  * misaligned pointer), IFR_ERR_LAUNCH, IFR_ERR_CUDA. */
 int ifr_victim_launch(ifr_ctx *ctx, const ifr_victim_cfg *cfg, void *stream, ifr_timing *out);
 
+/* ---- solo kernel profiles (Sec. 2.2 metrics; Sec. 5.1 estimator inputs) -- */
+/* Static launch properties of the kernel a victim or stressor configuration
+ * would run, the inputs of the SM-utilisation and occupancy metrics of Sec. 2.2
+ * (threads, registers and shared memory per block decide how many blocks fit on an
+ * SM, Sec. 2.1).  No GPU work is done. */
+typedef struct {
+    int32_t grid, block;           /* blocks per launch and threads per block */
+    int32_t regs_per_thread;       /* registers per thread (cudaFuncGetAttributes) */
+    int32_t static_smem;           /* bytes of static shared memory per block */
+    int32_t dynamic_smem;          /* bytes of dynamic shared memory per block */
+    int32_t max_blocks_per_sm;     /* occupancy limit of this launch shape */
+    int32_t tmem_cols;             /* tensor-memory columns per block */
+    int32_t uses_tensor;           /* 1 for tcgen05 kernels */
+    int32_t sm_count;              /* stressors: SMs allowed; victims: 0 (all) */
+    int32_t blocks_per_sm;         /* stressors: working blocks per allowed SM; victims: 0 */
+    int32_t launches;              /* launches per measurement (victims: K; scheduler: chain) */
+    int32_t reserved;
+    double bytes_per_launch;       /* victims: algorithmic bytes of one launch (stressors: 0) */
+    double flops_per_launch;       /* victims: algorithmic flops of one launch (stressors: 0) */
+} ifr_kernel_profile;
+
+/* Errors: IFR_ERR_ARG (invalid configuration, as in the launch calls), IFR_ERR_CUDA. */
+int ifr_victim_profile(ifr_ctx *ctx, const ifr_victim_cfg *cfg, ifr_kernel_profile *out);
+int ifr_stressor_profile(ifr_ctx *ctx, const ifr_stressor_cfg *cfg, ifr_kernel_profile *out);
+
+/* ---- slowdown predictor (Sec. 5.1 kernel-level interference estimator) --- */
+/* A multilayer perceptron on the solo profiles of a victim and a co-runner that
+ * predicts the victim's log slowdown.  Layer l computes Z_l = H_l W_l^T + b_l
+ * (bf16 operands, fp32 accumulation) and, for hidden layers, H_{l+1} =
+ * bf16(GELU(Z_l)) with the exact erf GELU; the last layer has one output.
+ * All buffers are caller-owned device memory, row-major; nothing is allocated. */
+#define IFR_MLP_MAX_LAYERS 8
+typedef struct {
+    int32_t n_layers;                     /* 1..IFR_MLP_MAX_LAYERS */
+    int32_t batch;                        /* rows B */
+    int32_t dims[IFR_MLP_MAX_LAYERS + 1]; /* dims[0] inputs ... dims[n_layers] = 1 */
+    const void *W[IFR_MLP_MAX_LAYERS];    /* bf16 [dims[l+1]][dims[l]] */
+    const float *b[IFR_MLP_MAX_LAYERS];   /* fp32 [dims[l+1]] */
+    void *H[IFR_MLP_MAX_LAYERS];          /* bf16 [B][dims[l]]; H[0] is the input X */
+    float *Z[IFR_MLP_MAX_LAYERS];         /* fp32 [B][dims[l+1]] pre-activations (forward output) */
+    float *dW[IFR_MLP_MAX_LAYERS];        /* fp32 [dims[l+1]][dims[l]] (backward output) */
+    float *db[IFR_MLP_MAX_LAYERS];        /* fp32 [dims[l+1]] (backward output) */
+    float *dZ[IFR_MLP_MAX_LAYERS];        /* fp32 [B][dims[l+1]] backward workspace */
+    void *dZh[IFR_MLP_MAX_LAYERS];        /* bf16 [B][dims[l+1]] backward workspace */
+    float *dX;                            /* fp32 [B][dims[0]] input gradient, or NULL */
+} ifr_mlp;
+
+/* Forward pass on `stream` (cudaStream_t; NULL = legacy default).  Writes Z[l]
+ * for every layer and H[l+1] for hidden layers; the prediction is Z[n_layers-1]
+ * ([B][1]).  Errors: IFR_ERR_ARG (shape, null buffer, last dim != 1), IFR_ERR_CUDA. */
+int ifr_mlp_forward(ifr_ctx *ctx, const ifr_mlp *mlp, void *stream);
+/* Backward pass for dY = dLoss/dprediction ([B] fp32): writes dW, db for every
+ * layer and dX when non-NULL.  GEMM operands are bf16 (dZ rounded once), the bias
+ * gradient uses the fp32 dZ.  Needs the Z and H of the matching forward pass. */
+int ifr_mlp_backward(ifr_ctx *ctx, const ifr_mlp *mlp, const float *dY, void *stream);
+/* Mean-squared error of yhat against target (n <= any): dY = 2 (yhat - t) / n and
+ * *loss = mean((yhat - t)^2) (loss may be NULL); device pointers. */
+int ifr_mse_grad(ifr_ctx *ctx, const float *yhat, const float *target, int n, float *dY, float *loss,
+                 void *stream);
+/* One Adam step (Kingma & Ba 2015; eps added after the square root, no weight
+ * decay) over n fp32 parameters w with gradient g and moments m, v (all device);
+ * `step` is 1-based; when w_bf16 is non-NULL the updated weights are also stored
+ * there as bf16. */
+int ifr_adam_step(ifr_ctx *ctx, float *w, const float *g, float *m, float *v, void *w_bf16, int64_t n, float lr,
+                  float beta1, float beta2, float eps, int step, void *stream);
+
 /* ---- sweep (Sec. 4.1 method) -------------------------------------------- */
 typedef struct {
     int32_t n_victims;

@@ -172,6 +172,17 @@ class Context:
             self.stressor_release(h)
         return r, logs
 
+    # -- solo kernel profiles
+    def victim_profile(self, cfg: ifr_victim_cfg) -> dict:
+        p = _abi.ifr_kernel_profile()
+        check(self._L.ifr_victim_profile(self._h, C.byref(cfg), C.byref(p)), "ifr_victim_profile")
+        return _struct_dict(p)
+
+    def stressor_profile(self, cfg: ifr_stressor_cfg) -> dict:
+        p = _abi.ifr_kernel_profile()
+        check(self._L.ifr_stressor_profile(self._h, C.byref(cfg), C.byref(p)), "ifr_stressor_profile")
+        return _struct_dict(p)
+
     # -- victims
     def victim_launch(self, cfg: ifr_victim_cfg, stream=None) -> dict:
         self._sync()

@@ -113,8 +113,30 @@ class ifr_sensitivity_out(C.Structure):
     ]
 
 
+class ifr_kernel_profile(C.Structure):
+    _fields_ = [
+        ("grid", C.c_int32), ("block", C.c_int32), ("regs_per_thread", C.c_int32), ("static_smem", C.c_int32),
+        ("dynamic_smem", C.c_int32), ("max_blocks_per_sm", C.c_int32), ("tmem_cols", C.c_int32),
+        ("uses_tensor", C.c_int32), ("sm_count", C.c_int32), ("blocks_per_sm", C.c_int32), ("launches", C.c_int32),
+        ("reserved", C.c_int32), ("bytes_per_launch", C.c_double), ("flops_per_launch", C.c_double),
+    ]
+
+
+IFR_MLP_MAX_LAYERS = 8
+
+
+class ifr_mlp(C.Structure):
+    _fields_ = [
+        ("n_layers", C.c_int32), ("batch", C.c_int32), ("dims", C.c_int32 * (IFR_MLP_MAX_LAYERS + 1)),
+        ("W", C.c_void_p * IFR_MLP_MAX_LAYERS), ("b", C.c_void_p * IFR_MLP_MAX_LAYERS),
+        ("H", C.c_void_p * IFR_MLP_MAX_LAYERS), ("Z", C.c_void_p * IFR_MLP_MAX_LAYERS),
+        ("dW", C.c_void_p * IFR_MLP_MAX_LAYERS), ("db", C.c_void_p * IFR_MLP_MAX_LAYERS),
+        ("dZ", C.c_void_p * IFR_MLP_MAX_LAYERS), ("dZh", C.c_void_p * IFR_MLP_MAX_LAYERS), ("dX", C.c_void_p),
+    ]
+
+
 STRUCTS = [ifr_device_info, ifr_stressor_cfg, ifr_stressor_result, ifr_block_log, ifr_victim_cfg, ifr_timing,
-           ifr_sweep_plan, ifr_cell_result, ifr_sensitivity_out]
+           ifr_sweep_plan, ifr_cell_result, ifr_sensitivity_out, ifr_kernel_profile, ifr_mlp]
 
 _lib = None
 
@@ -148,6 +170,13 @@ def load():
         "ifr_sweep": (i32, [vp, P(ifr_sweep_plan), P(ifr_cell_result), C.c_size_t, P(C.c_size_t)]),
         "ifr_sensitivity": (i32, [P(ifr_cell_result), C.c_size_t, i32, i32, i32, P(C.c_double),
                                   P(ifr_sensitivity_out)]),
+        "ifr_victim_profile": (i32, [vp, P(ifr_victim_cfg), P(ifr_kernel_profile)]),
+        "ifr_stressor_profile": (i32, [vp, P(ifr_stressor_cfg), P(ifr_kernel_profile)]),
+        "ifr_mlp_forward": (i32, [vp, P(ifr_mlp), vp]),
+        "ifr_mlp_backward": (i32, [vp, P(ifr_mlp), vp, vp]),
+        "ifr_mse_grad": (i32, [vp, vp, vp, i32, vp, vp, vp]),
+        "ifr_adam_step": (i32, [vp, vp, vp, vp, vp, vp, C.c_int64, C.c_float, C.c_float, C.c_float, C.c_float, i32,
+                                vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -207,6 +207,19 @@ int launch_gemm(const ifr_victim_cfg *c, cudaStream_t stream, DevTiming *tm) {
 
 }  // namespace
 
+int ifr_gemm_shape(const ifr_victim_cfg *c, VictimShape *s) {
+    const bool wide = c->n % 256 == 0;
+    s->fn = wide ? (const void *)gemm_bf16_kernel<256> : (const void *)gemm_bf16_kernel<128>;
+    s->grid = (int)((c->n / (wide ? 256 : 128)) * (c->m / BM));
+    s->block = 192;
+    s->smem = wide ? GemmCfg<256>::SMEM : GemmCfg<128>::SMEM;
+    s->tmem_cols = wide ? 256 : 128;
+    s->uses_tensor = 1;
+    s->flops = 2.0 * (double)c->m * (double)c->n * (double)c->k;
+    s->bytes = 2.0 * ((double)c->m + (double)c->n) * (double)c->k + 4.0 * (double)c->m * (double)c->n;
+    return IFR_OK;
+}
+
 int ifr_gemm_enqueue(ifr_ctx *, const ifr_victim_cfg *c, cudaStream_t stream, DevTiming *tm) {
     if (c->m > 65535 * BM || c->n > (1ll << 30) || c->k > (1ll << 30)) return IFR_ERR_ARG;
     if (c->n % 256 == 0) return launch_gemm<256>(c, stream, tm);

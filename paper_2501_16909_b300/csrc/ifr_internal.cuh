@@ -164,5 +164,14 @@ int ifr_timing_reset(DevTiming *tm, int n, cudaStream_t stream, uint64_t *progre
 void ifr_timing_to_host(const DevTiming &d, int repeats, ifr_timing *out);
 int ifr_ensure_timing(ifr_ctx *ctx, int n);
 
+// Launch shape and algorithmic work of one victim launch.
+struct VictimShape {
+    const void *fn;
+    int grid, block, smem, tmem_cols, uses_tensor;
+    double bytes, flops;
+};
+int ifr_victim_shape(ifr_ctx *ctx, const ifr_victim_cfg *cfg, VictimShape *s);
+
 // GEMM (ifr_gemm.cu)
 int ifr_gemm_enqueue(ifr_ctx *ctx, const ifr_victim_cfg *cfg, cudaStream_t stream, DevTiming *tm);
+int ifr_gemm_shape(const ifr_victim_cfg *cfg, VictimShape *s);

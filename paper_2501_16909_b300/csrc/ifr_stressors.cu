@@ -502,7 +502,83 @@ const void *smem_kernel_for(int ways) {
     }
 }
 
+// Kernel, block, dynamic shared memory and grid of a persistent stressor launch.
+struct StressShape {
+    const void *fn;
+    int block, smem, ways, bps, grid, occ;
+};
+
+StressShape stressor_shape(int num_sms, const ifr_stressor_cfg *cfg) {
+    StressShape s;
+    memset(&s, 0, sizeof s);
+    const int kind = cfg->kind;
+    s.block = kind == IFR_S_TENSOR ? 128 : (cfg->block ? cfg->block : kind_default_block(kind));
+    s.bps = cfg->blocks_per_sm ? cfg->blocks_per_sm : kind_default_bps(kind);
+    const int ilp = cfg->ilp ? cfg->ilp : 4;
+    switch (kind) {
+        case IFR_S_L2:
+        case IFR_S_HBM: s.fn = (const void *)stream_stress_kernel; break;
+        case IFR_S_FMA:
+            s.fn = ilp == 1 ? (const void *)fma_stress_kernel<1>
+                 : ilp == 2 ? (const void *)fma_stress_kernel<2>
+                 : ilp == 4 ? (const void *)fma_stress_kernel<4>
+                            : (const void *)fma_stress_kernel<8>;
+            break;
+        case IFR_S_SMEM_CF:
+        case IFR_S_SMEM_32W:
+            s.ways = cfg->smem_ways ? cfg->smem_ways : (kind == IFR_S_SMEM_CF ? 1 : 32);
+            s.fn = smem_kernel_for(s.ways);
+            s.smem = (s.block / 32) * 4096;
+            break;
+        case IFR_S_TENSOR:
+            s.fn = (const void *)tensor_stress_kernel;
+            s.smem = 32768 + 1024;
+            break;
+        case IFR_S_SCHED:
+            s.fn = (const void *)sched_stress_kernel;
+            s.block = 32;
+            s.grid = cfg->sched_blocks ? cfg->sched_blocks : 100000;
+            return s;
+        default: break;
+    }
+    // Launch enough blocks to fill every SM in the first wave (num_sms x occupancy):
+    // each allowed SM then receives at least blocks_per_sm blocks to claim its
+    // slots; the surplus blocks exit once the slots are taken.
+    if (s.fn) {
+        ifr_carveout(s.fn);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s.occ, s.fn, s.block, (size_t)s.smem) != cudaSuccess)
+            s.occ = 0;
+        if (s.occ > IFR_MAX_BPS) s.occ = IFR_MAX_BPS;
+        s.grid = num_sms * (s.occ > s.bps ? s.occ : s.bps);
+    } else {
+        s.grid = num_sms * s.bps;
+    }
+    return s;
+}
+
 }  // namespace
+
+extern "C" int ifr_stressor_profile(ifr_ctx *ctx, const ifr_stressor_cfg *cfg, ifr_kernel_profile *out) {
+    if (!ctx || !cfg || !out || cfg->kind < 0 || cfg->kind >= IFR_S_COUNT) return IFR_ERR_ARG;
+    memset(out, 0, sizeof *out);
+    const StressShape s = stressor_shape(ctx->info.num_sms, cfg);
+    cudaFuncAttributes fa;
+    IFR_CUDA(cudaFuncGetAttributes(&fa, s.fn));
+    int occ = 0;
+    IFR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, s.fn, s.block, (size_t)s.smem));
+    out->grid = s.grid;
+    out->block = s.block;
+    out->regs_per_thread = fa.numRegs;
+    out->static_smem = (int32_t)fa.sharedSizeBytes;
+    out->dynamic_smem = s.smem;
+    out->max_blocks_per_sm = occ;
+    out->tmem_cols = cfg->kind == IFR_S_TENSOR ? 128 : 0;
+    out->uses_tensor = cfg->kind == IFR_S_TENSOR;
+    out->sm_count = cfg->sm_count;
+    out->blocks_per_sm = cfg->kind == IFR_S_SCHED ? 0 : s.bps;
+    out->launches = cfg->kind == IFR_S_SCHED ? (cfg->sched_launches ? cfg->sched_launches : 64) : 1;
+    return IFR_OK;
+}
 
 int ifr_stressor_expected_arrivals(const Slot &s) {
     return s.cfg.kind == IFR_S_SCHED ? 1 : s.grid;
@@ -575,45 +651,11 @@ int ifr_stressor_enqueue(ifr_ctx *ctx, const ifr_stressor_cfg *cfg, cudaStream_t
     s.block = block;
     s.planned = p.planned;
     s.launches = 1;
-    // kernel and dynamic shared memory of this kind
-    const void *fn = nullptr;
-    size_t sh = 0;
-    int ways = 0;
-    switch (kind) {
-        case IFR_S_L2:
-        case IFR_S_HBM: fn = (const void *)stream_stress_kernel; break;
-        case IFR_S_FMA:
-            fn = p.ilp == 1 ? (const void *)fma_stress_kernel<1>
-               : p.ilp == 2 ? (const void *)fma_stress_kernel<2>
-               : p.ilp == 4 ? (const void *)fma_stress_kernel<4>
-                            : (const void *)fma_stress_kernel<8>;
-            break;
-        case IFR_S_SMEM_CF:
-        case IFR_S_SMEM_32W:
-            ways = cfg->smem_ways ? cfg->smem_ways : (kind == IFR_S_SMEM_CF ? 1 : 32);
-            fn = smem_kernel_for(ways);
-            sh = (size_t)(block / 32) * 4096;
-            break;
-        case IFR_S_TENSOR:
-            fn = (const void *)tensor_stress_kernel;
-            sh = 32768 + 1024;
-            break;
-        default: break;
-    }
-    // Launch enough blocks to fill every SM in the first wave (num_sms x occupancy):
-    // each allowed SM then receives at least blocks_per_sm blocks to claim its
-    // slots; the surplus blocks exit at once.
-    if (fn) {
-        ifr_carveout(fn);
-        int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kind == IFR_S_TENSOR ? 128 : block, sh) !=
-            cudaSuccess)
-            occ = 0;
-        if (occ > IFR_MAX_BPS) occ = IFR_MAX_BPS;
-        s.grid = num_sms * (occ > p.bps ? occ : p.bps);
-    } else {
-        s.grid = num_sms * p.bps;
-    }
+    const StressShape shape = stressor_shape(num_sms, cfg);
+    const void *fn = shape.fn;
+    const size_t sh = (size_t)shape.smem;
+    const int ways = shape.ways;
+    s.grid = shape.grid;
     ifr_carveout((const void *)stress_reset_kernel);
     stress_reset_kernel<<<1, 256, 0, stream>>>(s.d_state);
     IFR_CUDA(cudaGetLastError());

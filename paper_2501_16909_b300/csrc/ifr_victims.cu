@@ -395,54 +395,98 @@ int ifr_victim_validate(ifr_ctx *ctx, const ifr_victim_cfg *c) {
     (void)ctx;
 }
 
+// Launch shape of one victim launch (kernel, grid, block, dynamic shared memory)
+// and its algorithmic work; the single source of the choices the enqueue makes.
+int ifr_victim_shape(ifr_ctx *ctx, const ifr_victim_cfg *c, VictimShape *s) {
+    const int sms = ctx->info.num_sms;
+    memset(s, 0, sizeof *s);
+    s->block = 256;
+    switch (c->kind) {
+        case IFR_V_TRIAD:
+            s->fn = (const void *)triad_kernel;
+            s->grid = c->grid ? c->grid : sms * 8;
+            s->bytes = 12.0 * (double)c->n;
+            s->flops = 2.0 * (double)c->n;
+            return IFR_OK;
+        case IFR_V_LAYERNORM:
+        case IFR_V_SOFTMAX: {
+            const int64_t rows = c->m;
+            const int c4 = (int)c->n / 4;
+            const bool ln = c->kind == IFR_V_LAYERNORM;
+            if (c4 <= 256 * 4) {
+                s->fn = ln ? (const void *)layernorm_kernel<256, 4> : (const void *)softmax_kernel<256, 4>;
+                s->grid = c->grid ? c->grid : (int)(rows < (int64_t)sms * 8 ? rows : (int64_t)sms * 8);
+            } else if (c4 <= 256 * 8) {
+                s->fn = ln ? (const void *)layernorm_kernel<256, 8> : (const void *)softmax_kernel<256, 8>;
+                s->grid = c->grid ? c->grid : (int)(rows < (int64_t)sms * 8 ? rows : (int64_t)sms * 8);
+            } else {
+                s->fn = ln ? (const void *)layernorm_kernel<1024, 8> : (const void *)softmax_kernel<1024, 8>;
+                s->block = 1024;
+                s->grid = c->grid ? c->grid : (int)(rows < (int64_t)sms * 2 ? rows : (int64_t)sms * 2);
+            }
+            s->bytes = 8.0 * (double)rows * (double)c->n;
+            s->flops = (ln ? 5.0 : 4.0) * (double)rows * (double)c->n;
+            return IFR_OK;
+        }
+        case IFR_V_GEMV: {
+            s->fn = (const void *)gemv_kernel;
+            s->grid = c->grid ? c->grid : sms * 8;
+            if ((int64_t)s->grid * 8 > c->m) s->grid = (int)((c->m + 7) / 8);
+            s->smem = (int)(c->k * 2);
+            s->bytes = 2.0 * (double)c->m * (double)c->k + 2.0 * (double)c->k + 4.0 * (double)c->m;
+            s->flops = 2.0 * (double)c->m * (double)c->k;
+            return IFR_OK;
+        }
+        case IFR_V_HIST:
+            s->fn = (const void *)hist_kernel;
+            s->grid = c->grid ? c->grid : sms * 8;
+            s->bytes = 4.0 * (double)c->n;
+            return IFR_OK;
+        case IFR_V_GEMM: return ifr_gemm_shape(c, s);
+        default: return IFR_ERR_ARG;
+    }
+}
+
 // Enqueue K launches of a victim on `stream`, all stamping into *tm (already reset).
 int ifr_victim_enqueue(ifr_ctx *ctx, const ifr_victim_cfg *c, cudaStream_t stream, DevTiming *tm) {
     const int K = c->repeats > 0 ? c->repeats : 1;
-    const int sms = ctx->info.num_sms;
+    VictimShape sh;
+    int rc = ifr_victim_shape(ctx, c, &sh);
+    if (rc != IFR_OK) return rc;
     for (int rep = 0; rep < K; ++rep) {
         switch (c->kind) {
             case IFR_V_TRIAD: {
-                const int grid = c->grid ? c->grid : sms * 8;
-                ifr_carveout((const void *)triad_kernel);
-                triad_kernel<<<grid, 256, 0, stream>>>((float *)c->out, (const float *)c->in0, (const float *)c->in1,
-                                                       c->scalar, c->n, tm);
+                ifr_carveout(sh.fn);
+                triad_kernel<<<sh.grid, 256, 0, stream>>>((float *)c->out, (const float *)c->in0,
+                                                          (const float *)c->in1, c->scalar, c->n, tm);
                 break;
             }
             case IFR_V_LAYERNORM:
             case IFR_V_SOFTMAX: {
-                const int64_t rows = c->m;
-                const int cols = (int)c->n;
-                const int c4 = cols / 4;
+                const int c4 = (int)c->n / 4;
                 const bool ln = c->kind == IFR_V_LAYERNORM;
-                int grid = c->grid ? c->grid : (int)(rows < (int64_t)sms * 8 ? rows : (int64_t)sms * 8);
                 if (c4 <= 256 * 4) {
-                    grid = c->grid ? c->grid : (int)(rows < (int64_t)sms * 8 ? rows : (int64_t)sms * 8);
-                    if (ln) launch_ln<256, 4>(grid, stream, c, tm); else launch_sm<256, 4>(grid, stream, c, tm);
+                    if (ln) launch_ln<256, 4>(sh.grid, stream, c, tm); else launch_sm<256, 4>(sh.grid, stream, c, tm);
                 } else if (c4 <= 256 * 8) {
-                    if (ln) launch_ln<256, 8>(grid, stream, c, tm); else launch_sm<256, 8>(grid, stream, c, tm);
+                    if (ln) launch_ln<256, 8>(sh.grid, stream, c, tm); else launch_sm<256, 8>(sh.grid, stream, c, tm);
                 } else {
-                    grid = c->grid ? c->grid : (int)(rows < (int64_t)sms * 2 ? rows : (int64_t)sms * 2);
-                    if (ln) launch_ln<1024, 8>(grid, stream, c, tm); else launch_sm<1024, 8>(grid, stream, c, tm);
+                    if (ln) launch_ln<1024, 8>(sh.grid, stream, c, tm); else launch_sm<1024, 8>(sh.grid, stream, c, tm);
                 }
                 break;
             }
             case IFR_V_GEMV: {
-                const int64_t rows = c->m;
-                int grid = c->grid ? c->grid : sms * 8;
-                if ((int64_t)grid * 8 > rows) grid = (int)((rows + 7) / 8);
-                const size_t sh = (size_t)c->k * 2;
-                if (sh > 48 * 1024)
-                    cudaFuncSetAttribute(gemv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-                ifr_carveout((const void *)gemv_kernel);
-                gemv_kernel<<<grid, 256, sh, stream>>>((const __nv_bfloat16 *)c->in0, (const __nv_bfloat16 *)c->in1,
-                                                       (float *)c->out, rows, (int)c->k, tm);
+                if (sh.smem > 48 * 1024)
+                    cudaFuncSetAttribute(gemv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sh.smem);
+                ifr_carveout(sh.fn);
+                gemv_kernel<<<sh.grid, 256, sh.smem, stream>>>((const __nv_bfloat16 *)c->in0,
+                                                               (const __nv_bfloat16 *)c->in1, (float *)c->out, c->m,
+                                                               (int)c->k, tm);
                 break;
             }
             case IFR_V_HIST: {
                 IFR_CUDA(cudaMemsetAsync(c->out, 0, 256 * sizeof(uint32_t), stream));
-                int grid = c->grid ? c->grid : sms * 8;
-                ifr_carveout((const void *)hist_kernel);
-                hist_kernel<<<grid, 256, 0, stream>>>((const int32_t *)c->in0, c->n, (uint32_t *)c->out, tm);
+                ifr_carveout(sh.fn);
+                hist_kernel<<<sh.grid, 256, 0, stream>>>((const int32_t *)c->in0, c->n, (uint32_t *)c->out, tm);
                 break;
             }
             case IFR_V_GEMM: {
@@ -456,6 +500,34 @@ int ifr_victim_enqueue(ifr_ctx *ctx, const ifr_victim_cfg *c, cudaStream_t strea
         if (e != cudaSuccess) return ifr_cuda_fail(e, "victim launch", __FILE__, __LINE__);
         ctx->kernel_launches += 1;
     }
+    return IFR_OK;
+}
+
+extern "C" int ifr_victim_profile(ifr_ctx *ctx, const ifr_victim_cfg *cfg, ifr_kernel_profile *out) {
+    if (!ctx || !out) return IFR_ERR_ARG;
+    int rc = ifr_victim_validate(ctx, cfg);
+    if (rc != IFR_OK) return rc;
+    VictimShape s;
+    rc = ifr_victim_shape(ctx, cfg, &s);
+    if (rc != IFR_OK) return rc;
+    memset(out, 0, sizeof *out);
+    cudaFuncAttributes fa;
+    IFR_CUDA(cudaFuncGetAttributes(&fa, s.fn));
+    if (s.smem > 48 * 1024) cudaFuncSetAttribute(s.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, s.smem);
+    ifr_carveout(s.fn);
+    int occ = 0;
+    IFR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, s.fn, s.block, (size_t)s.smem));
+    out->grid = s.grid;
+    out->block = s.block;
+    out->regs_per_thread = fa.numRegs;
+    out->static_smem = (int32_t)fa.sharedSizeBytes;
+    out->dynamic_smem = s.smem;
+    out->max_blocks_per_sm = occ;
+    out->tmem_cols = s.tmem_cols;
+    out->uses_tensor = s.uses_tensor;
+    out->launches = cfg->repeats > 0 ? cfg->repeats : 1;
+    out->bytes_per_launch = s.bytes;
+    out->flops_per_launch = s.flops;
     return IFR_OK;
 }
 
