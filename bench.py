@@ -195,12 +195,39 @@ def run_ours(args):
         rate = units / (ms * 1e-3)
         full[A.STRESSOR_NAMES[kind]] = {"rate": rate, "unit": P.UNIT[kind] + "/s", "frac": rate / pk[kind][0],
                                         "peak": pk[kind][0], "peak_source": pk[kind][1], "ms": ms, "units": units}
+    # GPU time by kernel in the timed plain sweeps (CUDA events around each stressor
+    # run and each victim measurement): the dominant kernel gets the roofline
+    busy = {}
+    for rec in recs:
+        for c in rec[2]:
+            v = "victim:" + A.VICTIM_NAMES[wl.victim_kinds[c.victim]]
+            busy[v] = busy.get(v, 0.0) + c.timing.event_ms
+            if c.stressor >= 0 and c.level > 0:
+                k = A.STRESSOR_NAMES[wl.levels[c.stressor][0].kind]
+                busy[k] = busy.get(k, 0.0) + c.stress.elapsed_ms
+    tot_busy = sum(busy.values())
+    stress_busy = {k: v for k, v in busy.items() if not k.startswith("victim:")}
+    dom = max(stress_busy, key=stress_busy.get) if stress_busy else "hbm"
+    rl = {"hbm": ("hbm", 1e9, "GB/s", 1.0), "l2": ("l2", 1e9, "GB/s", 1.0), "fma": ("alu", 1e12, "TFLOP/s", 1.0),
+          "tensor": ("tensor", 1e12, "TFLOP/s", 1.0), "smem_cf": ("smem", 1e9, "GB/s", 128.0),
+          "smem_32w": ("smem", 1e9, "GB/s", 128.0), "sched": ("dispatch", 1e6, "Mblocks/s", 1.0)}
+    bound, scale, unit, mult = rl[dom]
+    fd = full[dom]
+    dom_kind = A.STRESSOR_NAMES.index(dom)
+    roofline = {"bound": bound, "achieved": round(fd["rate"] * mult / scale, 2),
+                "peak": round(fd["peak"] * mult / scale, 2), "unit": unit, "frac": round(fd["frac"], 4),
+                "traffic": None,
+                "kernel": "%s stressor at %d SMs (solo calibration runs of the timed steps: %d rounds)"
+                          % (dom, S, P.CAL_ROUNDS[dom_kind]),
+                "peak_source": fd["peak_source"] + " (of measured)" if "measured" in fd["peak_source"] else
+                fd["peak_source"],
+                "share_of_sweep_gpu_time": round(busy[dom] / tot_busy, 4)}
     hb = full.get("hbm")
-    roofline = {"bound": "hbm", "achieved": round(hb["rate"] / 1e9, 1), "peak": round(pk[A.IFR_S_HBM][0] / 1e9, 1),
-                "unit": "GB/s", "frac": round(hb["frac"], 4), "traffic": None,
-                "kernel": "stream_stress_kernel (HBM 4 GiB set, %d SMs x 2 blocks of 512, %d rounds x 4 chunks "
-                          "x 32 KiB per block)" % (S, P.CAL_ROUNDS[A.IFR_S_HBM]),
-                "peak_source": pk[A.IFR_S_HBM][1]}
+    roofline_hbm = {"bound": "hbm", "achieved": round(hb["rate"] / 1e9, 1), "peak": round(pk[A.IFR_S_HBM][0] / 1e9, 1),
+                    "unit": "GB/s", "frac": round(hb["frac"], 4), "traffic": None,
+                    "kernel": "stream_stress_kernel (HBM 4 GiB set, %d SMs x 2 blocks of 512, %d rounds x 4 chunks "
+                              "x 32 KiB per block)" % (S, P.CAL_ROUNDS[A.IFR_S_HBM]),
+                    "peak_source": pk[A.IFR_S_HBM][1]}
 
     # end to end through the public API with host-resident inputs
     e2e = None
@@ -224,6 +251,25 @@ def run_ours(args):
     e2e = {"value": round(n_e * world / te, 2), "unit": "cells/s",
            "h2d_bytes_per_step": sum(h.numel() * h.element_size() for h in host.values()),
            "d2h_bytes_per_step": sum(o.numel() * o.element_size() for o in outs.values())}
+
+    # the learned part: measured pairs (configuration-3 victims x co-runner configurations),
+    # trained by the library's MLP kernels; MAPE against held-out measured pairs
+    pred = None
+    if not args.no_predictor:
+        from paper_2501_16909_b300 import train_predictor as TP
+
+        tp0 = time.perf_counter()
+        data = TP.collect(ctx, repeats=1, log=lambda *x: None)
+        collect_s = time.perf_counter() - tp0
+        ev = {s: TP.evaluate(ctx, data, s) for s in ("random", "unseen")}
+        steps = sum(e["epochs"] * (e["train_pairs"] // 512) for e in ev.values())
+        train_s = sum(e["train_s"] for e in ev.values())
+        pred = {"pairs": int(len(data["y"])), "collect_s": round(collect_s, 2),
+                "mape_random_split": ev["random"]["mlp_mape"], "baseline_mape_random_split": ev["random"]["baseline_mape"],
+                "mape_unseen_corunners": ev["unseen"]["mlp_mape"],
+                "baseline_mape_unseen_corunners": ev["unseen"]["baseline_mape"],
+                "training_samples_per_s": round(steps * 512 / max(train_s, 1e-9), 1), "epochs": {
+                    s: e["epochs"] for s, e in ev.items()}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -260,7 +306,10 @@ def run_ours(args):
                          "noise": round(s["noise"], 4)} for v, s in enumerate(last[4])],
         "cells_valid": valid, "cells_hol": hol, "cells_total": len(last[3]),
         "victim_solo_window_ns": windows, "sched_launch_ns": t_launch,
+        "predictor": pred,
+        "sweep_gpu_ms_by_kernel": {k: round(v, 2) for k, v in sorted(busy.items(), key=lambda x: -x[1])},
         "roofline": roofline,
+        "roofline_hbm_stressor": roofline_hbm,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
@@ -361,6 +410,7 @@ def main():
     ap.add_argument("--workload", default="config2", choices=["config2", "config1"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-predictor", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

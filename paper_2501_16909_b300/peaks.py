@@ -6,7 +6,7 @@ turns that into the algorithmic quantity its resource's peak is stated in, and
 provides the peaks:
 
 * HBM        bytes/s — MEASURED_PEAKS.json `hbm_gbs` (STREAM-style copy)
-* L2         bytes/s — probe: the stream kernel over a 24 MiB set, every SM, 4 blocks each
+* L2         bytes/s — probe: best stream-kernel rate over 8 / 16 MiB sets, every SM
 * FP32 FMA   flop/s  — SMs x 128 lanes x 2 flop x max SM clock
 * tensor     flop/s  — MEASURED_PEAKS.json `bf16_tflops` (cuBLAS bf16 burst)
 * shared mem wavefronts/s — SMs x 1 wavefront per clock x max SM clock
@@ -27,7 +27,7 @@ UNIT = {A.IFR_S_HBM: "B", A.IFR_S_L2: "B", A.IFR_S_FMA: "flop", A.IFR_S_TENSOR: 
         A.IFR_S_SMEM_32W: "wavefront", A.IFR_S_SCHED: "block"}
 # fixed-work rounds of one calibration run per kind (about a millisecond at full SMs)
 CAL_ROUNDS = {A.IFR_S_HBM: 64, A.IFR_S_L2: 256, A.IFR_S_FMA: 32, A.IFR_S_TENSOR: 32, A.IFR_S_SMEM_CF: 64,
-              A.IFR_S_SMEM_32W: 4, A.IFR_S_SCHED: 0}
+              A.IFR_S_SMEM_32W: 32, A.IFR_S_SCHED: 0}
 
 
 def measured_peaks():
@@ -97,11 +97,18 @@ def peaks(ctx, l2_buf=None):
         A.IFR_S_SMEM_32W: (S * clk, "nominal: SMs x 1 shared-memory wavefront per clock x max SM clock"),
     }
     if l2_buf is not None:
-        nb = min(l2_buf.numel() * 4, 24 << 20)
-        nb -= nb % (512 * 64)
-        cfg = stressor_cfg(A.IFR_S_L2, sm_count=S, blocks_per_sm=4, block=512, buf=l2_buf, working_set_bytes=nb)
-        rate, _ = solo_rate(ctx, cfg, rounds=256)
-        out[A.IFR_S_L2] = (rate, "probe: stream kernel, 24 MiB L2-resident set, %d SMs x 4 blocks" % S)
+        best = (0.0, "")
+        for mib in (8, 16):
+            nb = min(l2_buf.numel() * 4, mib << 20)
+            nb -= nb % (512 * 64)
+            for bps in (2, 4):
+                cfg = stressor_cfg(A.IFR_S_L2, sm_count=S, blocks_per_sm=bps, block=512, buf=l2_buf,
+                                   working_set_bytes=nb)
+                rate, _ = solo_rate(ctx, cfg, rounds=256)
+                if rate > best[0]:
+                    best = (rate, "probe: best stream-kernel rate over 8 / 16 MiB L2-resident sets and 2 / 4 "
+                                  "blocks of 512 on every SM (%d MiB, %d blocks)" % (nb >> 20, bps))
+        out[A.IFR_S_L2] = best
     cfg = stressor_cfg(A.IFR_S_SCHED, sm_count=S, sched_blocks=100000, sched_cycles=1)
     rate, _ = solo_rate(ctx, cfg, launches=8)
     out[A.IFR_S_SCHED] = (rate, "probe: 1-cycle 32-thread blocks on every SM")

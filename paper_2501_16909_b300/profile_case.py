@@ -49,7 +49,7 @@ def main(argv=None):
         if kind == A.IFR_S_HBM:
             bufs["hbm"] = I.torch_u32_as_i32(1, (1 << 30) // 4, "cuda")
         if kind == A.IFR_S_L2:
-            bufs["l2"] = I.torch_u32_as_i32(3, (48 << 20) // 4, "cuda")
+            bufs["l2"] = I.torch_u32_as_i32(3, W.L2_SET_BYTES // 4, "cuda")
         cfg = W.stressor_level_cfg(kind, n_sm, bufs, seed=1)
         for _ in range(a.repeat):
             rate, res = P.solo_rate(ctx, cfg)

@@ -61,7 +61,7 @@ def main(argv=None):
 
     ctx = ifr.Context(0)
     S = ctx.info["num_sms"]
-    bufs = {"l2": I.torch_u32_as_i32(3, (48 << 20) // 4, "cuda"), "hbm": I.torch_u32_as_i32(1, (4 << 30) // 4, "cuda")}
+    bufs = {"l2": I.torch_u32_as_i32(3, (workloads.L2_SET_BYTES) // 4, "cuda"), "hbm": I.torch_u32_as_i32(1, (4 << 30) // 4, "cuda")}
     victims, vkinds, tensors = workloads.config3_victims("cuda")
     pk = peaks.peaks(ctx, bufs["l2"])
     base = workloads.config3_base_stressors(S, bufs)

@@ -77,7 +77,7 @@ def collect(ctx, repeats=2, log=print):
     from paper_2501_16909_b300.sweep_config3 import slowdown_table
 
     S = ctx.info["num_sms"]
-    bufs = {"l2": I.torch_u32_as_i32(3, (48 << 20) // 4, "cuda"), "hbm": I.torch_u32_as_i32(1, (4 << 30) // 4, "cuda")}
+    bufs = {"l2": I.torch_u32_as_i32(3, (workloads.L2_SET_BYTES) // 4, "cuda"), "hbm": I.torch_u32_as_i32(1, (4 << 30) // 4, "cuda")}
     victims, vkinds, _t = workloads.config3_victims("cuda")
     pk = peaks.peaks(ctx, bufs["l2"])
     rows = corunner_rows(S, bufs)
