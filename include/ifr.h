@@ -335,6 +335,33 @@ typedef struct {
  * IFR_ERR_CUDA.  A cell whose stressor timed out is recorded with valid = 0. */
 int ifr_sweep(ifr_ctx *ctx, const ifr_sweep_plan *plan, ifr_cell_result *cells, size_t cap, size_t *n_out);
 
+/* ---- kernel-with-kernel colocation (Sec. 4.1; Table 3 seq/col speedup) ---- */
+typedef struct {
+    ifr_timing victim_solo;     /* victim alone, K launches */
+    ifr_timing corunner_solo;   /* co-runner alone, one launch */
+    ifr_timing victim_corun;    /* victim while the co-runner chain runs */
+    ifr_timing corunner_corun;  /* the co-runner chain during the co-run */
+    int32_t valid;              /* the chain's first block started before the victim's first
+                                   block and its last block ended after the victim's last */
+    int32_t status;
+    int32_t corunner_launches;  /* length of the co-runner chain */
+    int32_t blocked;            /* head-of-line blocked (Sec. 4.2): no victim block could start
+                                   before the whole co-runner chain had finished */
+    uint64_t victim_release_ns; /* %globaltimer when the victim was released (a co-runner
+                                   block was running); latency = victim end - release */
+} ifr_corun_result;
+
+/* Colocate two workloads on concurrent streams: the co-runner runs as a chain of
+ * back-to-back launches on the context's stressor stream (long enough to cover
+ * 4x the victim's solo window when corunner_launches = 0), the victim's K
+ * launches start on the victim stream once a co-runner block is running (bounded
+ * wait), and every launch stamps %globaltimer.  The victim's slowdown is
+ * (victim_corun span / K) / (victim_solo span / K).  Both configurations are
+ * validated as in ifr_victim_launch.  Errors: IFR_ERR_ARG, IFR_ERR_CUDA,
+ * IFR_ERR_TIMEOUT (host wait). */
+int ifr_corun(ifr_ctx *ctx, const ifr_victim_cfg *victim, const ifr_victim_cfg *corunner, int corunner_launches,
+              ifr_corun_result *out);
+
 /* ---- sensitivity reduction (Sec. 4.3 slowdown; Sec. 5.1 estimator input) - */
 typedef struct {
     int32_t n_stressors, n_levels;

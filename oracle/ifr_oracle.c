@@ -106,14 +106,16 @@ void or_fma_block(uint64_t seed, int64_t k, int block, int ilp, int steps, int64
 /* ------------------------------------------------------------------------- */
 /* Shared-memory stressor (the paper's n-strided shared-memory copy, Sec.      */
 /* 4.4.1).  Each warp owns a 4 KiB array of 1024 words, word q initialised to  */
-/* low32(SplitMix64(seed<<32, (k*warps + w)*1024 + q)).  Every pass updates    */
-/* each word once with the LCG w <- 1664525*w + 1013904223 (mod 2^32); a round */
-/* is `passes` passes.  The access order (and hence the bank-conflict degree)  */
-/* does not change the result.  Returns the XOR of all words of the block.     */
+/* low32(SplitMix64(seed<<32, (k*warps + w)*1024 + q)).  Every pass loads and  */
+/* stores each word once; passes are numbered 0, 1, 2, ... over all rounds (a  */
+/* round is `passes` passes) and the even ones apply the LCG                    */
+/* w <- 1664525*w + 1013904223 (mod 2^32) while the odd ones copy the word.    */
+/* The access order (and hence the bank-conflict degree) does not change the   */
+/* result.  Returns the XOR of all words of the block.                         */
 /* ------------------------------------------------------------------------- */
 uint32_t or_smem_block(uint64_t seed, int64_t k, int warps, int64_t rounds, int passes) {
     uint64_t s0 = seed << 32;
-    int64_t steps = rounds * (int64_t)passes;
+    int64_t steps = (rounds * (int64_t)passes + 1) / 2; /* even pass indices */
     uint32_t acc = 0u;
     for (int w = 0; w < warps; ++w) {
         for (int q = 0; q < 1024; ++q) {

@@ -122,6 +122,14 @@ class ifr_kernel_profile(C.Structure):
     ]
 
 
+class ifr_corun_result(C.Structure):
+    _fields_ = [
+        ("victim_solo", ifr_timing), ("corunner_solo", ifr_timing), ("victim_corun", ifr_timing),
+        ("corunner_corun", ifr_timing), ("valid", C.c_int32), ("status", C.c_int32),
+        ("corunner_launches", C.c_int32), ("blocked", C.c_int32), ("victim_release_ns", C.c_uint64),
+    ]
+
+
 IFR_MLP_MAX_LAYERS = 8
 
 
@@ -136,7 +144,7 @@ class ifr_mlp(C.Structure):
 
 
 STRUCTS = [ifr_device_info, ifr_stressor_cfg, ifr_stressor_result, ifr_block_log, ifr_victim_cfg, ifr_timing,
-           ifr_sweep_plan, ifr_cell_result, ifr_sensitivity_out, ifr_kernel_profile, ifr_mlp]
+           ifr_sweep_plan, ifr_cell_result, ifr_sensitivity_out, ifr_kernel_profile, ifr_mlp, ifr_corun_result]
 
 _lib = None
 
@@ -170,6 +178,7 @@ def load():
         "ifr_sweep": (i32, [vp, P(ifr_sweep_plan), P(ifr_cell_result), C.c_size_t, P(C.c_size_t)]),
         "ifr_sensitivity": (i32, [P(ifr_cell_result), C.c_size_t, i32, i32, i32, P(C.c_double),
                                   P(ifr_sensitivity_out)]),
+        "ifr_corun": (i32, [vp, P(ifr_victim_cfg), P(ifr_victim_cfg), i32, P(ifr_corun_result)]),
         "ifr_victim_profile": (i32, [vp, P(ifr_victim_cfg), P(ifr_kernel_profile)]),
         "ifr_stressor_profile": (i32, [vp, P(ifr_stressor_cfg), P(ifr_kernel_profile)]),
         "ifr_mlp_forward": (i32, [vp, P(ifr_mlp), vp]),

@@ -289,20 +289,33 @@ __global__ void __launch_bounds__(1024) smem_stress_kernel(DevStress *st, Stress
         arr[q] = (uint32_t)ifr_splitmix64(s0, ((uint64_t)c.k * warps + warp) * 1024ull + q);
     __syncwarp();
     volatile uint32_t *mine = arr + 32 * (lane % WAYS) + lane / WAYS;
-    int64_t round = 0;
+    int64_t round = 0, gpass = 0;
     for (;; ++round) {
         if (threadIdx.x == 0) s_go[round & 1] = round_decision(st, p, round, c);
         __syncthreads();
         if (!s_go[round & 1]) break;
 #pragma unroll 1
-        for (int pass = 0; pass < (WAYS >= kSmemPassesCF ? 1 : kSmemPassesCF / WAYS); ++pass) {
+        for (int pass = 0; pass < (WAYS >= kSmemPassesCF ? 1 : kSmemPassesCF / WAYS); ++pass, ++gpass) {
+            // even passes update every word (LCG step), odd passes copy it back unchanged
+            const uint32_t mul = (gpass & 1) ? 1u : 1664525u, add = (gpass & 1) ? 0u : 1013904223u;
+            if (gpass & 1) {
 #pragma unroll
-            for (int jb = 0; jb < 32; jb += 8) {
-                uint32_t v[8];
+                for (int jb = 0; jb < 32; jb += 8) {
+                    uint32_t v[8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) v[i] = mine[smem_off<WAYS>(jb + i)];
+                    for (int i = 0; i < 8; ++i) v[i] = mine[smem_off<WAYS>(jb + i)];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) mine[smem_off<WAYS>(jb + i)] = v[i] * 1664525u + 1013904223u;
+                    for (int i = 0; i < 8; ++i) mine[smem_off<WAYS>(jb + i)] = v[i];
+                }
+            } else {
+#pragma unroll
+                for (int jb = 0; jb < 32; jb += 8) {
+                    uint32_t v[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) v[i] = mine[smem_off<WAYS>(jb + i)];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) mine[smem_off<WAYS>(jb + i)] = v[i] * mul + add;
+                }
             }
         }
     }

@@ -148,7 +148,95 @@ int capture_batch(ifr_ctx *ctx, const ifr_sweep_plan *p, const ifr_stressor_cfg 
     return rc;
 }
 
+// Waits (bounded) until a block of the measurement `tm` has started, then
+// stamps the release time into *release.
+__global__ void wait_started_kernel(const DevTiming *tm, uint64_t timeout_ns, DevTiming *status_to,
+                                    uint64_t *release) {
+    if (threadIdx.x != 0) return;
+    const uint64_t t0 = ifr_gtimer();
+    uint32_t it = 0;
+    while (*(const volatile uint64_t *)&tm->t_min == ~0ull) {
+        if (ifr_gtimer() - t0 > timeout_ns || ++it > (1u << 22)) {
+            status_to->status = IFR_ERR_NOT_RESIDENT;
+            break;
+        }
+        __nanosleep(256);
+    }
+    *release = ifr_gtimer();
+}
+
+int read_timing(ifr_ctx *ctx, int slot, int repeats, ifr_timing *out) {
+    DevTiming h;
+    IFR_CUDA(cudaMemcpy(&h, ctx->d_timing + slot, sizeof h, cudaMemcpyDeviceToHost));
+    ifr_timing_to_host(h, repeats, out);
+    return IFR_OK;
+}
+
 }  // namespace
+
+extern "C" int ifr_corun(ifr_ctx *ctx, const ifr_victim_cfg *victim, const ifr_victim_cfg *corunner,
+                         int corunner_launches, ifr_corun_result *out) {
+    if (!ctx || !out || corunner_launches < 0 || corunner_launches > 100000) return IFR_ERR_ARG;
+    int rc = ifr_victim_validate(ctx, victim);
+    if (!rc) rc = ifr_victim_validate(ctx, corunner);
+    if (rc) return rc;
+    memset(out, 0, sizeof *out);
+    rc = ifr_ensure_timing(ctx, 3);
+    if (rc) return rc;
+    IFR_CUDA(cudaDeviceSynchronize());
+    cudaStream_t sv = ctx->s_victim, ss = ctx->s_stress;
+    const int Kv = victim->repeats > 0 ? victim->repeats : 1;
+    // solo runs
+    rc = measure_solo_plain(ctx, victim, &out->victim_solo);
+    if (rc) return rc;
+    ifr_victim_cfg one = *corunner;
+    one.repeats = 1;
+    rc = measure_solo_plain(ctx, &one, &out->corunner_solo);
+    if (rc) return rc;
+    int n = corunner_launches;
+    if (n == 0) {
+        const double tv = (double)(out->victim_solo.t_end_ns - out->victim_solo.t_start_ns);
+        const double tc = (double)(out->corunner_solo.t_end_ns - out->corunner_solo.t_start_ns);
+        n = (int)(4.0 * tv / (tc > 1.0 ? tc : 1.0)) + 2;
+        if (n > 20000) n = 20000;
+    }
+    out->corunner_launches = n;
+    one.repeats = n;
+    // co-run: chain on the stressor stream, victim once a chain block is running
+    DevTiming *tv = ctx->d_timing, *tc = ctx->d_timing + 1;
+    cudaEvent_t reset_done;
+    IFR_CUDA(cudaEventCreateWithFlags(&reset_done, cudaEventDisableTiming));
+    // The victim side (waiter + K launches) is enqueued before the chain, so the
+    // waiter is already pending on the GPU when the chain's first block starts.
+    rc = ifr_timing_reset(tc, 1, ss, nullptr);
+    cudaEventRecord(reset_done, ss);
+    if (!rc) rc = ifr_timing_reset(tv, 1, sv, nullptr);
+    cudaStreamWaitEvent(sv, reset_done, 0);
+    uint64_t *release = (uint64_t *)(ctx->d_timing + 2);  // scratch word past the two measurements
+    if (!rc) {
+        wait_started_kernel<<<1, 32, 0, sv>>>(tc, 200000000ull, tv, release);
+        ctx->kernel_launches += 3;
+        rc = ifr_victim_enqueue(ctx, victim, sv, tv);
+    }
+    if (!rc) rc = ifr_victim_enqueue(ctx, &one, ss, tc);
+    IFR_CUDA(cudaEventRecord(ctx->ev_b, sv));
+    IFR_CUDA(cudaEventRecord(ctx->ev_a, ss));
+    int rc1 = wait_event_bounded(ctx->ev_b, 120000);
+    int rc2 = wait_event_bounded(ctx->ev_a, 120000);
+    cudaEventDestroy(reset_done);
+    if (rc) return rc;
+    if (rc1) return rc1;
+    if (rc2) return rc2;
+    rc = read_timing(ctx, 0, Kv, &out->victim_corun);
+    if (!rc) rc = read_timing(ctx, 1, n, &out->corunner_corun);
+    if (rc) return rc;
+    IFR_CUDA(cudaMemcpy(&out->victim_release_ns, release, sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    const ifr_timing &a = out->victim_corun, &b = out->corunner_corun;
+    out->valid = a.status == IFR_OK && b.status == IFR_OK && b.t_start_ns <= a.t_start_ns && b.t_end_ns >= a.t_end_ns;
+    out->blocked = a.status == IFR_OK && a.t_start_ns >= b.t_end_ns;
+    out->status = a.status != IFR_OK ? a.status : (out->valid ? IFR_OK : (out->blocked ? IFR_ERR_HOL : IFR_ERR_INVALID_CELL));
+    return IFR_OK;
+}
 
 extern "C" int ifr_sweep(ifr_ctx *ctx, const ifr_sweep_plan *p, ifr_cell_result *cells, size_t cap, size_t *n_out) {
     if (!ctx || !p || !n_out || p->n_victims <= 0 || !p->victims || p->n_stressors < 0 ||

@@ -69,3 +69,26 @@ def test_batched_sweep_config1(setup):
     cells = ctx.sweep(victims, levels, repeats=3, batched=True)
     got = _check(cells, 3, 3)
     assert got["slowdown"][0][3] > 1.2
+
+
+def test_corun_two_kernels_valid_and_consistent(setup):
+    """Kernel-with-kernel colocation: the chain covers the victim's window, the
+    reduction of the raw timestamps equals the reported slowdown, and two
+    HBM-bound kernels slow each other down (they share the DRAM bandwidth)."""
+    ctx, victims, _levels, _ = setup
+    n = 1 << 24
+    b = torch.empty(n, device="cuda").uniform_(-1, 1)
+    c = torch.empty(n, device="cuda").uniform_(-1, 1)
+    a = torch.empty(n, device="cuda")
+    # the co-runner leaves room on every SM (2 blocks of 256 threads) so both can be resident
+    co = ifr.victim_cfg(A.IFR_V_TRIAD, b, c, a, n=n, scalar=0.5, repeats=1, grid=2 * ctx.info["num_sms"])
+    r = ctx.corun(victims[0], co)
+    assert r["valid"] == 1 and r["status"] == 0 and r["corunner_launches"] >= 2, r
+    vs, vc = r["victim_solo"], r["victim_corun"]
+    assert vc["t_start_ns"] >= r["corunner_corun"]["t_start_ns"]
+    assert vc["t_end_ns"] <= r["corunner_corun"]["t_end_ns"]
+    want = ((vc["t_end_ns"] - vc["t_start_ns"]) / vc["repeats"]) / ((vs["t_end_ns"] - vs["t_start_ns"]) / vs["repeats"])
+    assert math.isclose(r["victim_slowdown"], want, rel_tol=1e-12)
+    assert r["victim_slowdown"] > 1.1
+    assert r["blocked"] == 0 and r["corunner_corun"]["t_start_ns"] <= r["victim_release_ns"] <= vc["t_start_ns"]
+

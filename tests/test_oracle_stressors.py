@@ -135,16 +135,18 @@ def test_smem_mapping_bijective_and_conflict_degree(ways):
 
 @pytest.mark.parametrize("ways", [1, 8, 32])
 def test_smem_brute_force_matches(ways):
-    seed, k, warps, rounds, passes = 6, 3, 2, 3, 2
+    seed, k, warps, rounds, passes = 6, 3, 2, 3, 3
     s0 = I.state0(seed)
     acc = 0
     for w in range(warps):
         mem = [I.splitmix64_at(s0, (k * warps + w) * 1024 + q) & 0xFFFFFFFF for q in range(1024)]
-        for _ in range(rounds * passes):
+        for gp in range(rounds * passes):
             for j in range(32):
                 for lane in range(32):
                     q = smem_word(lane, j, ways)
-                    mem[q] = (mem[q] * 1664525 + 1013904223) & 0xFFFFFFFF
+                    v = mem[q]
+                    # even passes apply the LCG, odd passes copy the word back
+                    mem[q] = (v * 1664525 + 1013904223) & 0xFFFFFFFF if gp % 2 == 0 else v
         for v in mem:
             acc ^= v
     assert oracle.smem_block(seed, k, warps, rounds, passes) == acc
