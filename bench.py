@@ -179,9 +179,9 @@ def run_ours(args):
     batched_s = sum(r[0]["batched_s"] for r in recs)
     cells = wl.n_cells * args.steps
     if world > 1:
-        tt = torch.tensor([batched_s, plain_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        batched_s, plain_s = float(tt[0]), float(tt[1])
+        from paper_2501_16909_b300 import replicas
+
+        batched_s, plain_s = replicas.max_over_ranks([batched_s, plain_s], device="cuda")
     val_b = cells * world / batched_s
     val_p = cells * world / plain_s
 
