@@ -3,14 +3,22 @@
 // The paper's shared-memory experiment colocates torch.mm (cuBLAS) with a strided
 // shared-memory stressor (Sec. 4.4.1); this is the library's own GEMM.
 //
-// One CTA computes a 128 x BN tile (BN = 256, or 128 when N is not a multiple of
-// 256) with 192 threads:
+// Persistent: one CTA per SM walks the 128 x BN output tiles (BN = 256, or 128 when
+// N is not a multiple of 256) in row-major tile order, stride gridDim.x.  192 threads:
 //   warp 0, lane 0   TMA producer: 64-wide K slices of A (128 rows) and B (BN rows)
-//                    into a STAGES-deep ring of 128-byte-swizzled shared tiles
-//   warp 1           allocates BN TMEM columns; lane 0 issues tcgen05.mma
-//                    (M = 128, N = BN, K = 16) and commits each stage back to the
-//                    producer, then the finished accumulator to the epilogue
-//   warps 2..5       epilogue: TMEM -> registers (tcgen05.ld) -> fp32 C rows
+//                    into a STAGES-deep ring of 128-byte-swizzled shared tiles; the
+//                    ring runs on across tile boundaries, so the next tile's loads
+//                    overlap the current tile's epilogue
+//   warp 1           allocates BN TMEM columns (one fp32 accumulator); lane 0 issues
+//                    tcgen05.mma (M = 128, N = BN, K = 16), commits every stage back to
+//                    the producer and every finished tile to the epilogue
+//   warps 2..5       epilogue, one warp per TMEM lane quadrant: 16-column chunks are
+//                    read with tcgen05.ld while the previous chunk is stored to C; the
+//                    accumulator is released after the last chunk's read
+// Registers are granted per SM sub-partition (four 16 K files, the block's warps
+// spread over them), so beside the widest stressor pair (2 x 512 threads x 40
+// registers: 8 warps x 1280 on every sub-partition) two GEMM warps must fit in 6144
+// registers: at most 96 per thread, which the 16-column chunks keep.
 // Every mbarrier wait is bounded; a CTA that times out records IFR_ERR_TIMEOUT in
 // the measurement's status, drains its outstanding TMA copies and frees TMEM.
 #include <cuda.h>
@@ -26,8 +34,10 @@ namespace {
 // stressor block (the tensor stressor needs 34 KiB, the shared-memory stressor
 // 2 x 33 KiB): a colocation-friendly configuration in the sense of Sec. 5.3.
 // Four stages (195 KiB) would make the GEMM and those stressors mutually exclusive.
-constexpr int BM = 128, BK = 64, STAGES = 3;
-constexpr uint64_t kGemmTimeoutNs = 1000000000ull;
+// One BN-column accumulator (not two) likewise leaves TMEM for the tensor stressor.
+constexpr int BM = 128, BK = 64, STAGES = 3, EPI_WARPS = 4, GEMM_THREADS = 64 + 32 * EPI_WARPS;
+constexpr uint64_t kGemmTimeoutNs = 4000000000ull;
+int g_num_sms = 0;  // persistent grid size (set from the context before each launch)
 
 template <int BN>
 struct GemmCfg {
@@ -37,12 +47,10 @@ struct GemmCfg {
     static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
 };
 
-__device__ __forceinline__ void g_enter(DevTiming *tm) {
-    if (threadIdx.x == 0) {
-        const unsigned long long t = ifr_gtimer();
-        atomicMin((unsigned long long *)&tm->t_min, t);
-        if (tm->progress) atomicMax((unsigned long long *)tm->progress, t);
-    }
+__device__ __forceinline__ void g_stamp(DevTiming *tm, bool first) {
+    const unsigned long long t = ifr_gtimer();
+    if (first) atomicMin((unsigned long long *)&tm->t_min, t);
+    if (tm->progress) atomicMax((unsigned long long *)tm->progress, t);
 }
 __device__ __forceinline__ void g_exit(DevTiming *tm) {
     __syncthreads();
@@ -56,22 +64,34 @@ __device__ __forceinline__ void g_exit(DevTiming *tm) {
     }
 }
 
+// 16 consecutive fp32 values of one C row (64 B) as four 16-byte stores.
+__device__ __forceinline__ void store_row16(float *dst, const uint32_t (&r)[16]) {
+    float4 *d = (float4 *)dst;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+        d[e] = make_float4(__uint_as_float(r[4 * e]), __uint_as_float(r[4 * e + 1]), __uint_as_float(r[4 * e + 2]),
+                           __uint_as_float(r[4 * e + 3]));
+}
+
 template <int BN>
-__global__ void __launch_bounds__(192, 1) gemm_bf16_kernel(const __grid_constant__ CUtensorMap ta,
-                                                           const __grid_constant__ CUtensorMap tb,
-                                                           float *__restrict__ C, int N, int K, DevTiming *tm) {
+__global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_kernel(const __grid_constant__ CUtensorMap ta,
+                                                                    const __grid_constant__ CUtensorMap tb,
+                                                                    float *__restrict__ C, int M, int N, int K,
+                                                                    DevTiming *tm) {
     using Cf = GemmCfg<BN>;
+    constexpr int CHUNKS = BN / 16;
     extern __shared__ uint8_t g_smem_raw[];
     uint8_t *base = (uint8_t *)(((uintptr_t)g_smem_raw + 1023u) & ~(uintptr_t)1023u);
     uint64_t *full = (uint64_t *)(base + STAGES * Cf::STAGE);
     uint64_t *empty = full + STAGES;
     uint64_t *tfull = empty + STAGES;
-    uint32_t *tmem_slot = (uint32_t *)(tfull + 1);
+    uint64_t *tempty = tfull + 1;
+    uint32_t *tmem_slot = (uint32_t *)(tempty + 1);
     volatile int *fail = (volatile int *)(tmem_slot + 1);
 
-    g_enter(tm);
+    if (threadIdx.x == 0) g_stamp(tm, true);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int tiles_n = N / BN, n_tiles = (M / BM) * tiles_n;
     const int KT = K / BK;
     const uint64_t deadline = ifr_gtimer() + kGemmTimeoutNs;
     if (threadIdx.x == 0) {
@@ -80,6 +100,7 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_kernel(const __grid_constant
             tc::mbar_init(&empty[s], 1);
         }
         tc::mbar_init(tfull, 1);
+        tc::mbar_init(tempty, EPI_WARPS);
         *fail = 0;
         tc::fence_mbar_init();
         tc::prefetch_tmap(&ta);
@@ -95,59 +116,84 @@ __global__ void __launch_bounds__(192, 1) gemm_bf16_kernel(const __grid_constant
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0 && lane == 0) {
-        int issued = 0;
-        for (int kt = 0; kt < KT; ++kt) {
-            const int s = kt % STAGES;
-            if (kt >= STAGES && !tc::mbar_wait(&empty[s], (uint32_t)((kt / STAGES) - 1) & 1u, deadline)) {
-                *fail = 1;
-                break;
+        int64_t g = 0;
+        for (int tile = blockIdx.x; tile < n_tiles && !*fail; tile += gridDim.x) {
+            const int m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
+            for (int kt = 0; kt < KT; ++kt, ++g) {
+                const int s = (int)(g % STAGES);
+                if (g >= STAGES && !tc::mbar_wait(&empty[s], (uint32_t)((g / STAGES) - 1) & 1u, deadline)) {
+                    *fail = 1;
+                    break;
+                }
+                uint8_t *sa = base + s * Cf::STAGE;
+                tc::mbar_arrive_expect_tx(&full[s], (uint32_t)Cf::STAGE);
+                tc::tma_load_2d(sa, &ta, &full[s], kt * BK, m0);
+                tc::tma_load_2d(sa + Cf::A_BYTES, &tb, &full[s], kt * BK, n0);
             }
-            uint8_t *sa = base + s * Cf::STAGE;
-            tc::mbar_arrive_expect_tx(&full[s], (uint32_t)Cf::STAGE);
-            tc::tma_load_2d(sa, &ta, &full[s], kt * BK, m0);
-            tc::tma_load_2d(sa + Cf::A_BYTES, &tb, &full[s], kt * BK, n0);
-            issued = kt + 1;
         }
         // drain: the copies of the last stages have landed before the CTA may exit
-        for (int kt = issued - STAGES < 0 ? 0 : issued - STAGES; kt < issued; ++kt)
-            tc::mbar_wait(&full[kt % STAGES], (uint32_t)(kt / STAGES) & 1u, deadline + 100000000ull);
+        for (int64_t q = g - STAGES < 0 ? 0 : g - STAGES; q < g; ++q)
+            tc::mbar_wait(&full[q % STAGES], (uint32_t)(q / STAGES) & 1u, deadline + 100000000ull);
     } else if (warp == 1 && lane == 0) {
         constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
-        for (int kt = 0; kt < KT; ++kt) {
-            const int s = kt % STAGES;
-            if (!tc::mbar_wait(&full[s], (uint32_t)(kt / STAGES) & 1u, deadline)) {
+        int64_t g = 0;
+        int j = 0;
+        for (int tile = blockIdx.x; tile < n_tiles && !*fail; tile += gridDim.x, ++j) {
+            if (j > 0 && !tc::mbar_wait(tempty, (uint32_t)((j - 1) & 1), deadline)) {
                 *fail = 1;
                 break;
             }
             tc::fence_after();
-            const uint32_t sa = tc::smem_u32(base + s * Cf::STAGE);
-            const uint64_t adesc = tc::desc_sw128(sa);
-            const uint64_t bdesc = tc::desc_sw128(sa + Cf::A_BYTES);
+            for (int kt = 0; kt < KT; ++kt, ++g) {
+                const int s = (int)(g % STAGES);
+                if (!tc::mbar_wait(&full[s], (uint32_t)(g / STAGES) & 1u, deadline)) {
+                    *fail = 1;
+                    break;
+                }
+                tc::fence_after();
+                const uint32_t sa = tc::smem_u32(base + s * Cf::STAGE);
+                const uint64_t adesc = tc::desc_sw128(sa);
+                const uint64_t bdesc = tc::desc_sw128(sa + Cf::A_BYTES);
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk)
-                tc::mma_bf16(tmem, adesc + 2ull * kk, bdesc + 2ull * kk, idesc, (uint32_t)((kt | kk) != 0));
-            tc::mma_commit(&empty[s]);
+                for (int kk = 0; kk < BK / 16; ++kk)
+                    tc::mma_bf16(tmem, adesc + 2ull * kk, bdesc + 2ull * kk, idesc, (uint32_t)((kt | kk) != 0));
+                tc::mma_commit(&empty[s]);
+            }
+            tc::mma_commit(tfull);  // also on failure, so the epilogue's wait completes
         }
-        tc::mma_commit(tfull);
     } else if (warp >= 2) {
         const int q = warp & 3;  // TMEM lane quadrant this warp may access
-        const bool ok = tc::mbar_wait(tfull, 0u, deadline + 100000000ull);
-        tc::fence_after();
-        if (__all_sync(0xffffffffu, ok && !*fail)) {
-            float *crow = C + (size_t)(m0 + q * 32 + lane) * (size_t)N + n0;
-#pragma unroll 1
-            for (int cc = 0; cc < BN; cc += 32) {
-                uint32_t r[32];
-                tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)cc, r);
-                tc::tmem_ld_wait();
-                float4 *dst = (float4 *)(crow + cc);
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    dst[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
-                                         __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+        const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
+        int j = 0;
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++j) {
+            const bool ok = tc::mbar_wait(tfull, (uint32_t)(j & 1), deadline + 100000000ull);
+            tc::fence_after();
+            if (!__all_sync(0xffffffffu, ok && !*fail)) {
+                if (lane == 0) *fail = 1;
+                break;
             }
-        } else if (lane == 0) {
-            *fail = 1;
+            const int m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
+            float *crow = C + (size_t)(m0 + q * 32 + lane) * (size_t)N + n0;
+            uint32_t ra[16], rb[16];
+            tc::tmem_ld16(trow, ra);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int c = 0; c < CHUNKS; c += 2) {
+                tc::tmem_ld16(trow + (uint32_t)((c + 1) * 16), rb);
+                store_row16(crow + c * 16, ra);
+                tc::tmem_ld_wait();
+                if (c + 2 < CHUNKS) {
+                    tc::tmem_ld16(trow + (uint32_t)((c + 2) * 16), ra);
+                    store_row16(crow + (c + 1) * 16, rb);
+                    tc::tmem_ld_wait();
+                } else {
+                    tc::fence_before();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(tempty);  // accumulator drained: the next tile may start
+                    store_row16(crow + (c + 1) * 16, rb);
+                }
+            }
+            if (warp == 2 && lane == 0) g_stamp(tm, false);  // victim progress, one stamp per tile
         }
     }
     tc::fence_before();
@@ -200,18 +246,22 @@ int launch_gemm(const ifr_victim_cfg *c, cudaStream_t stream, DevTiming *tm) {
     rc = make_map(&tb, c->in1, c->n, c->k, BN);
     if (rc) return rc;
     ifr_carveout((const void *)gemm_bf16_kernel<BN>);
-    dim3 grid((unsigned)(c->n / BN), (unsigned)(c->m / BM));
-    gemm_bf16_kernel<BN><<<grid, 192, GemmCfg<BN>::SMEM, stream>>>(ta, tb, (float *)c->out, (int)c->n, (int)c->k, tm);
+    const int tiles = (int)((c->n / BN) * (c->m / BM));
+    const int grid = tiles < g_num_sms ? tiles : g_num_sms;
+    gemm_bf16_kernel<BN><<<grid, GEMM_THREADS, GemmCfg<BN>::SMEM, stream>>>(ta, tb, (float *)c->out, (int)c->m,
+                                                                           (int)c->n, (int)c->k, tm);
     return IFR_OK;
 }
 
 }  // namespace
 
 int ifr_gemm_shape(const ifr_victim_cfg *c, VictimShape *s) {
+    if (g_num_sms == 0) cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, 0);
     const bool wide = c->n % 256 == 0;
     s->fn = wide ? (const void *)gemm_bf16_kernel<256> : (const void *)gemm_bf16_kernel<128>;
-    s->grid = (int)((c->n / (wide ? 256 : 128)) * (c->m / BM));
-    s->block = 192;
+    const int tiles = (int)((c->n / (wide ? 256 : 128)) * (c->m / BM));
+    s->grid = tiles < g_num_sms ? tiles : g_num_sms;
+    s->block = GEMM_THREADS;
     s->smem = wide ? GemmCfg<256>::SMEM : GemmCfg<128>::SMEM;
     s->tmem_cols = wide ? 256 : 128;
     s->uses_tensor = 1;
@@ -220,7 +270,8 @@ int ifr_gemm_shape(const ifr_victim_cfg *c, VictimShape *s) {
     return IFR_OK;
 }
 
-int ifr_gemm_enqueue(ifr_ctx *, const ifr_victim_cfg *c, cudaStream_t stream, DevTiming *tm) {
+int ifr_gemm_enqueue(ifr_ctx *ctx, const ifr_victim_cfg *c, cudaStream_t stream, DevTiming *tm) {
+    g_num_sms = ctx->info.num_sms;
     if (c->m > 65535 * BM || c->n > (1ll << 30) || c->k > (1ll << 30)) return IFR_ERR_ARG;
     if (c->n % 256 == 0) return launch_gemm<256>(c, stream, tm);
     return launch_gemm<128>(c, stream, tm);

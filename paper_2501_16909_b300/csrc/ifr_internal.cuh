@@ -133,7 +133,7 @@ struct ifr_ctx {
 // that stressor and victim blocks can share an SM without a carveout switch
 // (the paper sets the same split for the same reason, Sec. 4.4.2).
 void ifr_carveout(const void *func);
-#define IFR_HOL_NS 20000000ull  // 20 ms without victim progress = head-of-line blocked
+#define IFR_HOL_NS 50000000ull  // 50 ms without victim progress = head-of-line blocked
 
 // ---------------------------------------------------------------- internal API
 #define IFR_CUDA(call)                                      \
