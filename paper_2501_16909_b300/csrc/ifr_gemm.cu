@@ -3,9 +3,15 @@
 // The paper's shared-memory experiment colocates torch.mm (cuBLAS) with a strided
 // shared-memory stressor (Sec. 4.4.1); this is the library's own GEMM.
 //
-// Persistent: one CTA per SM walks the 128 x BN output tiles (BN = 256, or 128 when
-// N is not a multiple of 256) in row-major tile order, stride gridDim.x.  192 threads:
-//   warp 0, lane 0   TMA producer: 64-wide K slices of A (128 rows) and B (BN rows)
+// Persistent: one CTA per SM takes 128 x BN output tiles (BN = 256, or 128 when N is
+// not a multiple of 256) in row-major tile order until none are left: its first tile
+// is its own index, every later one comes from a device counter.  Handing tiles out on demand keeps the load balance of a one-CTA-per-tile
+// launch: a CTA on an SM that a stressor slows takes fewer tiles instead of holding
+// up the grid with a fixed share.  192 threads:
+//   warp 0, lane 0   tile scheduler and TMA producer: takes tile blockIdx.x first and
+//                    then claims tiles gridDim.x, gridDim.x + 1, ... from the counter; publishes
+//                    its index in a 4-entry shared ring for the other roles, and loads
+//                    64-wide K slices of A (128 rows) and B (BN rows)
 //                    into a STAGES-deep ring of 128-byte-swizzled shared tiles; the
 //                    ring runs on across tile boundaries, so the next tile's loads
 //                    overlap the current tile's epilogue
@@ -20,7 +26,9 @@
 // registers: 8 warps x 1280 on every sub-partition) two GEMM warps must fit in 6144
 // registers: at most 96 per thread, which the 16-column chunks keep.
 // Every mbarrier wait is bounded; a CTA that times out records IFR_ERR_TIMEOUT in
-// the measurement's status, drains its outstanding TMA copies and frees TMEM.
+// the measurement's status, drains its outstanding TMA copies and frees TMEM.  The
+// last CTA of a launch to finish returns the tile counter to zero for the next one
+// (launches on one measurement record are stream-ordered).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <string.h>
@@ -36,6 +44,7 @@ namespace {
 // Four stages (195 KiB) would make the GEMM and those stressors mutually exclusive.
 // One BN-column accumulator (not two) likewise leaves TMEM for the tensor stressor.
 constexpr int BM = 128, BK = 64, STAGES = 3, EPI_WARPS = 4, GEMM_THREADS = 64 + 32 * EPI_WARPS;
+constexpr int RING = 4;  // tile indices in flight between the scheduler and the consumers
 constexpr uint64_t kGemmTimeoutNs = 4000000000ull;
 int g_num_sms = 0;  // persistent grid size (set from the context before each launch)
 
@@ -44,7 +53,7 @@ struct GemmCfg {
     static constexpr int A_BYTES = BM * BK * 2;
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
+    static constexpr int SMEM = STAGES * STAGE + 1024 + 256;  // + alignment slack + barriers / ring
 };
 
 __device__ __forceinline__ void g_stamp(DevTiming *tm, bool first) {
@@ -86,7 +95,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_kernel(const __grid
     uint64_t *empty = full + STAGES;
     uint64_t *tfull = empty + STAGES;
     uint64_t *tempty = tfull + 1;
-    uint32_t *tmem_slot = (uint32_t *)(tempty + 1);
+    uint64_t *sfull = tempty + 1;   // [RING] tile index published
+    uint64_t *sempty = sfull + RING; // [RING] tile index read by the MMA lane and 4 epilogue warps
+    int32_t *ring = (int32_t *)(sempty + RING);
+    uint32_t *tmem_slot = (uint32_t *)(ring + RING);
     volatile int *fail = (volatile int *)(tmem_slot + 1);
 
     if (threadIdx.x == 0) g_stamp(tm, true);
@@ -98,6 +110,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_kernel(const __grid
         for (int s = 0; s < STAGES; ++s) {
             tc::mbar_init(&full[s], 1);
             tc::mbar_init(&empty[s], 1);
+        }
+        for (int r = 0; r < RING; ++r) {
+            tc::mbar_init(&sfull[r], 1);
+            tc::mbar_init(&sempty[r], 1 + EPI_WARPS);
         }
         tc::mbar_init(tfull, 1);
         tc::mbar_init(tempty, EPI_WARPS);
@@ -117,10 +133,21 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_kernel(const __grid
 
     if (warp == 0 && lane == 0) {
         int64_t g = 0;
-        for (int tile = blockIdx.x; tile < n_tiles && !*fail; tile += gridDim.x) {
+        // The following tile is claimed just before the wait for the current tile's
+        // last free stage, so the atomic's round trip hides behind that wait while the
+        // CTA holds the claim only for the stages still in flight.
+        uint32_t next = blockIdx.x;  // first tile: the CTA's own index; later ones from the counter
+        for (int j = 0;; ++j) {
+            const int r = j % RING;
+            if (j >= RING && !tc::mbar_wait(&sempty[r], (uint32_t)((j / RING) - 1) & 1u, deadline)) *fail = 1;
+            const int tile = (*fail || next >= (uint32_t)n_tiles) ? -1 : (int)next;
+            ring[r] = tile;
+            tc::mbar_arrive(&sfull[r]);  // release: the index is visible to the waiting roles
+            if (tile < 0) break;
             const int m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
             for (int kt = 0; kt < KT; ++kt, ++g) {
                 const int s = (int)(g % STAGES);
+                if (kt == KT - 1) next = gridDim.x + atomicAdd(&tm->tile_next, 1u);
                 if (g >= STAGES && !tc::mbar_wait(&empty[s], (uint32_t)((g / STAGES) - 1) & 1u, deadline)) {
                     *fail = 1;
                     break;
@@ -137,11 +164,17 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_kernel(const __grid
     } else if (warp == 1 && lane == 0) {
         constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
         int64_t g = 0;
-        int j = 0;
-        for (int tile = blockIdx.x; tile < n_tiles && !*fail; tile += gridDim.x, ++j) {
+        for (int j = 0;; ++j) {
+            const int r = j % RING;
+            const bool got = tc::mbar_wait(&sfull[r], (uint32_t)(j / RING) & 1u, deadline + 50000000ull);
+            const int tile = got ? ring[r] : -1;
+            tc::mbar_arrive(&sempty[r]);
+            if (!got) *fail = 1;
+            if (tile < 0) break;
             if (j > 0 && !tc::mbar_wait(tempty, (uint32_t)((j - 1) & 1), deadline)) {
                 *fail = 1;
-                break;
+                tc::mma_commit(tfull);
+                continue;  // read the ring on to its end marker
             }
             tc::fence_after();
             for (int kt = 0; kt < KT; ++kt, ++g) {
@@ -164,8 +197,17 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_kernel(const __grid
     } else if (warp >= 2) {
         const int q = warp & 3;  // TMEM lane quadrant this warp may access
         const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
-        int j = 0;
-        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++j) {
+        for (int j = 0;; ++j) {
+            const int r = j % RING;
+            const bool got = tc::mbar_wait(&sfull[r], (uint32_t)(j / RING) & 1u, deadline + 50000000ull);
+            const int tile = got ? ring[r] : -1;
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&sempty[r]);
+            if (!__all_sync(0xffffffffu, got)) {
+                if (lane == 0) *fail = 1;
+                break;
+            }
+            if (tile < 0) break;
             const bool ok = tc::mbar_wait(tfull, (uint32_t)(j & 1), deadline + 100000000ull);
             tc::fence_after();
             if (!__all_sync(0xffffffffu, ok && !*fail)) {
@@ -204,6 +246,14 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_kernel(const __grid
     }
     if (threadIdx.x == 0 && *fail) tm->status = IFR_ERR_TIMEOUT;
     g_exit(tm);
+    if (threadIdx.x == 0) {
+        // every CTA has claimed its last tile before it counts itself done
+        __threadfence();
+        if (atomicAdd(&tm->tile_done, 1u) == gridDim.x - 1u) {
+            atomicExch(&tm->tile_next, 0u);
+            atomicExch(&tm->tile_done, 0u);
+        }
+    }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {

@@ -74,6 +74,8 @@ struct DevTiming {
     int32_t status;
     uint32_t sm_bits[IFR_MAX_SMS / 32];
     uint64_t *progress;  // context-wide "last victim block entry/exit" (%globaltimer)
+    uint32_t tile_next;  // GEMM: next output tile to hand out (0 between launches)
+    uint32_t tile_done;  // GEMM: CTAs of the running launch that have finished
 };
 
 // Kernel parameters of a stressor launch (passed by value).

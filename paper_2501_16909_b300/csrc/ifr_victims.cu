@@ -16,12 +16,6 @@ __device__ __forceinline__ void v_enter(DevTiming *tm) {
         if (tm->progress) atomicMax((unsigned long long *)tm->progress, t);
     }
 }
-// Progress stamp every 16 iterations of a block's loop (thread 0), so that a
-// stressor watching for head-of-line blocking sees long-lived blocks working.
-__device__ __forceinline__ void v_tick(DevTiming *tm, int64_t it) {
-    if (threadIdx.x == 0 && (it & 15) == 15 && tm->progress)
-        atomicMax((unsigned long long *)tm->progress, (unsigned long long)ifr_gtimer());
-}
 __device__ __forceinline__ void v_exit(DevTiming *tm) {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -41,6 +35,8 @@ __global__ void timing_reset_kernel(DevTiming *tm, int n, uint64_t *progress) {
         tm[i].t_max = 0ull;
         tm[i].blocks = 0u;
         tm[i].status = 0;
+        tm[i].tile_next = 0u;
+        tm[i].tile_done = 0u;
         for (int j = 0; j < IFR_MAX_SMS / 32; ++j) tm[i].sm_bits[j] = 0u;
     }
 }
@@ -139,7 +135,6 @@ __global__ void __launch_bounds__(NT) layernorm_kernel(const float *__restrict__
     const int c4 = cols >> 2;
     const float inv_n = 1.0f / (float)cols;
     for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
-        v_tick(tm, (r - blockIdx.x) / gridDim.x);
         const float4 *xr = (const float4 *)(x + r * cols);
         float4 v[VPT];
         float s = 0.f;
@@ -186,7 +181,6 @@ __global__ void __launch_bounds__(NT) softmax_kernel(const float *__restrict__ x
     v_enter(tm);
     const int c4 = cols >> 2;
     for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
-        v_tick(tm, (r - blockIdx.x) / gridDim.x);
         const float4 *xr = (const float4 *)(x + r * cols);
         float4 v[VPT];
         float m = -INFINITY;
@@ -242,7 +236,6 @@ __global__ void __launch_bounds__(256) gemv_kernel(const __nv_bfloat16 *__restri
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     for (int64_t r = (int64_t)blockIdx.x * wpb + warp; r < rows; r += (int64_t)gridDim.x * wpb) {
-        if (warp == 0) v_tick(tm, (r - blockIdx.x * wpb) / ((int64_t)gridDim.x * wpb));
         const uint4 *ar = (const uint4 *)(A + r * cols);
         float acc = 0.f;
         int j = lane;
@@ -306,9 +299,7 @@ __global__ void __launch_bounds__(256) hist_kernel(const int32_t *__restrict__ k
     const int4 *k4 = (const int4 *)keys;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t tick = 0;
-    for (; i + 3 * stride < n4; i += 4 * stride, ++tick) {
-        v_tick(tm, tick);
+    for (; i + 3 * stride < n4; i += 4 * stride) {
         int4 v[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
