@@ -84,6 +84,14 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# DRAM bytes (read + write) per launch of the roofline kernels, from the committed
+# ncu captures of the same launch (file under profiles/ named beside each); an entry
+# is removed when its kernel changes, so the line then reports null.
+NCU_DRAM_BYTES = {
+    "smem_32w": 19968,  # smem_32w_stressor_148sm.md
+}
+
+
 def dist_env():
     return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -216,7 +224,7 @@ def run_ours(args):
     dom_kind = A.STRESSOR_NAMES.index(dom)
     roofline = {"bound": bound, "achieved": round(fd["rate"] * mult / scale, 2),
                 "peak": round(fd["peak"] * mult / scale, 2), "unit": unit, "frac": round(fd["frac"], 4),
-                "traffic": None,
+                "traffic": NCU_DRAM_BYTES.get(dom),
                 "kernel": "%s stressor at %d SMs (solo calibration runs of the timed steps: %d rounds)"
                           % (dom, S, P.CAL_ROUNDS[dom_kind]),
                 "peak_source": fd["peak_source"] + " (of measured)" if "measured" in fd["peak_source"] else
@@ -224,7 +232,7 @@ def run_ours(args):
                 "share_of_sweep_gpu_time": round(busy[dom] / tot_busy, 4)}
     hb = full.get("hbm")
     roofline_hbm = {"bound": "hbm", "achieved": round(hb["rate"] / 1e9, 1), "peak": round(pk[A.IFR_S_HBM][0] / 1e9, 1),
-                    "unit": "GB/s", "frac": round(hb["frac"], 4), "traffic": None,
+                    "unit": "GB/s", "frac": round(hb["frac"], 4), "traffic": NCU_DRAM_BYTES.get("hbm"),
                     "kernel": "stream_stress_kernel (HBM 4 GiB set, %d SMs x 2 blocks of 512, %d rounds x 4 chunks "
                               "x 32 KiB per block)" % (S, P.CAL_ROUNDS[A.IFR_S_HBM]),
                     "peak_source": pk[A.IFR_S_HBM][1]}
@@ -240,7 +248,8 @@ def run_ours(args):
         mp, msrc = P.measured_peaks()
         g = wl.victims[gv]
         roofline_gemm = {"bound": "tensor", "achieved": round(ach, 1), "peak": mp["bf16_tflops"],
-                         "unit": "TFLOP/s", "frac": round(ach / mp["bf16_tflops"], 4), "traffic": None,
+                         "unit": "TFLOP/s", "frac": round(ach / mp["bf16_tflops"], 4),
+                         "traffic": NCU_DRAM_BYTES.get("gemm"),
                          "kernel": "gemm_bf16_kernel<256> (BF16 %dx%dx%d, persistent, %d CTAs; solo launches of the "
                                    "timed plain sweeps)" % (g.m, g.n, g.k, prof["grid"]),
                          "peak_source": "MEASURED_PEAKS bf16_tflops (%s, burst)" % msrc,
