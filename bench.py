@@ -89,6 +89,8 @@ class ClockSampler:
 # is removed when its kernel changes, so the line then reports null.
 NCU_DRAM_BYTES = {
     "smem_32w": 19968,  # smem_32w_stressor_148sm.md
+    "hbm": 2486113792,  # hbm_stream_stressor_1GiB_148sm.md (same blocks and rounds; set > L2)
+    "gemm": 111298048,  # gemm_bf16_tcgen05_4096.md
 }
 
 

@@ -5,7 +5,8 @@ full-intensity rate, i.e. all SMs at duty 1), find for each f a configuration
 (sm_count, duty) whose solo fixed-work rate is within +-5 % of f * rate_max:
 
   1. bisect on sm_count (the rate grows monotonically with the SMs used) for the
-     smallest count whose rate reaches the target;
+     smallest count whose rate reaches the target; the count just below replaces it
+     when that one is closer and within the tolerance; a target of 1 takes all SMs;
   2. if that overshoots by more than the tolerance, lower the duty cycle
      (active fraction of each period) by the measured ratio, and correct once
      more with the secant between the two duty points.
@@ -72,9 +73,12 @@ class Tuner:
                     hi = mid
                 else:
                     lo = mid + 1
-            n = hi
-            # the count just below may land closer to the target than the first one above it
-            if n > 1 and abs(self.rate(n - 1) - target) < abs(self.rate(n) - target):
+            n = self.S if f >= 1.0 else hi  # the full rate is the all-SM rate by definition
+            # the count just below may land closer to the target than the first one above
+            # it; take it only when it is within the tolerance (an undershoot cannot be
+            # repaired with the duty cycle, an overshoot can)
+            if (n == hi and n > 1 and abs(self.rate(n - 1) - target) < abs(self.rate(n) - target)
+                    and abs(self.rate(n - 1) / target - 1) <= self.tol):
                 n -= 1
             duty, r = 1.0, self.rate(n)
             if self.base.kind != A.IFR_S_SCHED and r > target * (1 + self.tol):
