@@ -41,6 +41,8 @@ def lib():
         L.or_stream_block_checksum.argtypes = [p, i64, i64, i64, i64, i64]
         L.or_fma_block.restype = None
         L.or_fma_block.argtypes = [u64, i64, i32, i32, i32, i64, p, p]
+        L.or_fp64_block.restype = None
+        L.or_fp64_block.argtypes = [u64, i64, i32, i32, i32, i64, p, p]
         L.or_smem_block.restype = u32
         L.or_smem_block.argtypes = [u64, i64, i32, i64, i32]
         L.or_tensor_block.restype = u32
@@ -83,6 +85,13 @@ def stream_block_checksum(buf_u32: np.ndarray, chunk_elems: int, active_planned:
 def fma_block(seed: int, k: int, block: int, ilp: int, steps: int, rounds: int):
     r0, fin = C.c_uint32(0), C.c_uint32(0)
     lib().or_fma_block(seed, k, block, ilp, steps, rounds, C.byref(r0), C.byref(fin))
+    return int(r0.value), int(fin.value)
+
+
+def fp64_block(seed: int, k: int, block: int, ilp: int, steps: int, rounds: int):
+    """FP64 multiply-chain stressor block (Sec. 4.4.3): (round-0 XOR, final XOR)."""
+    r0, fin = C.c_uint32(0), C.c_uint32(0)
+    lib().or_fp64_block(seed, k, block, ilp, steps, rounds, C.byref(r0), C.byref(fin))
     return int(r0.value), int(fin.value)
 
 

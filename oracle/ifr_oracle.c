@@ -104,6 +104,43 @@ void or_fma_block(uint64_t seed, int64_t k, int block, int ilp, int steps, int64
 }
 
 /* ------------------------------------------------------------------------- */
+/* FP64 stressor (the paper's compute kernel turned to fp64 multiplication,    */
+/* Sec. 4.4.3, scenarios S1-S4 = ILP 1-4).  One multiplier per launch, from    */
+/* output 0 of SplitMix64(seed<<32):                                           */
+/*   a = 1 - (1 + (u0>>54)) * 2^-40            (exact in fp64, 0 < a < 1)      */
+/* Chain j of thread t of active block k, g = (k*block + t)*ilp + j, starts at */
+/*   x0 = 1 + (u(g+2)>>12) * 2^-52             (exact, in [1, 2))              */
+/* and iterates x <- x * a (one IEEE rounding), `steps` times per round.  Each */
+/* chain contributes the XOR of the two 32-bit halves of its bits.            */
+/* round0_xor: XOR over chains after round 0; final_xor: after `rounds`.       */
+/* ------------------------------------------------------------------------- */
+static uint32_t f64_fold(double d) {
+    uint64_t u;
+    memcpy(&u, &d, sizeof u);
+    return (uint32_t)(u ^ (u >> 32));
+}
+
+void or_fp64_block(uint64_t seed, int64_t k, int block, int ilp, int steps, int64_t rounds,
+                   uint32_t *round0_xor, uint32_t *final_xor) {
+    uint64_t s0 = seed << 32;
+    double a = 1.0 - (double)(1u + (unsigned)(or_splitmix64(s0, 0) >> 54)) * ldexp(1.0, -40);
+    uint32_t r0 = 0u, fin = 0u;
+    for (int t = 0; t < block; ++t) {
+        for (int j = 0; j < ilp; ++j) {
+            uint64_t g = ((uint64_t)k * (uint64_t)block + (uint64_t)t) * (uint64_t)ilp + (uint64_t)j;
+            double x = 1.0 + (double)(or_splitmix64(s0, g + 2u) >> 12) * ldexp(1.0, -52);
+            for (int64_t r = 0; r < rounds; ++r) {
+                for (int s = 0; s < steps; ++s) x = x * a;
+                if (r == 0) r0 ^= f64_fold(x);
+            }
+            fin ^= f64_fold(x);
+        }
+    }
+    if (round0_xor) *round0_xor = r0;
+    if (final_xor) *final_xor = fin;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Shared-memory stressor (the paper's n-strided shared-memory copy, Sec.      */
 /* 4.4.1).  Each warp owns a 4 KiB array of 1024 words, word q initialised to  */
 /* low32(SplitMix64(seed<<32, (k*warps + w)*1024 + q)).  Every pass loads and  */

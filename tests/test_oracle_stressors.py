@@ -108,6 +108,74 @@ def test_fma_rounds_compose_and_fixed_point():
     assert abs(float(x) - xs) <= 2.0 * abs(float(np.spacing(np.float32(xs)))) / (1 - a)
 
 
+# ---------------------------------------------------------------- FP64 multiply chains
+def _round_f64(q: Fraction) -> float:
+    """Correctly rounded (nearest, ties to even) fp64 value of a positive normal rational."""
+    e = q.numerator.bit_length() - q.denominator.bit_length()
+    if Fraction(2) ** e > q:
+        e -= 1
+    if Fraction(2) ** (e + 1) <= q:
+        e += 1
+    scaled = q * Fraction(2) ** (52 - e)
+    m = scaled.numerator // scaled.denominator
+    rem = scaled - m
+    if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and m % 2 == 1):
+        m += 1
+    return float(Fraction(m) * Fraction(2) ** (e - 52))
+
+
+def _fold64(v: float) -> int:
+    u = int(np.array([v], np.float64).view(np.uint64)[0])
+    return (u ^ (u >> 32)) & 0xFFFFFFFF
+
+
+def _fp64_params(seed):
+    s0 = I.state0(seed)
+    a = 1 - Fraction(1 + (I.splitmix64_at(s0, 0) >> 54), 2**40)
+    return s0, a
+
+
+def _fp64_brute(seed, k, block, ilp, steps, rounds):
+    """Exact rational products rounded to fp64 one step at a time (Sec. 4.4.3 chains)."""
+    s0, a = _fp64_params(seed)
+    r0 = fin = 0
+    for t in range(block):
+        for j in range(ilp):
+            g = (k * block + t) * ilp + j
+            x = 1 + Fraction(I.splitmix64_at(s0, g + 2) >> 12, 2**52)
+            for r in range(rounds):
+                for _ in range(steps):
+                    x = Fraction(_round_f64(x * a))
+                if r == 0:
+                    r0 ^= _fold64(float(x))
+            fin ^= _fold64(float(x))
+    return r0, fin
+
+
+def test_fp64_exact_rational_brute_force():
+    assert oracle.fp64_block(3, 2, 3, 2, 25, 2) == _fp64_brute(3, 2, 3, 2, 25, 2)
+    assert oracle.fp64_block(0, 0, 2, 4, 30, 1) == _fp64_brute(0, 0, 2, 4, 30, 1)
+
+
+def test_fp64_rounds_compose_and_error_bound():
+    assert oracle.fp64_block(5, 1, 4, 2, 64, 2)[1] == oracle.fp64_block(5, 1, 4, 2, 128, 1)[1]
+    # one chain (block 1, ilp 1): the rounded product stays within n half-ulps of the
+    # exact x0 * a^n (each step adds a relative error of at most 2^-53)
+    seed, n = 11, 4000
+    s0, a = _fp64_params(seed)
+    x0 = 1 + Fraction(I.splitmix64_at(s0, 2) >> 12, 2**52)
+    exact = float(x0 * a ** n)
+    _, fin = oracle.fp64_block(seed, 0, 1, 1, n, 1)
+    # the fold loses the value; recover it by re-running the chain in Python floats
+    x = float(x0)
+    af = float(a)
+    for _ in range(n):
+        x = x * af
+    assert _fold64(x) == fin
+    assert abs(x - exact) <= n * 2.0**-53 * abs(exact) * 1.01
+    assert 0 < float(a) < 1 and float(a) == a  # the multiplier is exact in fp64
+
+
 # ---------------------------------------------------------------- shared memory
 def smem_word(lane, j, ways):
     """(row, bank) -> word index for lane `lane`, iteration j, conflict degree `ways`."""
