@@ -37,7 +37,7 @@
 extern "C" {
 #endif
 
-#define IFR_ABI_VERSION 1
+#define IFR_ABI_VERSION 2
 
 /* ---- status codes ------------------------------------------------------- */
 #define IFR_OK 0
@@ -102,7 +102,8 @@ typedef enum {
     IFR_S_SMEM_32W = 4, /* shared-memory ld/st, 32-way bank conflicts */
     IFR_S_L2 = 5,       /* streaming XOR read of an L2-resident buffer */
     IFR_S_HBM = 6,      /* streaming XOR read of an HBM-sized buffer */
-    IFR_S_COUNT = 7
+    IFR_S_FP64 = 7,     /* dependent fp64 multiply chains (Sec. 4.4.3), ILP chains/thread */
+    IFR_S_COUNT = 8
 } ifr_stressor_kind;
 
 typedef struct {
@@ -112,7 +113,7 @@ typedef struct {
                                 spread evenly over the SM id range. */
     int32_t blocks_per_sm;   /* persistent blocks per allowed SM (0 = kind default) */
     int32_t block;           /* threads per block (0 = kind default) */
-    int32_t ilp;             /* FMA: independent chains per thread (1,2,4,8; 0 = 4) */
+    int32_t ilp;             /* FMA / FP64: independent chains per thread (1,2,4,8; 0 = 4) */
     int32_t smem_ways;       /* SMEM: bank-conflict degree 1..32 power of 2 (0 = kind) */
     float duty;              /* active fraction of each period, (0, 1]; 0 or 1 = always */
     int32_t period_ns;       /* duty-cycle period (0 = 100000) */
@@ -124,15 +125,20 @@ typedef struct {
     int32_t sched_blocks;    /* SCHED: blocks per launch (0 = 100000) */
     int32_t sched_launches;  /* SCHED: launches enqueued (0 = 64) */
     int32_t sched_cycles;    /* SCHED: busy cycles per block (0 = 100) */
-    int32_t mask_mode;       /* 0: shared SMs, %smid filter; 1: green-context partition */
+    int32_t mask_mode;       /* 0: sm_count SMs spread evenly over the SM ids (%smid filter);
+                                1: green-context partition (IFR_ERR_UNSUPPORTED);
+                                2: exactly the SMs set in sm_mask (%smid filter), e.g. two
+                                   disjoint partitions as in Sec. 4.3's inter-SM runs;
+                                   sm_count must equal the number of bits set */
     uint64_t deadline_ns;    /* device-side limit on the run (0 = 2 s) */
+    uint32_t sm_mask[IFR_MAX_SMS / 32]; /* mask_mode 2: bit s of word s/32 allows SM id s */
 } ifr_stressor_cfg;
 
 typedef struct {
     uint32_t checksum;       /* XOR of the per-block checksums (SCHED: of all blocks) */
     int32_t status;          /* first error recorded by any block, or IFR_OK */
     uint64_t rounds;         /* rounds summed over active blocks (SCHED: working blocks) */
-    uint64_t work;           /* kind units: chunks (L2/HBM), FMA steps/thread-chain,
+    uint64_t work;           /* kind units: chunks (L2/HBM), FMA / FP64 steps/thread-chain,
                                 smem ld/st pairs/lane, tile MMAs, busy blocks (SCHED) */
     uint64_t t_start_ns;     /* earliest active-block start (%globaltimer) */
     uint64_t t_start_last_ns;/* latest active-block start */
@@ -242,6 +248,36 @@ typedef struct {
  * then the call still synchronises).  Errors: IFR_ERR_ARG (shape, null or
  * misaligned pointer), IFR_ERR_LAUNCH, IFR_ERR_CUDA. */
 int ifr_victim_launch(ifr_ctx *ctx, const ifr_victim_cfg *cfg, void *stream, ifr_timing *out);
+
+/* ---- two stressors against each other (Sec. 3 pitfalls, Sec. 4.3, Sec. 4.4.3) -- */
+/* The paper's kernel-against-kernel experiments colocate two fixed-work kernels
+ * and compare each one's latency with its latency alone: two compute kernels at
+ * 6.25 % achieved occupancy (Pitfall 1), a compute kernel beside a copy kernel
+ * (Pitfall 2), two copy kernels on disjoint SM partitions over growing data
+ * (L2 pollution, Sec. 4.3), and two fp64 compute kernels whose speedup
+ * sequential/colocated tracks the summed pipe utilisation (Table 3).
+ * ifr_stressor_pair runs A alone, B alone, then A and B released at the same
+ * instant on two streams (both streams wait on one event recorded after a short
+ * device-side gate, so neither starts first by a host launch latency).  Both
+ * configurations must be fixed-work (max_rounds > 0) persistent kinds (not
+ * IFR_S_SCHED); their SM sets (mask_mode 0 or 2) may overlap or be disjoint.
+ * Spans are %globaltimer first-block start to last-block end. */
+typedef struct {
+    ifr_stressor_result solo_a, solo_b;  /* each alone */
+    ifr_stressor_result co_a, co_b;      /* released together */
+    double solo_a_ns, solo_b_ns;         /* spans alone */
+    double co_a_ns, co_b_ns;             /* spans under co-run */
+    double seq_ns;                       /* solo_a_ns + solo_b_ns: back to back */
+    double col_ns;                       /* co-run makespan: last end - first start */
+    int32_t overlapped;                  /* 1 if the two co-run spans intersect */
+    int32_t status;                      /* first non-OK status of the four runs, else IFR_OK */
+} ifr_pair_result;
+
+/* Errors: IFR_ERR_ARG (null pointer, max_rounds <= 0, IFR_S_SCHED, invalid
+ * configuration as in ifr_stressor_launch), IFR_ERR_CAPACITY (fewer than two free
+ * stressor slots), IFR_ERR_TIMEOUT (a run did not finish within 60 s on the host),
+ * IFR_ERR_CUDA.  A run whose blocks hit their deadline is reported in `status`. */
+int ifr_stressor_pair(ifr_ctx *ctx, const ifr_stressor_cfg *a, const ifr_stressor_cfg *b, ifr_pair_result *out);
 
 /* ---- solo kernel profiles (Sec. 2.2 metrics; Sec. 5.1 estimator inputs) -- */
 /* Static launch properties of the kernel a victim or stressor configuration

@@ -183,6 +183,16 @@ class Context:
         check(self._L.ifr_stressor_profile(self._h, C.byref(cfg), C.byref(p)), "ifr_stressor_profile")
         return _struct_dict(p)
 
+    def stressor_pair(self, a: ifr_stressor_cfg, b: ifr_stressor_cfg) -> dict:
+        """ifr_stressor_pair: A alone, B alone, then both released together (fixed work)."""
+        self._sync()
+        r = _abi.ifr_pair_result()
+        check(self._L.ifr_stressor_pair(self._h, C.byref(a), C.byref(b), C.byref(r)), "ifr_stressor_pair")
+        d = {k: getattr(r, k) for k, _ in r._fields_ if k not in ("solo_a", "solo_b", "co_a", "co_b")}
+        for k in ("solo_a", "solo_b", "co_a", "co_b"):
+            d[k] = _struct_dict(getattr(r, k))
+        return d
+
     # -- victims
     def victim_launch(self, cfg: ifr_victim_cfg, stream=None) -> dict:
         self._sync()

@@ -30,8 +30,8 @@ IFR_MAX_LEVELS = 16
 IFR_MAX_SMS = 256
 
 # stressor kinds
-IFR_S_SCHED, IFR_S_FMA, IFR_S_TENSOR, IFR_S_SMEM_CF, IFR_S_SMEM_32W, IFR_S_L2, IFR_S_HBM = range(7)
-STRESSOR_NAMES = ["sched", "fma", "tensor", "smem_cf", "smem_32w", "l2", "hbm"]
+IFR_S_SCHED, IFR_S_FMA, IFR_S_TENSOR, IFR_S_SMEM_CF, IFR_S_SMEM_32W, IFR_S_L2, IFR_S_HBM, IFR_S_FP64 = range(8)
+STRESSOR_NAMES = ["sched", "fma", "tensor", "smem_cf", "smem_32w", "l2", "hbm", "fp64"]
 # victim kinds
 IFR_V_TRIAD, IFR_V_GEMM, IFR_V_GEMV, IFR_V_LAYERNORM, IFR_V_SOFTMAX, IFR_V_HIST = range(6)
 VICTIM_NAMES = ["triad", "gemm", "gemv", "layernorm", "softmax", "hist"]
@@ -53,7 +53,7 @@ class ifr_stressor_cfg(C.Structure):
         ("ilp", C.c_int32), ("smem_ways", C.c_int32), ("duty", C.c_float), ("period_ns", C.c_int32),
         ("working_set_bytes", C.c_int64), ("buf", C.c_void_p), ("seed", C.c_uint64), ("max_rounds", C.c_int64),
         ("sched_blocks", C.c_int32), ("sched_launches", C.c_int32), ("sched_cycles", C.c_int32),
-        ("mask_mode", C.c_int32), ("deadline_ns", C.c_uint64),
+        ("mask_mode", C.c_int32), ("deadline_ns", C.c_uint64), ("sm_mask", C.c_uint32 * (IFR_MAX_SMS // 32)),
     ]
 
 
@@ -122,6 +122,15 @@ class ifr_kernel_profile(C.Structure):
     ]
 
 
+class ifr_pair_result(C.Structure):
+    _fields_ = [
+        ("solo_a", ifr_stressor_result), ("solo_b", ifr_stressor_result), ("co_a", ifr_stressor_result),
+        ("co_b", ifr_stressor_result), ("solo_a_ns", C.c_double), ("solo_b_ns", C.c_double),
+        ("co_a_ns", C.c_double), ("co_b_ns", C.c_double), ("seq_ns", C.c_double), ("col_ns", C.c_double),
+        ("overlapped", C.c_int32), ("status", C.c_int32),
+    ]
+
+
 class ifr_corun_result(C.Structure):
     _fields_ = [
         ("victim_solo", ifr_timing), ("corunner_solo", ifr_timing), ("victim_corun", ifr_timing),
@@ -144,7 +153,8 @@ class ifr_mlp(C.Structure):
 
 
 STRUCTS = [ifr_device_info, ifr_stressor_cfg, ifr_stressor_result, ifr_block_log, ifr_victim_cfg, ifr_timing,
-           ifr_sweep_plan, ifr_cell_result, ifr_sensitivity_out, ifr_kernel_profile, ifr_mlp, ifr_corun_result]
+           ifr_sweep_plan, ifr_cell_result, ifr_sensitivity_out, ifr_kernel_profile, ifr_mlp, ifr_corun_result,
+           ifr_pair_result]
 
 _lib = None
 
@@ -179,6 +189,7 @@ def load():
         "ifr_sensitivity": (i32, [P(ifr_cell_result), C.c_size_t, i32, i32, i32, P(C.c_double),
                                   P(ifr_sensitivity_out)]),
         "ifr_corun": (i32, [vp, P(ifr_victim_cfg), P(ifr_victim_cfg), i32, P(ifr_corun_result)]),
+        "ifr_stressor_pair": (i32, [vp, P(ifr_stressor_cfg), P(ifr_stressor_cfg), P(ifr_pair_result)]),
         "ifr_victim_profile": (i32, [vp, P(ifr_victim_cfg), P(ifr_kernel_profile)]),
         "ifr_stressor_profile": (i32, [vp, P(ifr_stressor_cfg), P(ifr_kernel_profile)]),
         "ifr_mlp_forward": (i32, [vp, P(ifr_mlp), vp]),

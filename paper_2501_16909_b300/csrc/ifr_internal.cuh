@@ -93,6 +93,7 @@ struct StressParams {
     int64_t n_chunks;     // L2/HBM chunks (chunk = blockDim * 4 int4)
     int32_t ilp;          // FMA
     float fma_a, fma_b;   // FMA multiplier and addend (launch-wide)
+    double fp64_a;        // FP64 multiplier (launch-wide)
     int32_t ways;         // SMEM
     int32_t sched_blocks, sched_cycles;
     ifr_block_log *logs;

@@ -26,6 +26,8 @@ namespace {
 constexpr int kStreamChunksPerRound = 4;  // L2/HBM: chunks per round
 // FMA: steps per chain per round = kFmaWork / ILP (16384 FMAs per thread per round)
 constexpr int kFmaWork = 16384;
+// FP64: steps per chain per round = kFp64Work / ILP (1024 multiplies per thread per round)
+constexpr int kFp64Work = 1024;
 // SMEM: passes over the warp array per round = max(1, 8 / WAYS)
 constexpr int kSmemPassesCF = 8;
 constexpr int kSchedLcgSteps = 16;        // SCHED: LCG steps per block result
@@ -263,6 +265,55 @@ __global__ void __launch_bounds__(1024) fma_stress_kernel(DevStress *st, StressP
     if (threadIdx.x == 0) write_log(p, st, c, round, (uint64_t)round * (kFmaWork / ILP), cs, cs2);
 }
 
+// ------------------------------------------------------------------ FP64 multiply
+// The compute kernel of Sec. 4.4.3 on fp64 multiplication (__dmul_rn): ILP
+// independent chains x <- x * a per thread, one launch-wide multiplier just below 1.
+template <int ILP>
+__global__ void __launch_bounds__(1024) fp64_stress_kernel(DevStress *st, StressParams p) {
+    __shared__ int s_k;
+    __shared__ uint64_t s_t0;
+    __shared__ int s_go[2];
+    __shared__ uint32_t s_red[32];
+    BlockCtl c;
+    if (!block_enter(st, p, c, &s_k, &s_t0)) return;
+    const uint64_t s0 = p.seed << 32;
+    const double a = p.fp64_a;
+    double x[ILP];
+#pragma unroll
+    for (int j = 0; j < ILP; ++j) {
+        const uint64_t g = ((uint64_t)c.k * blockDim.x + threadIdx.x) * ILP + j;
+        x[j] = 1.0 + (double)(ifr_splitmix64(s0, g + 2ull) >> 12) * 0x1p-52;
+    }
+    uint32_t r0 = 0u;
+    int64_t round = 0;
+    for (;; ++round) {
+        if (threadIdx.x == 0) s_go[round & 1] = round_decision(st, p, round, c);
+        __syncthreads();
+        if (!s_go[round & 1]) break;
+#pragma unroll 8
+        for (int s = 0; s < kFp64Work / ILP; ++s) {
+#pragma unroll
+            for (int j = 0; j < ILP; ++j) x[j] = __dmul_rn(x[j], a);
+        }
+        if (round == 0) {
+#pragma unroll
+            for (int j = 0; j < ILP; ++j) {
+                const uint64_t u = (uint64_t)__double_as_longlong(x[j]);
+                r0 ^= (uint32_t)(u ^ (u >> 32));
+            }
+        }
+    }
+    uint32_t fin = 0u;
+#pragma unroll
+    for (int j = 0; j < ILP; ++j) {
+        const uint64_t u = (uint64_t)__double_as_longlong(x[j]);
+        fin ^= (uint32_t)(u ^ (u >> 32));
+    }
+    uint32_t cs = ifr_block_xor(r0, s_red);
+    uint32_t cs2 = ifr_block_xor(fin, s_red);
+    if (threadIdx.x == 0) write_log(p, st, c, round, (uint64_t)round * (kFp64Work / ILP), cs, cs2);
+}
+
 // ------------------------------------------------------------------ shared memory
 // Lane l = g*WAYS + r, iteration j: bank = g + (32/WAYS)*(j % WAYS),
 // row = r + WAYS*(j / WAYS), word = 32*row + bank.  For a fixed j the WAYS lanes
@@ -473,6 +524,7 @@ int kind_default_block(int kind) {
     switch (kind) {
         case IFR_S_SCHED: return 32;
         case IFR_S_FMA: return 128;
+        case IFR_S_FP64: return 128;
         case IFR_S_TENSOR: return 128;
         case IFR_S_SMEM_CF:
         case IFR_S_SMEM_32W: return 256;
@@ -536,6 +588,12 @@ StressShape stressor_shape(int num_sms, const ifr_stressor_cfg *cfg) {
                  : ilp == 2 ? (const void *)fma_stress_kernel<2>
                  : ilp == 4 ? (const void *)fma_stress_kernel<4>
                             : (const void *)fma_stress_kernel<8>;
+            break;
+        case IFR_S_FP64:
+            s.fn = ilp == 1 ? (const void *)fp64_stress_kernel<1>
+                 : ilp == 2 ? (const void *)fp64_stress_kernel<2>
+                 : ilp == 4 ? (const void *)fp64_stress_kernel<4>
+                            : (const void *)fp64_stress_kernel<8>;
             break;
         case IFR_S_SMEM_CF:
         case IFR_S_SMEM_32W:
@@ -604,7 +662,8 @@ static int validate_cfg(ifr_ctx *ctx, const ifr_stressor_cfg *c) {
     if (c->block < 0 || c->block > 1024 || (c->block % 32) != 0) return IFR_ERR_ARG;
     if (c->duty < 0.f || c->duty > 1.f) return IFR_ERR_ARG;
     if (c->max_rounds < 0) return IFR_ERR_ARG;
-    if (c->kind == IFR_S_FMA && !(c->ilp == 0 || c->ilp == 1 || c->ilp == 2 || c->ilp == 4 || c->ilp == 8))
+    if ((c->kind == IFR_S_FMA || c->kind == IFR_S_FP64) &&
+        !(c->ilp == 0 || c->ilp == 1 || c->ilp == 2 || c->ilp == 4 || c->ilp == 8))
         return IFR_ERR_ARG;
     if (c->kind == IFR_S_SMEM_CF || c->kind == IFR_S_SMEM_32W) {
         int w = c->smem_ways;
@@ -623,7 +682,19 @@ static int validate_cfg(ifr_ctx *ctx, const ifr_stressor_cfg *c) {
     if (c->kind == IFR_S_TENSOR && ((c->block != 0 && c->block != 128) || c->blocks_per_sm > 2)) return IFR_ERR_ARG;
     if (c->kind == IFR_S_SCHED && (c->sched_blocks < 0 || c->sched_launches < 0 || c->sched_cycles < 0))
         return IFR_ERR_ARG;
-    if (c->mask_mode != 0) return IFR_ERR_UNSUPPORTED;
+    if (c->mask_mode == 1) return IFR_ERR_UNSUPPORTED;
+    if (c->mask_mode == 2) {
+        // explicit SM set: only ids of this device, exactly sm_count of them
+        int bits = 0;
+        for (int s = 0; s < IFR_MAX_SMS; ++s) {
+            if (!((c->sm_mask[s >> 5] >> (s & 31)) & 1u)) continue;
+            if (s >= ctx->info.num_sms) return IFR_ERR_ARG;
+            ++bits;
+        }
+        if (bits != c->sm_count) return IFR_ERR_ARG;
+    } else if (c->mask_mode != 0) {
+        return IFR_ERR_ARG;
+    }
     return IFR_OK;
 }
 
@@ -640,7 +711,10 @@ int ifr_stressor_enqueue(ifr_ctx *ctx, const ifr_stressor_cfg *cfg, cudaStream_t
     memset(&p, 0, sizeof p);
     p.kind = kind;
     p.bps = cfg->blocks_per_sm ? cfg->blocks_per_sm : kind_default_bps(kind);
-    ifr_compute_mask(num_sms, cfg->sm_count, p.mask);
+    if (cfg->mask_mode == 2)
+        memcpy(p.mask, cfg->sm_mask, sizeof p.mask);
+    else
+        ifr_compute_mask(num_sms, cfg->sm_count, p.mask);
     p.planned = cfg->sm_count * p.bps;
     p.seed = cfg->seed;
     p.max_rounds = cfg->max_rounds;
@@ -654,6 +728,8 @@ int ifr_stressor_enqueue(ifr_ctx *ctx, const ifr_stressor_cfg *cfg, cudaStream_t
         const uint64_t u0 = host_splitmix64(p.seed << 32, 0), u1 = host_splitmix64(p.seed << 32, 1);
         p.fma_a = (float)(1.0 - 0x1p-12 - (double)(u0 >> 53) * 0x1p-23);
         p.fma_b = (float)((double)((int64_t)(u1 >> 40) - (1 << 23)) * 0x1p-29);
+        // FP64 multiplier: a = 1 - (1 + (u0 >> 54)) 2^-40 (exact in fp64, 0 < a < 1)
+        p.fp64_a = 1.0 - (double)(1u + (unsigned)(u0 >> 54)) * 0x1p-40;
     }
     p.logs = s.d_logs;
     if (s.watch) {
@@ -689,6 +765,14 @@ int ifr_stressor_enqueue(ifr_ctx *ctx, const ifr_stressor_cfg *cfg, cudaStream_t
                 case 2: fma_stress_kernel<2><<<grid, blk, 0, stream>>>(s.d_state, p); break;
                 case 4: fma_stress_kernel<4><<<grid, blk, 0, stream>>>(s.d_state, p); break;
                 default: fma_stress_kernel<8><<<grid, blk, 0, stream>>>(s.d_state, p); break;
+            }
+            break;
+        case IFR_S_FP64:
+            switch (p.ilp) {
+                case 1: fp64_stress_kernel<1><<<grid, blk, 0, stream>>>(s.d_state, p); break;
+                case 2: fp64_stress_kernel<2><<<grid, blk, 0, stream>>>(s.d_state, p); break;
+                case 4: fp64_stress_kernel<4><<<grid, blk, 0, stream>>>(s.d_state, p); break;
+                default: fp64_stress_kernel<8><<<grid, blk, 0, stream>>>(s.d_state, p); break;
             }
             break;
         case IFR_S_SMEM_CF:

@@ -238,6 +238,98 @@ extern "C" int ifr_corun(ifr_ctx *ctx, const ifr_victim_cfg *victim, const ifr_v
     return IFR_OK;
 }
 
+namespace {
+// Holds its stream for `ns` of %globaltimer (bounded), so that work enqueued on
+// other streams behind an event recorded after it is released at one instant.
+__global__ void gate_kernel(uint64_t ns) {
+    if (threadIdx.x != 0) return;
+    const uint64_t t0 = ifr_gtimer();
+    uint32_t it = 0;
+    while (ifr_gtimer() - t0 < ns && ++it < (1u << 22)) __nanosleep(1000);
+}
+
+double span_ns(const ifr_stressor_result &r) {
+    return r.t_end_ns > r.t_start_ns ? (double)(r.t_end_ns - r.t_start_ns) : 0.0;
+}
+
+// One fixed-work stressor run on `stream` in a fresh slot; fills *out.
+int run_fixed(ifr_ctx *ctx, const ifr_stressor_cfg *cfg, cudaStream_t stream, ifr_stressor_result *out) {
+    const int slot = ifr_slot_alloc(ctx);
+    if (slot < 0) return slot;
+    ctx->slots[slot].watch = 0;
+    int rc = ifr_stressor_enqueue(ctx, cfg, stream, slot);
+    if (rc) return rc;
+    rc = wait_event_bounded(ctx->slots[slot].ev_end, 60000);
+    if (!rc) rc = ifr_stressor_collect(ctx, slot);
+    if (!rc) *out = ctx->slots[slot].result;
+    ctx->slots[slot].in_use = 0;
+    return rc;
+}
+}  // namespace
+
+extern "C" int ifr_stressor_pair(ifr_ctx *ctx, const ifr_stressor_cfg *a, const ifr_stressor_cfg *b,
+                                 ifr_pair_result *out) {
+    if (!ctx || !a || !b || !out) return IFR_ERR_ARG;
+    if (a->max_rounds <= 0 || b->max_rounds <= 0 || a->kind == IFR_S_SCHED || b->kind == IFR_S_SCHED)
+        return IFR_ERR_ARG;
+    memset(out, 0, sizeof *out);
+    IFR_CUDA(cudaDeviceSynchronize());
+    int rc = run_fixed(ctx, a, ctx->s_stress, &out->solo_a);
+    if (!rc) rc = run_fixed(ctx, b, ctx->s_stress, &out->solo_b);
+    if (rc) return rc;
+    // co-run: both streams wait behind a 300 us gate, then run their reset and kernel
+    const int sa = ifr_slot_alloc(ctx);
+    if (sa < 0) return sa;
+    ctx->slots[sa].watch = 0;
+    ctx->slots[sa].in_use = 1;  // reserve while the second slot is chosen
+    const int sb = ifr_slot_alloc(ctx);
+    ctx->slots[sa].in_use = 0;
+    if (sb < 0) return sb;
+    ctx->slots[sb].watch = 0;
+    ifr_carveout((const void *)gate_kernel);
+    gate_kernel<<<1, 32, 0, ctx->s_ctrl>>>(300000ull);
+    IFR_CUDA(cudaGetLastError());
+    ctx->kernel_launches += 1;
+    IFR_CUDA(cudaEventRecord(ctx->ev_a, ctx->s_ctrl));
+    IFR_CUDA(cudaStreamWaitEvent(ctx->s_stress, ctx->ev_a, 0));
+    IFR_CUDA(cudaStreamWaitEvent(ctx->s_victim, ctx->ev_a, 0));
+    rc = ifr_stressor_enqueue(ctx, a, ctx->s_stress, sa);
+    if (rc) return rc;
+    rc = ifr_stressor_enqueue(ctx, b, ctx->s_victim, sb);
+    if (rc) {
+        wait_event_bounded(ctx->slots[sa].ev_end, 60000);
+        ctx->slots[sa].in_use = 0;
+        return rc;
+    }
+    int rc1 = wait_event_bounded(ctx->slots[sa].ev_end, 60000);
+    int rc2 = wait_event_bounded(ctx->slots[sb].ev_end, 60000);
+    if (!rc1) rc1 = ifr_stressor_collect(ctx, sa);
+    if (!rc2) rc2 = ifr_stressor_collect(ctx, sb);
+    out->co_a = ctx->slots[sa].result;
+    out->co_b = ctx->slots[sb].result;
+    ctx->slots[sa].in_use = 0;
+    ctx->slots[sb].in_use = 0;
+    if (rc1) return rc1;
+    if (rc2) return rc2;
+    out->solo_a_ns = span_ns(out->solo_a);
+    out->solo_b_ns = span_ns(out->solo_b);
+    out->co_a_ns = span_ns(out->co_a);
+    out->co_b_ns = span_ns(out->co_b);
+    out->seq_ns = out->solo_a_ns + out->solo_b_ns;
+    const uint64_t t0 = out->co_a.t_start_ns < out->co_b.t_start_ns ? out->co_a.t_start_ns : out->co_b.t_start_ns;
+    const uint64_t t1 = out->co_a.t_end_ns > out->co_b.t_end_ns ? out->co_a.t_end_ns : out->co_b.t_end_ns;
+    out->col_ns = t1 > t0 ? (double)(t1 - t0) : 0.0;
+    out->overlapped = out->co_a.t_start_ns < out->co_b.t_end_ns && out->co_b.t_start_ns < out->co_a.t_end_ns;
+    const int32_t sts[4] = {out->solo_a.status, out->solo_b.status, out->co_a.status, out->co_b.status};
+    out->status = IFR_OK;
+    for (int i = 0; i < 4; ++i)
+        if (sts[i] != IFR_OK) {
+            out->status = sts[i];
+            break;
+        }
+    return IFR_OK;
+}
+
 extern "C" int ifr_sweep(ifr_ctx *ctx, const ifr_sweep_plan *p, ifr_cell_result *cells, size_t cap, size_t *n_out) {
     if (!ctx || !p || !n_out || p->n_victims <= 0 || !p->victims || p->n_stressors < 0 ||
         p->n_stressors > IFR_MAX_STRESSORS || p->n_levels < 0 || p->n_levels > IFR_MAX_LEVELS || p->repeats <= 0)

@@ -1,0 +1,328 @@
+"""The paper's characterisation experiments, re-run on B300 with the library's kernels.
+
+    python -m paper_2501_16909_b300.experiments [names ...] [--repeats R] [--out results.json]
+
+Each experiment is the B300 counterpart of one measurement of the paper, built from
+the library's stressors and victims through the C ABI (no vLLM, cuBLAS or MPS):
+
+  pitfall1  Sec. 3, Pitfall 1: two compute kernels of one 128-thread block per SM
+            (the paper's 6.25 % achieved occupancy): (a) one of them squeezed onto
+            6.25 % of the SMs with the same total work, (b) both colocated on all SMs.
+  pitfall2  Sec. 3, Pitfall 2: a compute kernel (one 512-thread block per SM, ILP 8:
+            four warps per sub-partition, enough to issue an FFMA every cycle) beside a
+            copy kernel over 4 GiB (one 1024-thread block per SM) with similar solo
+            time: each one's slowdown and the compute kernel's issue rate.  The paper
+            used 1024 threads for both; here that would need 73 728 registers per SM
+            (40 + 32 per thread), so the pair could not share an SM at all.
+  ipc       Sec. 4.4.2, Table 2: the compute kernel at S1..S4 (ILP 1, 2, 4, 8; one
+            128-thread block per SM) beside memory-bound victims: its solo issue rate
+            and each victim's slowdown.
+  fp64      Sec. 4.4.3, Table 3: two fp64 compute kernels at S1..S4 (ILP 1..4, one
+            128-thread block per SM): solo fp64-pipe utilisation and issue rate, and
+            the speedup of running them together over running them back to back.
+  l2        Sec. 4.3, Fig. 3: two copy kernels on disjoint SM halves over growing
+            per-instance data: one kernel's slowdown against alone, and its solo rate.
+  smem      Sec. 4.4.1, Fig. 4: BF16 GEMM victims (1024^3, 2048^3, 4096^3) beside the
+            n-strided shared-memory stressor, n = 1, 2, 4, ..., 32: slowdown per n.
+
+Issue rates are warp instructions of the kernel's arithmetic (FFMA or DMUL) per cycle
+per SM at the maximum SM clock; the loop's few other instructions are not counted.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import torch  # noqa: E402
+
+import ifr_inputs as I  # noqa: E402
+
+from . import _abi as A  # noqa: E402
+from . import peaks as P  # noqa: E402
+from . import stressor_cfg, victim_cfg  # noqa: E402
+
+GiB = 1 << 30
+MiB = 1 << 20
+
+
+# ----------------------------------------------------------------------------- helpers
+def mask_bits(sm_ids):
+    """ifr_stressor_cfg.sm_mask words for a set of SM ids (mask_mode 2)."""
+    words = [0] * (A.IFR_MAX_SMS // 32)
+    for s in sm_ids:
+        words[s >> 5] |= 1 << (s & 31)
+    return words
+
+
+def with_mask(cfg, sm_ids):
+    ids = sorted(set(sm_ids))
+    cfg.mask_mode = 2
+    cfg.sm_count = len(ids)
+    for i, w in enumerate(mask_bits(ids)):
+        cfg.sm_mask[i] = w
+    return cfg
+
+
+def issue_rate(rate_ops, S, clk_hz):
+    """Warp instructions per cycle per SM for `rate_ops` thread-level operations per s."""
+    return rate_ops / 32.0 / (S * clk_hz)
+
+
+def pair_stats(runs):
+    """Medians over repeated ifr_stressor_pair results."""
+    med = lambda k: statistics.median(r[k] for r in runs)
+    return {
+        "solo_a_us": med("solo_a_ns") / 1e3, "solo_b_us": med("solo_b_ns") / 1e3,
+        "co_a_us": med("co_a_ns") / 1e3, "co_b_us": med("co_b_ns") / 1e3,
+        "slowdown_a": statistics.median(r["co_a_ns"] / r["solo_a_ns"] for r in runs),
+        "slowdown_b": statistics.median(r["co_b_ns"] / r["solo_b_ns"] for r in runs),
+        "speedup_seq_over_col": statistics.median(r["seq_ns"] / r["col_ns"] for r in runs),
+        "all_overlapped": all(r["overlapped"] for r in runs),
+        "all_ok": all(r["status"] == A.IFR_OK for r in runs),
+    }
+
+
+def run_pair(ctx, a, b, repeats):
+    return pair_stats([ctx.stressor_pair(a, b) for _ in range(repeats)])
+
+
+def fixed_span_us(ctx, cfg):
+    res, _ = ctx.run_stressor(cfg, 30000)
+    return (res["t_end_ns"] - res["t_start_ns"]) / 1e3, res
+
+
+def slowdowns_from_cells(cells, n_victims, n_levels):
+    """Per victim: [slowdown at level 0..n_levels] = median measured time / median solo."""
+    per = lambda t: (t.t_end_ns - t.t_start_ns) / max(1, t.repeats)
+    out = []
+    for v in range(n_victims):
+        solo = [per(c.timing) for c in cells if c.victim == v and c.stressor < 0 and c.valid]
+        t0 = statistics.median(solo)
+        row = []
+        for lv in range(n_levels + 1):
+            xs = [per(c.timing) for c in cells if c.victim == v and c.stressor == 0 and c.level == lv and c.valid]
+            row.append(round(statistics.median(xs) / t0, 3) if xs else None)
+        out.append({"solo_us": round(t0 / 1e3, 2), "slowdown": row})
+    return out
+
+
+# ----------------------------------------------------------------------------- experiments
+def exp_pitfall1(ctx, repeats):
+    S = ctx.info["num_sms"]
+    rounds = 64
+    base = dict(block=128, blocks_per_sm=1, ilp=4, max_rounds=rounds)
+    full = stressor_cfg(A.IFR_S_FMA, sm_count=S, seed=1, **base)
+    t_full = statistics.median(fixed_span_us(ctx, full)[0] for _ in range(repeats))
+    # (a) the same S blocks' work on 6.25 % of the SMs, 16 blocks per SM (2048 threads)
+    n = max(1, round(0.0625 * S))
+    bps = min(16, math.ceil(S / n))
+    sq_rounds = max(1, round(rounds * S / (n * bps)))
+    squeezed = stressor_cfg(A.IFR_S_FMA, sm_count=n, seed=1, block=128, blocks_per_sm=bps, ilp=4,
+                            max_rounds=sq_rounds)
+    t_sq = statistics.median(fixed_span_us(ctx, squeezed)[0] for _ in range(repeats))
+    work_ratio = (n * bps * sq_rounds) / (S * rounds)
+    # (b) two instances on all SMs
+    other = stressor_cfg(A.IFR_S_FMA, sm_count=S, seed=2, **base)
+    pr = run_pair(ctx, full, other, repeats)
+    return {
+        "experiment": "pitfall1", "paper": "Sec. 3 Pitfall 1 (H100: 8.57x squeezed, 1.73x colocated)",
+        "kernel": "FMA chains, ILP 4, one 128-thread block per SM (4 of 64 warps: 6.25 % occupancy)",
+        "full_sms_us": round(t_full, 1),
+        "squeezed": {"sms": n, "blocks_per_sm": bps, "rounds": sq_rounds, "work_ratio": round(work_ratio, 4),
+                     "us": round(t_sq, 1), "latency_increase": round(t_sq / t_full / work_ratio, 3)},
+        "colocated": pr,
+    }
+
+
+def exp_pitfall2(ctx, repeats, hbm_buf):
+    S = ctx.info["num_sms"]
+    clk = ctx.info["sm_clock_khz"] * 1e3
+    copy = stressor_cfg(A.IFR_S_HBM, sm_count=S, blocks_per_sm=1, block=1024, buf=hbm_buf,
+                        working_set_bytes=hbm_buf.numel() * 4, seed=1, max_rounds=512)
+    t_copy, _ = fixed_span_us(ctx, copy)
+    comp = stressor_cfg(A.IFR_S_FMA, sm_count=S, blocks_per_sm=1, block=512, ilp=8, seed=3, max_rounds=4)
+    t_c, _ = fixed_span_us(ctx, comp)
+    comp.max_rounds = max(1, round(4 * t_copy / t_c))  # similar solo times, as in the paper
+    rate, _ = P.solo_rate(ctx, comp, rounds=comp.max_rounds)
+    pr = run_pair(ctx, comp, copy, repeats)
+    return {
+        "experiment": "pitfall2", "paper": "Sec. 3 Pitfall 2 (H100: copy latency doubles; compute IPC 3.99)",
+        "compute": "FMA chains, ILP 8, one 512-thread block per SM, %d rounds" % comp.max_rounds,
+        "copy": "stream read of a 4 GiB set, one 1024-thread block per SM, 512 rounds (5 GB)",
+        "compute_issue_rate": round(issue_rate(rate / 2, S, clk), 3),
+        "slowdown_compute": pr["slowdown_a"], "slowdown_copy": pr["slowdown_b"], "pair": pr,
+    }
+
+
+def _decode_victims():
+    t = {}
+    R = 8192
+    t["vA"] = I.torch_normal_bf16(13, R * R, "cuda").view(R, R)
+    t["vx"] = I.torch_normal_bf16(14, R, "cuda")
+    t["vy"] = torch.empty(R, device="cuda")
+    t["sx"] = I.torch_uniform_pm1(16, 2048 * 4096, "cuda").view(2048, 4096)
+    t["sy"] = torch.empty_like(t["sx"])
+    t["lx"] = I.torch_uniform_pm1(15, 16384 * 4096, "cuda").view(16384, 4096)
+    t["ly"] = torch.empty_like(t["lx"])
+    victims = [
+        ("gemv 8192x8192", victim_cfg(A.IFR_V_GEMV, t["vA"], t["vx"], t["vy"], m=R, k=R, repeats=16)),
+        ("softmax 2048x4096", victim_cfg(A.IFR_V_SOFTMAX, t["sx"], None, t["sy"], m=2048, n=4096, repeats=16)),
+        ("layernorm 16384x4096", victim_cfg(A.IFR_V_LAYERNORM, t["lx"], None, t["ly"], m=16384, n=4096, repeats=4)),
+    ]
+    return victims, t
+
+
+def exp_ipc(ctx, repeats):
+    S = ctx.info["num_sms"]
+    clk = ctx.info["sm_clock_khz"] * 1e3
+    victims, _t = _decode_victims()
+    ilps = [1, 2, 4, 8]
+    row = [stressor_cfg(A.IFR_S_FMA, sm_count=S, blocks_per_sm=1, block=128, ilp=i, seed=4, deadline_ns=2 * 10**9)
+           for i in ilps]
+    ipc = []
+    for c in row:
+        rate, _ = P.solo_rate(ctx, c, rounds=32)
+        ipc.append(round(issue_rate(rate / 2, S, clk), 3))
+    cells = ctx.sweep([v for _, v in victims], [row], repeats=repeats, batched=False)
+    sl = slowdowns_from_cells(cells, len(victims), len(row))
+    return {
+        "experiment": "ipc", "paper": "Sec. 4.4.2 Table 2 (RTX3090: compute IPC 1.18 / 2.06 / 2.9 / 3.45 for S1-S4)",
+        "scenarios": ["S%d (ILP %d)" % (i + 1, x) for i, x in enumerate(ilps)],
+        "compute_issue_rate": ipc,
+        "victims": [{"victim": name, **s} for (name, _), s in zip(victims, sl)],
+        "note": "slowdown[0] is the zero-SM stressor (harness only); slowdown[i] is scenario S_i",
+    }
+
+
+def exp_fp64(ctx, repeats, fp64_peak):
+    S = ctx.info["num_sms"]
+    clk = ctx.info["sm_clock_khz"] * 1e3
+    rows = []
+    for ilp in (1, 2, 4, 8):
+        a = stressor_cfg(A.IFR_S_FP64, sm_count=S, blocks_per_sm=1, block=128, ilp=ilp, seed=5, max_rounds=8)
+        b = stressor_cfg(A.IFR_S_FP64, sm_count=S, blocks_per_sm=1, block=128, ilp=ilp, seed=6, max_rounds=8)
+        rate, _ = P.solo_rate(ctx, a, rounds=8)
+        pr = run_pair(ctx, a, b, repeats)
+        rows.append({"ilp": ilp, "issue_rate": round(issue_rate(rate, S, clk), 4),
+                     "fp64_pipe_util": round(rate / fp64_peak, 4), "dmul_per_s": rate,
+                     "speedup_seq_over_col": round(pr["speedup_seq_over_col"], 3), "pair": pr})
+    return {
+        "experiment": "fp64", "paper": "Sec. 4.4.3 Table 3 (H100: util 24/48/69/91 %, speedup 1.93/1.87/1.33/1.03)",
+        "kernel": "fp64 multiply chains (__dmul_rn), one 128-thread block per SM, 8 rounds of 1024 multiplies",
+        "fp64_peak_dmul_per_s": fp64_peak,
+        "fp64_peak_per_sm_per_clock": round(fp64_peak / (S * clk), 3),
+        "scenarios": rows,
+    }
+
+
+def exp_l2(ctx, repeats):
+    S = ctx.info["num_sms"]
+    half = S // 2
+    ids_a, ids_b = list(range(half)), list(range(half, S))
+    sizes_mib = [1, 2, 4, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256]
+    top = sizes_mib[-1] * MiB
+    buf_a = I.torch_u32_as_i32(21, top // 4, "cuda")
+    buf_b = I.torch_u32_as_i32(22, top // 4, "cuda")
+    out = []
+    for mib in sizes_mib:
+        nb = mib * MiB
+        per_round = half * 4 * 16 * 1024  # 4 chunks of 16 B x 1024 threads per block per round
+        rounds = max(256, math.ceil(8 * nb / per_round))
+        a = with_mask(stressor_cfg(A.IFR_S_L2, blocks_per_sm=1, block=1024, buf=buf_a, working_set_bytes=nb,
+                                   seed=1, max_rounds=rounds), ids_a)
+        b = with_mask(stressor_cfg(A.IFR_S_L2, blocks_per_sm=1, block=1024, buf=buf_b, working_set_bytes=nb,
+                                   seed=2, max_rounds=rounds), ids_b)
+        pr = run_pair(ctx, a, b, repeats)
+        bytes_a = half * rounds * 4 * 16 * 1024
+        out.append({"mib_per_instance": mib, "rounds": rounds, "slowdown_a": round(pr["slowdown_a"], 3),
+                    "slowdown_b": round(pr["slowdown_b"], 3),
+                    "solo_a_gbs": round(bytes_a / (pr["solo_a_us"] * 1e3), 1),
+                    "co_a_gbs": round(bytes_a / (pr["co_a_us"] * 1e3), 1), "ok": pr["all_ok"],
+                    "overlapped": pr["all_overlapped"]})
+    return {
+        "experiment": "l2", "paper": "Sec. 4.3 Fig. 3 (H100, 50 MB L2: no slowdown <= 8 MB, peak 2.15x at 16 MB, "
+                                     "~1.12x beyond 26 MB)",
+        "kernels": "stream read (XOR fold) of its own set, one 1024-thread block per SM; instance A on SM ids "
+                   "0..%d, B on %d..%d (disjoint, mask_mode 2)" % (half - 1, half, S - 1),
+        "l2_bytes": ctx.info["l2_bytes"], "sizes": out,
+    }
+
+
+def exp_smem(ctx, repeats):
+    S = ctx.info["num_sms"]
+    victims, keep = [], []
+    for dim, k in ((1024, 64), (2048, 16), (4096, 4)):
+        a = I.torch_normal_bf16(31, dim * dim, "cuda").view(dim, dim)
+        b = I.torch_normal_bf16(32, dim * dim, "cuda").view(dim, dim)
+        c = torch.empty(dim, dim, device="cuda")
+        keep += [a, b, c]
+        victims.append(("gemm %d^3" % dim, victim_cfg(A.IFR_V_GEMM, a, b, c, m=dim, n=dim, k=dim, repeats=k)))
+    ways = [1, 2, 4, 8, 16, 32]
+    row = [stressor_cfg(A.IFR_S_SMEM_32W, sm_count=S, blocks_per_sm=2, block=256, smem_ways=w, seed=7)
+           for w in ways]
+    cells = ctx.sweep([v for _, v in victims], [row], repeats=repeats, batched=False)
+    sl = slowdowns_from_cells(cells, len(victims), len(row))
+    return {
+        "experiment": "smem", "paper": "Sec. 4.4.1 Fig. 4 (H100 torch.mm: 1.79x at dims 2048, 3.75x at dims 1024, "
+                                       "32-way)",
+        "stressor": "n-strided shared-memory ld/st, 2 blocks of 256 threads on every SM",
+        "ways": ways,
+        "victims": [{"victim": name, **s} for (name, _), s in zip(victims, sl)],
+        "note": "slowdown[0] is the zero-SM stressor (harness only); slowdown[i] is n = ways[i-1]",
+    }
+
+
+NAMES = ["pitfall1", "pitfall2", "ipc", "fp64", "l2", "smem"]
+
+
+def main(argv=None):
+    import paper_2501_16909_b300 as ifr
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("names", nargs="*", default=NAMES)
+    ap.add_argument("--repeats", type=int, default=3)
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args(argv)
+    bad = [n for n in a.names if n not in NAMES]
+    if bad:
+        raise SystemExit("unknown experiment(s) %s; choose from %s" % (bad, NAMES))
+    ctx = ifr.Context(0)
+    results = []
+    pk = None
+    hbm = None
+    for name in a.names:
+        t0 = time.perf_counter()
+        if name == "pitfall1":
+            r = exp_pitfall1(ctx, a.repeats)
+        elif name == "pitfall2":
+            hbm = hbm if hbm is not None else I.torch_u32_as_i32(1, (4 * GiB) // 4, "cuda")
+            r = exp_pitfall2(ctx, a.repeats, hbm)
+        elif name == "ipc":
+            r = exp_ipc(ctx, a.repeats)
+        elif name == "fp64":
+            pk = pk or P.peaks(ctx)
+            r = exp_fp64(ctx, a.repeats, pk[A.IFR_S_FP64][0])
+        elif name == "l2":
+            r = exp_l2(ctx, a.repeats)
+        else:
+            r = exp_smem(ctx, a.repeats)
+        r["seconds"] = round(time.perf_counter() - t0, 2)
+        results.append(r)
+        print(json.dumps(r), flush=True)
+    if a.out:
+        with open(a.out, "w") as f:
+            json.dump(results, f, indent=1)
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -11,6 +11,8 @@ provides the peaks:
 * tensor     flop/s  — MEASURED_PEAKS.json `bf16_tflops` (cuBLAS bf16 burst)
 * shared mem wavefronts/s — SMs x 1 wavefront per clock x max SM clock
 * scheduler  blocks/s — probe: zero-cycle 32-thread blocks on every SM
+* FP64       flop/s  — probe: best fp64 multiply-chain rate on every SM over
+                        occupancy and ILP (one multiply = one flop)
 """
 from __future__ import annotations
 
@@ -24,10 +26,10 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 TILE_MMA_FLOP = 2 * 128 * 128 * 64
 FMA_STEPS = 4096
 UNIT = {A.IFR_S_HBM: "B", A.IFR_S_L2: "B", A.IFR_S_FMA: "flop", A.IFR_S_TENSOR: "flop", A.IFR_S_SMEM_CF: "wavefront",
-        A.IFR_S_SMEM_32W: "wavefront", A.IFR_S_SCHED: "block"}
+        A.IFR_S_SMEM_32W: "wavefront", A.IFR_S_SCHED: "block", A.IFR_S_FP64: "flop"}
 # fixed-work rounds of one calibration run per kind (about a millisecond at full SMs)
 CAL_ROUNDS = {A.IFR_S_HBM: 64, A.IFR_S_L2: 256, A.IFR_S_FMA: 32, A.IFR_S_TENSOR: 32, A.IFR_S_SMEM_CF: 64,
-              A.IFR_S_SMEM_32W: 32, A.IFR_S_SCHED: 0}
+              A.IFR_S_SMEM_32W: 32, A.IFR_S_SCHED: 0, A.IFR_S_FP64: 16}
 
 
 def measured_peaks():
@@ -54,6 +56,8 @@ def work_units(cfg, res):
         return w * block * 64
     if k == A.IFR_S_FMA:
         return w * block * (cfg.ilp or 4) * 2
+    if k == A.IFR_S_FP64:
+        return w * block * (cfg.ilp or 4)
     if k == A.IFR_S_TENSOR:
         return w * TILE_MMA_FLOP
     if k in (A.IFR_S_SMEM_CF, A.IFR_S_SMEM_32W):
@@ -109,6 +113,14 @@ def peaks(ctx, l2_buf=None):
                     best = (rate, "probe: best stream-kernel rate over 8 / 16 MiB L2-resident sets and 2 / 4 "
                                   "blocks of 512 on every SM (%d MiB, %d blocks)" % (nb >> 20, bps))
         out[A.IFR_S_L2] = best
+    best = (0.0, "")
+    for bps, ilp in ((4, 4), (8, 4), (4, 8), (8, 8)):
+        cfg = stressor_cfg(A.IFR_S_FP64, sm_count=S, blocks_per_sm=bps, block=256, ilp=ilp)
+        rate, _ = solo_rate(ctx, cfg, rounds=8)
+        if rate > best[0]:
+            best = (rate, "probe: best fp64 multiply-chain rate over 4 / 8 blocks of 256 and ILP 4 / 8 on every "
+                          "SM (%d blocks, ILP %d)" % (bps, ilp))
+    out[A.IFR_S_FP64] = best
     cfg = stressor_cfg(A.IFR_S_SCHED, sm_count=S, sched_blocks=100000, sched_cycles=1)
     rate, _ = solo_rate(ctx, cfg, launches=8)
     out[A.IFR_S_SCHED] = (rate, "probe: 1-cycle 32-thread blocks on every SM")

@@ -80,6 +80,8 @@ STRESSOR_DEFAULTS = {
     A.IFR_S_SMEM_32W: dict(block=256, blocks_per_sm=2),
     A.IFR_S_L2: dict(block=512, blocks_per_sm=2),
     A.IFR_S_HBM: dict(block=512, blocks_per_sm=2),
+    # the paper's fp64 compute kernel shape (Sec. 4.4.3): one 128-thread block per SM
+    A.IFR_S_FP64: dict(block=128, blocks_per_sm=1, ilp=4),
 }
 
 VICTIM_LAUNCHES = {A.IFR_V_GEMM: 4, A.IFR_V_GEMV: 16, A.IFR_V_LAYERNORM: 4, A.IFR_V_SOFTMAX: 4, A.IFR_V_HIST: 8,

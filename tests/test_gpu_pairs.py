@@ -1,0 +1,124 @@
+"""FP64 stressor parity (Sec. 4.4.3), explicit SM masks (the disjoint partitions of
+Sec. 4.3's inter-SM runs) and ifr_stressor_pair (the kernel-against-kernel runs of
+Sec. 3, Sec. 4.3 and Table 3), through the C ABI."""
+import pytest
+
+import oracle
+from oracle import reduction as R
+import paper_2501_16909_b300 as ifr
+from paper_2501_16909_b300 import _abi as A
+from paper_2501_16909_b300.experiments import with_mask
+from tests.gpu_common import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+FP64_WORK = 1024  # multiplies per thread per round
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    need_gpu()
+    c = ifr.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("ilp", [1, 2, 4, 8])
+def test_fp64_block_checksums_match_oracle(ctx, ilp):
+    block, sms, rounds, seed = 64, 6, 2, 9 + ilp
+    cfg = ifr.stressor_cfg(A.IFR_S_FP64, sm_count=sms, blocks_per_sm=1, block=block, ilp=ilp, seed=seed,
+                           max_rounds=rounds)
+    res, logs = ctx.run_stressor(cfg)
+    assert res["status"] == A.IFR_OK
+    assert len(logs) == sms
+    steps = FP64_WORK // ilp
+    for L in logs:
+        assert L["work"] == rounds * steps
+        assert (L["checksum"], L["checksum2"]) == oracle.fp64_block(seed, L["index"], block, ilp, steps, rounds)
+
+
+def test_fp64_ragged_block_and_many_rounds(ctx):
+    # a block size that is not a power of two, and more rounds than the fold period
+    block, rounds, seed = 96, 5, 77
+    cfg = ifr.stressor_cfg(A.IFR_S_FP64, sm_count=3, blocks_per_sm=2, block=block, ilp=4, seed=seed,
+                           max_rounds=rounds)
+    res, logs = ctx.run_stressor(cfg)
+    assert res["status"] == A.IFR_OK and len(logs) == 6
+    for L in logs:
+        assert (L["checksum"], L["checksum2"]) == oracle.fp64_block(seed, L["index"], block, 4, FP64_WORK // 4, rounds)
+
+
+def test_explicit_mask_confines_blocks(ctx):
+    S = ctx.info["num_sms"]
+    ids = [0, 3, 17, S - 1]
+    cfg = with_mask(ifr.stressor_cfg(A.IFR_S_FMA, blocks_per_sm=2, block=128, ilp=4, seed=1, max_rounds=2), ids)
+    res, logs = ctx.run_stressor(cfg)
+    assert res["status"] == A.IFR_OK
+    assert {L["smid"] for L in logs} == set(ids)
+    assert res["sms_used"] == len(ids) and res["blocks_active"] == 2 * len(ids)
+
+
+def test_explicit_mask_rejects_inconsistent_masks(ctx):
+    S = ctx.info["num_sms"]
+    cfg = with_mask(ifr.stressor_cfg(A.IFR_S_FMA, block=128, max_rounds=1), [1, 2])
+    cfg.sm_count = 3  # does not match the two bits set
+    with pytest.raises(ifr.IfrError) as e:
+        ctx.stressor_launch(cfg)
+    assert e.value.status == A.IFR_ERR_ARG
+    if S < A.IFR_MAX_SMS:
+        beyond = with_mask(ifr.stressor_cfg(A.IFR_S_FMA, block=128, max_rounds=1), [S])  # no such SM
+        with pytest.raises(ifr.IfrError) as e:
+            ctx.stressor_launch(beyond)
+        assert e.value.status == A.IFR_ERR_ARG
+    green = ifr.stressor_cfg(A.IFR_S_FMA, sm_count=4, block=128, max_rounds=1, mask_mode=1)
+    with pytest.raises(ifr.IfrError) as e:
+        ctx.stressor_launch(green)
+    assert e.value.status == A.IFR_ERR_UNSUPPORTED
+
+
+def test_pair_on_disjoint_halves(ctx):
+    S = ctx.info["num_sms"]
+    h = S // 2
+    a = with_mask(ifr.stressor_cfg(A.IFR_S_FMA, blocks_per_sm=1, block=128, ilp=4, seed=1, max_rounds=16), range(h))
+    b = with_mask(ifr.stressor_cfg(A.IFR_S_FMA, blocks_per_sm=1, block=128, ilp=4, seed=2, max_rounds=16),
+                  range(h, S))
+    r = ctx.stressor_pair(a, b)
+    assert r["status"] == A.IFR_OK and r["overlapped"] == 1
+    # the same fixed work gives the same checksums alone and together
+    assert r["co_a"]["checksum"] == r["solo_a"]["checksum"]
+    assert r["co_b"]["checksum"] == r["solo_b"]["checksum"]
+    assert {r["co_a"]["sms_used"], r["co_b"]["sms_used"]} == {h, S - h}
+    # arithmetic-only kernels on disjoint SMs do not interfere beyond noise
+    assert 0.8 < r["co_a_ns"] / r["solo_a_ns"] < 1.25
+    assert r["seq_ns"] == pytest.approx(r["solo_a_ns"] + r["solo_b_ns"])
+    assert r["col_ns"] >= max(r["co_a_ns"], r["co_b_ns"]) - 1.0
+    # two halves at once take about as long as one: speedup near 2
+    assert 1.5 < r["seq_ns"] / r["col_ns"] < 2.5
+    # spans and the seq/col speedup follow the oracle's reading of Table 3 on the raw stamps
+    for k in ("solo_a", "solo_b", "co_a", "co_b"):
+        assert r[k + "_ns"] == r[k]["t_end_ns"] - r[k]["t_start_ns"]
+    sp = R.corun_speedup(r["solo_a_ns"], r["solo_b_ns"], r["co_a"]["t_start_ns"], r["co_a"]["t_end_ns"],
+                         r["co_b"]["t_start_ns"], r["co_b"]["t_end_ns"])
+    assert r["seq_ns"] / r["col_ns"] == pytest.approx(sp, rel=1e-12)
+
+
+def test_pair_same_sms_fp64_speedup_bounded(ctx):
+    S = ctx.info["num_sms"]
+    a = ifr.stressor_cfg(A.IFR_S_FP64, sm_count=S, blocks_per_sm=1, block=128, ilp=4, seed=3, max_rounds=2)
+    b = ifr.stressor_cfg(A.IFR_S_FP64, sm_count=S, blocks_per_sm=1, block=128, ilp=4, seed=4, max_rounds=2)
+    r = ctx.stressor_pair(a, b)
+    assert r["status"] == A.IFR_OK and r["overlapped"] == 1
+    assert r["co_a"]["checksum"] == r["solo_a"]["checksum"]
+    # two identical kernels sharing every SM: no faster than twice, no slower than back to back
+    assert 0.8 < r["seq_ns"] / r["col_ns"] < 2.2
+
+
+def test_pair_rejects_unbounded_or_scheduler_kinds(ctx):
+    S = ctx.info["num_sms"]
+    bounded = ifr.stressor_cfg(A.IFR_S_FMA, sm_count=S, block=128, max_rounds=1)
+    unbounded = ifr.stressor_cfg(A.IFR_S_FMA, sm_count=S, block=128)
+    sched = ifr.stressor_cfg(A.IFR_S_SCHED, sm_count=S, max_rounds=1)
+    for a, b in ((bounded, unbounded), (sched, bounded)):
+        with pytest.raises(ifr.IfrError) as e:
+            ctx.stressor_pair(a, b)
+        assert e.value.status == A.IFR_ERR_ARG
