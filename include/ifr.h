@@ -103,7 +103,8 @@ typedef enum {
     IFR_S_L2 = 5,       /* streaming XOR read of an L2-resident buffer */
     IFR_S_HBM = 6,      /* streaming XOR read of an HBM-sized buffer */
     IFR_S_FP64 = 7,     /* dependent fp64 multiply chains (Sec. 4.4.3), ILP chains/thread */
-    IFR_S_COUNT = 8
+    IFR_S_SLEEP = 8,    /* blocks that hold their SM slot and sleep (Sec. 4.2 sleep kernel) */
+    IFR_S_COUNT = 9
 } ifr_stressor_kind;
 
 typedef struct {
@@ -116,8 +117,10 @@ typedef struct {
     int32_t ilp;             /* FMA / FP64: independent chains per thread (1,2,4,8; 0 = 4) */
     int32_t smem_ways;       /* SMEM: bank-conflict degree 1..32 power of 2 (0 = kind) */
     float duty;              /* active fraction of each period, (0, 1]; 0 or 1 = always */
-    int32_t period_ns;       /* duty-cycle period (0 = 100000) */
-    int64_t working_set_bytes; /* L2/HBM: bytes of buf streamed; multiple of block*64 */
+    int32_t period_ns;       /* duty-cycle period (0 = 100000); SLEEP: sleep per round */
+    int64_t working_set_bytes; /* L2/HBM: bytes of buf streamed; multiple of block*64.
+                                  SLEEP: dynamic shared memory held per block
+                                  (<= the device's opt-in limit per block - 1 KiB) */
     const void *buf;         /* L2/HBM: device buffer of >= working_set_bytes, 16-B aligned */
     uint64_t seed;           /* private seed for FMA / SMEM / TENSOR / SCHED values */
     int64_t max_rounds;      /* > 0: each block stops after this many rounds (fixed work);
@@ -138,7 +141,7 @@ typedef struct {
     uint32_t checksum;       /* XOR of the per-block checksums (SCHED: of all blocks) */
     int32_t status;          /* first error recorded by any block, or IFR_OK */
     uint64_t rounds;         /* rounds summed over active blocks (SCHED: working blocks) */
-    uint64_t work;           /* kind units: chunks (L2/HBM), FMA / FP64 steps/thread-chain,
+    uint64_t work;           /* kind units: chunks (L2/HBM), FMA / FP64 steps/thread-chain, rounds (SLEEP),
                                 smem ld/st pairs/lane, tile MMAs, busy blocks (SCHED) */
     uint64_t t_start_ns;     /* earliest active-block start (%globaltimer) */
     uint64_t t_start_last_ns;/* latest active-block start */
@@ -278,6 +281,31 @@ typedef struct {
  * stressor slots), IFR_ERR_TIMEOUT (a run did not finish within 60 s on the host),
  * IFR_ERR_CUDA.  A run whose blocks hit their deadline is reported in `status`. */
 int ifr_stressor_pair(ifr_ctx *ctx, const ifr_stressor_cfg *a, const ifr_stressor_cfg *b, ifr_pair_result *out);
+
+/* ---- a victim beside a fixed-work stressor, latency from release (Sec. 4.2) -- */
+/* The paper's block-scheduler experiment launches a sleep kernel and an LLM decode
+ * step together and reports the step's latency: a victim block that cannot fit next
+ * to the sleeping blocks waits for them to leave (head-of-line blocking).  Because
+ * such a victim starts late, its latency is counted from its release, not from its
+ * first block.  ifr_colocate runs the victim's K launches alone, the stressor (fixed
+ * work, max_rounds > 0, not IFR_S_SCHED) alone, and then the victim arriving at the
+ * running stressor: both streams leave a device-side gate together, the victim's
+ * stream waits (bounded, 200 ms) until every stressor block is resident, stamps its
+ * release and launches.  Alone, the release is the gate's end.  *_ns = last block
+ * exit - release (the stressor's from the gate). */
+typedef struct {
+    ifr_timing victim_solo, victim_co;        /* K victim launches alone / beside the stressor */
+    ifr_stressor_result stress_solo, stress_co;
+    double victim_solo_ns, victim_co_ns;      /* release to the victim's last block exit */
+    double stress_solo_ns, stress_co_ns;      /* release to the stressor's last block exit */
+    int32_t blocked;    /* 1 if no victim block started before a stressor block ended (left its SM) */
+    int32_t status;     /* first non-OK status of the four runs, else IFR_OK */
+} ifr_colocate_result;
+
+/* Errors: IFR_ERR_ARG (null pointer, max_rounds <= 0, IFR_S_SCHED, invalid
+ * configurations), IFR_ERR_CAPACITY, IFR_ERR_TIMEOUT (60 s host bound), IFR_ERR_CUDA. */
+int ifr_colocate(ifr_ctx *ctx, const ifr_stressor_cfg *stressor, const ifr_victim_cfg *victim,
+                 ifr_colocate_result *out);
 
 /* ---- solo kernel profiles (Sec. 2.2 metrics; Sec. 5.1 estimator inputs) -- */
 /* Static launch properties of the kernel a victim or stressor configuration

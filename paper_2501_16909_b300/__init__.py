@@ -193,6 +193,17 @@ class Context:
             d[k] = _struct_dict(getattr(r, k))
         return d
 
+    def colocate(self, stressor: ifr_stressor_cfg, victim: ifr_victim_cfg) -> dict:
+        """ifr_colocate: victim alone, stressor alone, both released together (latency from release)."""
+        self._sync()
+        r = _abi.ifr_colocate_result()
+        check(self._L.ifr_colocate(self._h, C.byref(stressor), C.byref(victim), C.byref(r)), "ifr_colocate")
+        nested = ("victim_solo", "victim_co", "stress_solo", "stress_co")
+        d = {k: getattr(r, k) for k, _ in r._fields_ if k not in nested}
+        for k in nested:
+            d[k] = _struct_dict(getattr(r, k))
+        return d
+
     # -- victims
     def victim_launch(self, cfg: ifr_victim_cfg, stream=None) -> dict:
         self._sync()

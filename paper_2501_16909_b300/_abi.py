@@ -30,8 +30,9 @@ IFR_MAX_LEVELS = 16
 IFR_MAX_SMS = 256
 
 # stressor kinds
-IFR_S_SCHED, IFR_S_FMA, IFR_S_TENSOR, IFR_S_SMEM_CF, IFR_S_SMEM_32W, IFR_S_L2, IFR_S_HBM, IFR_S_FP64 = range(8)
-STRESSOR_NAMES = ["sched", "fma", "tensor", "smem_cf", "smem_32w", "l2", "hbm", "fp64"]
+(IFR_S_SCHED, IFR_S_FMA, IFR_S_TENSOR, IFR_S_SMEM_CF, IFR_S_SMEM_32W, IFR_S_L2, IFR_S_HBM, IFR_S_FP64,
+ IFR_S_SLEEP) = range(9)
+STRESSOR_NAMES = ["sched", "fma", "tensor", "smem_cf", "smem_32w", "l2", "hbm", "fp64", "sleep"]
 # victim kinds
 IFR_V_TRIAD, IFR_V_GEMM, IFR_V_GEMV, IFR_V_LAYERNORM, IFR_V_SOFTMAX, IFR_V_HIST = range(6)
 VICTIM_NAMES = ["triad", "gemm", "gemv", "layernorm", "softmax", "hist"]
@@ -131,6 +132,14 @@ class ifr_pair_result(C.Structure):
     ]
 
 
+class ifr_colocate_result(C.Structure):
+    _fields_ = [
+        ("victim_solo", ifr_timing), ("victim_co", ifr_timing), ("stress_solo", ifr_stressor_result),
+        ("stress_co", ifr_stressor_result), ("victim_solo_ns", C.c_double), ("victim_co_ns", C.c_double),
+        ("stress_solo_ns", C.c_double), ("stress_co_ns", C.c_double), ("blocked", C.c_int32), ("status", C.c_int32),
+    ]
+
+
 class ifr_corun_result(C.Structure):
     _fields_ = [
         ("victim_solo", ifr_timing), ("corunner_solo", ifr_timing), ("victim_corun", ifr_timing),
@@ -154,7 +163,7 @@ class ifr_mlp(C.Structure):
 
 STRUCTS = [ifr_device_info, ifr_stressor_cfg, ifr_stressor_result, ifr_block_log, ifr_victim_cfg, ifr_timing,
            ifr_sweep_plan, ifr_cell_result, ifr_sensitivity_out, ifr_kernel_profile, ifr_mlp, ifr_corun_result,
-           ifr_pair_result]
+           ifr_pair_result, ifr_colocate_result]
 
 _lib = None
 
@@ -190,6 +199,7 @@ def load():
                                   P(ifr_sensitivity_out)]),
         "ifr_corun": (i32, [vp, P(ifr_victim_cfg), P(ifr_victim_cfg), i32, P(ifr_corun_result)]),
         "ifr_stressor_pair": (i32, [vp, P(ifr_stressor_cfg), P(ifr_stressor_cfg), P(ifr_pair_result)]),
+        "ifr_colocate": (i32, [vp, P(ifr_stressor_cfg), P(ifr_victim_cfg), P(ifr_colocate_result)]),
         "ifr_victim_profile": (i32, [vp, P(ifr_victim_cfg), P(ifr_kernel_profile)]),
         "ifr_stressor_profile": (i32, [vp, P(ifr_stressor_cfg), P(ifr_kernel_profile)]),
         "ifr_mlp_forward": (i32, [vp, P(ifr_mlp), vp]),

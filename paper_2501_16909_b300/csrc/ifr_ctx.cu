@@ -94,6 +94,9 @@ extern "C" int ifr_init(int device, ifr_ctx **out) {
     TRY(cudaMemset(c->d_progress, 0, sizeof(uint64_t)));
     rc = ifr_ensure_timing(c, 64);
     if (rc != IFR_OK) goto fail;
+    if ((rc = ifr_preload_stressors()) || (rc = ifr_preload_victims()) || (rc = ifr_preload_gemm()) ||
+        (rc = ifr_preload_sweep()) || (rc = ifr_preload_mlp()))
+        goto fail;
 #undef TRY
     *out = c;
     return IFR_OK;
@@ -175,6 +178,13 @@ int ifr_slot_prepare(ifr_ctx *ctx, int slot) {
         IFR_CUDA(cudaEventCreate(&s.ev_end));
         IFR_CUDA(cudaEventCreateWithFlags(&s.ev_reset, cudaEventDisableTiming));
     }
+    return IFR_OK;
+}
+
+int ifr_preload(const void *func) {
+    cudaFuncAttributes a;
+    IFR_CUDA(cudaFuncGetAttributes(&a, func));
+    ifr_carveout(func);
     return IFR_OK;
 }
 

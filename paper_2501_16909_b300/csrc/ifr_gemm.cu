@@ -326,3 +326,8 @@ int ifr_gemm_enqueue(ifr_ctx *ctx, const ifr_victim_cfg *c, cudaStream_t stream,
     if (c->n % 256 == 0) return launch_gemm<256>(c, stream, tm);
     return launch_gemm<128>(c, stream, tm);
 }
+
+int ifr_preload_gemm() {
+    int rc = ifr_preload((const void *)gemm_bf16_kernel<128>);
+    return rc ? rc : ifr_preload((const void *)gemm_bf16_kernel<256>);
+}

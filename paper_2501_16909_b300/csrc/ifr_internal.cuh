@@ -136,6 +136,15 @@ struct ifr_ctx {
 // that stressor and victim blocks can share an SM without a carveout switch
 // (the paper sets the same split for the same reason, Sec. 4.4.2).
 void ifr_carveout(const void *func);
+// Load a kernel now (and set its carveout).  With lazy module loading a kernel's
+// first launch can wait for the device to drain, which would hold a victim back
+// behind a running stressor; ifr_init therefore loads every kernel of the library.
+int ifr_preload(const void *func);
+int ifr_preload_stressors();
+int ifr_preload_victims();
+int ifr_preload_gemm();
+int ifr_preload_sweep();
+int ifr_preload_mlp();
 #define IFR_HOL_NS 50000000ull  // 50 ms without victim progress = head-of-line blocked
 
 // ---------------------------------------------------------------- internal API

@@ -322,3 +322,13 @@ extern "C" int ifr_adam_step(ifr_ctx *ctx, float *w, const float *g, float *m, f
     ctx->kernel_launches += 1;
     return IFR_OK;
 }
+
+int ifr_preload_mlp() {
+    const void *fns[] = {(const void *)mlp_gemm_kernel, (const void *)copy_bf16_kernel, (const void *)colsum_kernel,
+                         (const void *)mse_grad_kernel, (const void *)adam_kernel};
+    for (const void *f : fns) {
+        int rc = ifr_preload(f);
+        if (rc) return rc;
+    }
+    return IFR_OK;
+}

@@ -314,6 +314,44 @@ __global__ void __launch_bounds__(1024) fp64_stress_kernel(DevStress *st, Stress
     if (threadIdx.x == 0) write_log(p, st, c, round, (uint64_t)round * (kFp64Work / ILP), cs, cs2);
 }
 
+// ------------------------------------------------------------------ sleep
+// The sleep kernel of Sec. 4.2: each active block holds its SM slot (threads,
+// registers and `working_set_bytes` of dynamic shared memory) while thread 0 sleeps
+// `period_ns` per round; the other threads wait at the barrier.  No arithmetic, so
+// no checksum: work = rounds.
+__global__ void __launch_bounds__(1024) sleep_stress_kernel(DevStress *st, StressParams p) {
+    __shared__ int s_k;
+    __shared__ uint64_t s_t0;
+    __shared__ int s_go[2];
+    BlockCtl c;
+    if (!block_enter(st, p, c, &s_k, &s_t0)) return;
+    int64_t round = 0;
+    for (;; ++round) {
+        if (threadIdx.x == 0) {
+            int go = round_decision(st, p, round, c);
+            if (go) {
+                const uint64_t until = ifr_gtimer() + p.period_ns;
+                uint32_t it = 0;
+                uint64_t now;
+                while ((now = ifr_gtimer()) < until) {
+                    if (now >= c.deadline) {
+                        c.status = IFR_ERR_TIMEOUT;
+                        go = 0;
+                        break;
+                    }
+                    if (ifr_ld_volatile(&st->stop) || ++it > kMaxSpin) break;
+                    const uint64_t left = until - now;
+                    __nanosleep((unsigned)(left > 20000u ? 20000u : left));
+                }
+            }
+            s_go[round & 1] = go;
+        }
+        __syncthreads();
+        if (!s_go[round & 1]) break;
+    }
+    if (threadIdx.x == 0) write_log(p, st, c, round, (uint64_t)round, 0u, 0u);
+}
+
 // ------------------------------------------------------------------ shared memory
 // Lane l = g*WAYS + r, iteration j: bank = g + (32/WAYS)*(j % WAYS),
 // row = r + WAYS*(j / WAYS), word = 32*row + bank.  For a fixed j the WAYS lanes
@@ -507,11 +545,18 @@ __global__ void __launch_bounds__(32) sched_stress_kernel(DevStress *st, StressP
     }
 }
 
-__global__ void wait_resident_kernel(DevStress *st, uint32_t expected, uint64_t timeout_ns, DevTiming *tm) {
+// Residency wait on the victim stream.  A persistent stressor is resident once all
+// its planned SM slots are claimed (`planned` > 0): the occupancy-sized grid's surplus
+// blocks exit as soon as they arrive after that, and waiting for every one of them to
+// arrive was seen on B300 to hold the victim back until the stressor had finished.
+// Without planned slots (the zero-SM level, the scheduler stressor) it waits for
+// `expected` arrivals.
+__global__ void wait_resident_kernel(DevStress *st, uint32_t expected, uint32_t planned, uint64_t timeout_ns,
+                                     DevTiming *tm) {
     if (threadIdx.x != 0) return;
     const uint64_t t0 = ifr_gtimer();
     uint32_t it = 0;
-    while (ifr_ld_volatile(&st->arrived) < expected) {
+    while (planned > 0 ? ifr_ld_volatile(&st->active) < planned : ifr_ld_volatile(&st->arrived) < expected) {
         if (ifr_gtimer() - t0 > timeout_ns || ++it > kMaxSpin) {
             if (tm) tm->status = IFR_ERR_NOT_RESIDENT;
             break;
@@ -525,6 +570,7 @@ int kind_default_block(int kind) {
         case IFR_S_SCHED: return 32;
         case IFR_S_FMA: return 128;
         case IFR_S_FP64: return 128;
+        case IFR_S_SLEEP: return 128;
         case IFR_S_TENSOR: return 128;
         case IFR_S_SMEM_CF:
         case IFR_S_SMEM_32W: return 256;
@@ -554,6 +600,22 @@ const void *smem_fn() {
         attr = true;
     }
     return (const void *)smem_stress_kernel<W>;
+}
+
+// The sleep kernel may hold up to the device's opt-in shared memory per block.
+const void *sleep_fn() {
+    static bool attr = false;
+    if (!attr) {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        int static_bytes = 0;
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, sleep_stress_kernel) == cudaSuccess) static_bytes = (int)fa.sharedSizeBytes;
+        attr = cudaFuncSetAttribute(sleep_stress_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    optin - static_bytes) == cudaSuccess;
+    }
+    return (const void *)sleep_stress_kernel;
 }
 
 const void *smem_kernel_for(int ways) {
@@ -604,6 +666,10 @@ StressShape stressor_shape(int num_sms, const ifr_stressor_cfg *cfg) {
         case IFR_S_TENSOR:
             s.fn = (const void *)tensor_stress_kernel;
             s.smem = 32768 + 1024;
+            break;
+        case IFR_S_SLEEP:
+            s.fn = sleep_fn();
+            s.smem = (int)cfg->working_set_bytes;
             break;
         case IFR_S_SCHED:
             s.fn = (const void *)sched_stress_kernel;
@@ -682,6 +748,9 @@ static int validate_cfg(ifr_ctx *ctx, const ifr_stressor_cfg *c) {
     if (c->kind == IFR_S_TENSOR && ((c->block != 0 && c->block != 128) || c->blocks_per_sm > 2)) return IFR_ERR_ARG;
     if (c->kind == IFR_S_SCHED && (c->sched_blocks < 0 || c->sched_launches < 0 || c->sched_cycles < 0))
         return IFR_ERR_ARG;
+    if (c->kind == IFR_S_SLEEP &&
+        (c->working_set_bytes < 0 || c->working_set_bytes > ctx->info.smem_per_block_optin - 1024 || c->period_ns < 0))
+        return IFR_ERR_ARG;
     if (c->mask_mode == 1) return IFR_ERR_UNSUPPORTED;
     if (c->mask_mode == 2) {
         // explicit SM set: only ids of this device, exactly sm_count of them
@@ -741,7 +810,6 @@ int ifr_stressor_enqueue(ifr_ctx *ctx, const ifr_stressor_cfg *cfg, cudaStream_t
     s.planned = p.planned;
     s.launches = 1;
     const StressShape shape = stressor_shape(num_sms, cfg);
-    const void *fn = shape.fn;
     const size_t sh = (size_t)shape.smem;
     const int ways = shape.ways;
     s.grid = shape.grid;
@@ -791,6 +859,9 @@ int ifr_stressor_enqueue(ifr_ctx *ctx, const ifr_stressor_cfg *cfg, cudaStream_t
             s.block = 128;
             tensor_stress_kernel<<<grid, 128, sh, stream>>>(s.d_state, p);
             break;
+        case IFR_S_SLEEP:
+            sleep_stress_kernel<<<grid, blk, sh, stream>>>(s.d_state, p);
+            break;
         case IFR_S_SCHED: {
             p.sched_blocks = cfg->sched_blocks ? cfg->sched_blocks : 100000;
             p.sched_cycles = cfg->sched_cycles ? cfg->sched_cycles : 100;
@@ -818,7 +889,9 @@ int ifr_enqueue_wait_resident(ifr_ctx *ctx, int slot, cudaStream_t stream, DevTi
     // the wait must not start before the stressor's state reset (cross-stream edge)
     IFR_CUDA(cudaStreamWaitEvent(stream, s.ev_reset, 0));
     ifr_carveout((const void *)wait_resident_kernel);
-    wait_resident_kernel<<<1, 32, 0, stream>>>(s.d_state, (uint32_t)ifr_stressor_expected_arrivals(s), timeout_ns, tm);
+    const uint32_t planned = s.cfg.kind == IFR_S_SCHED ? 0u : (uint32_t)s.planned;
+    wait_resident_kernel<<<1, 32, 0, stream>>>(s.d_state, (uint32_t)ifr_stressor_expected_arrivals(s), planned,
+                                               timeout_ns, tm);
     IFR_CUDA(cudaGetLastError());
     ctx->kernel_launches += 1;
     return IFR_OK;
@@ -1040,5 +1113,21 @@ extern "C" int ifr_stream_stressor_noalloc(int kind, const void *buf, int64_t wo
     noalloc_logs_clear_kernel<<<(p.planned + 127) / 128, 128, 0, s>>>(logs_out, p.planned);
     stream_stress_kernel<<<grid, block, 0, s>>>(st, p);
     IFR_CUDA(cudaGetLastError());
+    return IFR_OK;
+}
+
+int ifr_preload_stressors() {
+    const void *fns[] = {
+        (const void *)stress_reset_kernel, (const void *)stream_stress_kernel,
+        (const void *)fma_stress_kernel<1>, (const void *)fma_stress_kernel<2>, (const void *)fma_stress_kernel<4>,
+        (const void *)fma_stress_kernel<8>, (const void *)fp64_stress_kernel<1>, (const void *)fp64_stress_kernel<2>,
+        (const void *)fp64_stress_kernel<4>, (const void *)fp64_stress_kernel<8>, smem_kernel_for(1),
+        smem_kernel_for(2), smem_kernel_for(4), smem_kernel_for(8), smem_kernel_for(16), smem_kernel_for(32),
+        (const void *)tensor_stress_kernel, (const void *)sched_stress_kernel, sleep_fn(),
+        (const void *)wait_resident_kernel, (const void *)noalloc_logs_clear_kernel};
+    for (const void *f : fns) {
+        int rc = ifr_preload(f);
+        if (rc) return rc;
+    }
     return IFR_OK;
 }

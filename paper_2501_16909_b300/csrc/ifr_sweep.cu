@@ -240,12 +240,31 @@ extern "C" int ifr_corun(ifr_ctx *ctx, const ifr_victim_cfg *victim, const ifr_v
 
 namespace {
 // Holds its stream for `ns` of %globaltimer (bounded), so that work enqueued on
-// other streams behind an event recorded after it is released at one instant.
-__global__ void gate_kernel(uint64_t ns) {
+// other streams behind an event recorded after it is released at one instant;
+// stamps the release time into *release when given.
+__global__ void gate_kernel(uint64_t ns, uint64_t *release) {
     if (threadIdx.x != 0) return;
     const uint64_t t0 = ifr_gtimer();
     uint32_t it = 0;
     while (ifr_gtimer() - t0 < ns && ++it < (1u << 22)) __nanosleep(1000);
+    if (release) *release = ifr_gtimer();
+}
+
+// Stamps %globaltimer into *release (the point from which a victim's latency counts).
+__global__ void stamp_kernel(uint64_t *release) {
+    if (threadIdx.x == 0) *release = ifr_gtimer();
+}
+
+// Enqueue the gate on the control stream and make `a` (and `b`, if given) wait for it.
+int enqueue_gate(ifr_ctx *ctx, cudaStream_t a, cudaStream_t b, uint64_t *release) {
+    ifr_carveout((const void *)gate_kernel);
+    gate_kernel<<<1, 32, 0, ctx->s_ctrl>>>(300000ull, release);
+    IFR_CUDA(cudaGetLastError());
+    ctx->kernel_launches += 1;
+    IFR_CUDA(cudaEventRecord(ctx->ev_a, ctx->s_ctrl));
+    IFR_CUDA(cudaStreamWaitEvent(a, ctx->ev_a, 0));
+    if (b) IFR_CUDA(cudaStreamWaitEvent(b, ctx->ev_a, 0));
+    return IFR_OK;
 }
 
 double span_ns(const ifr_stressor_result &r) {
@@ -286,13 +305,8 @@ extern "C" int ifr_stressor_pair(ifr_ctx *ctx, const ifr_stressor_cfg *a, const 
     ctx->slots[sa].in_use = 0;
     if (sb < 0) return sb;
     ctx->slots[sb].watch = 0;
-    ifr_carveout((const void *)gate_kernel);
-    gate_kernel<<<1, 32, 0, ctx->s_ctrl>>>(300000ull);
-    IFR_CUDA(cudaGetLastError());
-    ctx->kernel_launches += 1;
-    IFR_CUDA(cudaEventRecord(ctx->ev_a, ctx->s_ctrl));
-    IFR_CUDA(cudaStreamWaitEvent(ctx->s_stress, ctx->ev_a, 0));
-    IFR_CUDA(cudaStreamWaitEvent(ctx->s_victim, ctx->ev_a, 0));
+    rc = enqueue_gate(ctx, ctx->s_stress, ctx->s_victim, nullptr);
+    if (rc) return rc;
     rc = ifr_stressor_enqueue(ctx, a, ctx->s_stress, sa);
     if (rc) return rc;
     rc = ifr_stressor_enqueue(ctx, b, ctx->s_victim, sb);
@@ -321,6 +335,96 @@ extern "C" int ifr_stressor_pair(ifr_ctx *ctx, const ifr_stressor_cfg *a, const 
     out->col_ns = t1 > t0 ? (double)(t1 - t0) : 0.0;
     out->overlapped = out->co_a.t_start_ns < out->co_b.t_end_ns && out->co_b.t_start_ns < out->co_a.t_end_ns;
     const int32_t sts[4] = {out->solo_a.status, out->solo_b.status, out->co_a.status, out->co_b.status};
+    out->status = IFR_OK;
+    for (int i = 0; i < 4; ++i)
+        if (sts[i] != IFR_OK) {
+            out->status = sts[i];
+            break;
+        }
+    return IFR_OK;
+}
+
+extern "C" int ifr_colocate(ifr_ctx *ctx, const ifr_stressor_cfg *sc, const ifr_victim_cfg *vc,
+                            ifr_colocate_result *out) {
+    if (!ctx || !sc || !vc || !out) return IFR_ERR_ARG;
+    if (sc->max_rounds <= 0 || sc->kind == IFR_S_SCHED) return IFR_ERR_ARG;
+    int rc = ifr_victim_validate(ctx, vc);
+    if (rc) return rc;
+    memset(out, 0, sizeof *out);
+    rc = ifr_ensure_timing(ctx, 3);
+    if (rc) return rc;
+    IFR_CUDA(cudaDeviceSynchronize());
+    const int K = vc->repeats > 0 ? vc->repeats : 1;
+    DevTiming *tv = ctx->d_timing;
+    // scratch words past the measurements: gate end, victim release (co-run)
+    uint64_t *gate_t = (uint64_t *)(ctx->d_timing + 2), *vrel = gate_t + 1;
+    // mode 0: victim alone, 1: stressor alone, 2: victim arriving at the running stressor
+    for (int mode = 0; mode < 3; ++mode) {
+        const bool run_v = mode != 1, run_s = mode != 0;
+        if (run_v) {
+            rc = ifr_timing_reset(tv, 1, ctx->s_victim, nullptr);
+            if (rc) return rc;
+        }
+        rc = enqueue_gate(ctx, ctx->s_victim, ctx->s_stress, gate_t);
+        if (rc) return rc;
+        int slot = -1;
+        if (run_s) {
+            slot = ifr_slot_alloc(ctx);
+            if (slot < 0) return slot;
+            ctx->slots[slot].watch = 0;
+            rc = ifr_stressor_enqueue(ctx, sc, ctx->s_stress, slot);
+            if (rc) return rc;
+        }
+        if (run_v && run_s) {
+            // the victim arrives at a running stressor: every stressor block resident
+            // first (bounded wait, 200 ms), then the release stamp
+            rc = ifr_enqueue_wait_resident(ctx, slot, ctx->s_victim, tv, 200000000ull);
+            if (rc) return rc;
+            ifr_carveout((const void *)stamp_kernel);
+            stamp_kernel<<<1, 32, 0, ctx->s_victim>>>(vrel);
+            IFR_CUDA(cudaGetLastError());
+            ctx->kernel_launches += 1;
+        }
+        if (run_v) {
+            rc = ifr_victim_enqueue(ctx, vc, ctx->s_victim, tv);
+            if (!rc) rc = cudaEventRecord(ctx->ev_b, ctx->s_victim) == cudaSuccess ? IFR_OK : IFR_ERR_CUDA;
+        }
+        int rcv = run_v && !rc ? wait_event_bounded(ctx->ev_b, 60000) : IFR_OK;
+        int rcs = run_s ? wait_event_bounded(ctx->slots[slot].ev_end, 60000) : IFR_OK;
+        if (run_s && !rcs) rcs = ifr_stressor_collect(ctx, slot);
+        if (run_s) ctx->slots[slot].in_use = 0;
+        if (rc) return rc;
+        if (rcv) return rcv;
+        if (rcs) return rcs;
+        uint64_t stamps[2] = {0, 0};
+        IFR_CUDA(cudaMemcpy(stamps, gate_t, sizeof stamps, cudaMemcpyDeviceToHost));
+        const uint64_t rel = stamps[0], rel_v = run_s ? stamps[1] : stamps[0];
+        ifr_timing t;
+        memset(&t, 0, sizeof t);
+        if (run_v) {
+            rc = read_timing(ctx, 0, K, &t);
+            if (rc) return rc;
+        }
+        const ifr_stressor_result r = run_s ? ctx->slots[slot].result : ifr_stressor_result{};
+        const double tv_ns = run_v && t.t_end_ns > rel_v ? (double)(t.t_end_ns - rel_v) : 0.0;
+        const double ts_ns = run_s && r.t_end_ns > rel ? (double)(r.t_end_ns - rel) : 0.0;
+        if (mode == 0) {
+            out->victim_solo = t;
+            out->victim_solo_ns = tv_ns;
+        } else if (mode == 1) {
+            out->stress_solo = r;
+            out->stress_solo_ns = ts_ns;
+        } else {
+            out->victim_co = t;
+            out->stress_co = r;
+            out->victim_co_ns = tv_ns;
+            out->stress_co_ns = ts_ns;
+        }
+    }
+    // blocked: no victim block could start until a stressor block had left its SM
+    out->blocked = out->victim_co.t_start_ns >= out->stress_co.t_end_first_ns;
+    const int32_t sts[4] = {out->victim_solo.status, out->stress_solo.status, out->victim_co.status,
+                            out->stress_co.status};
     out->status = IFR_OK;
     for (int i = 0; i < 4; ++i)
         if (sts[i] != IFR_OK) {
@@ -463,4 +567,13 @@ extern "C" int ifr_sweep(ifr_ctx *ctx, const ifr_sweep_plan *p, ifr_cell_result 
         if (e) cudaGraphExecDestroy(e);
     *n_out = n;
     return rc;
+}
+
+int ifr_preload_sweep() {
+    const void *fns[] = {(const void *)wait_started_kernel, (const void *)gate_kernel, (const void *)stamp_kernel};
+    for (const void *f : fns) {
+        int rc = ifr_preload(f);
+        if (rc) return rc;
+    }
+    return IFR_OK;
 }

@@ -563,3 +563,16 @@ extern "C" int ifr_launch_count(ifr_ctx *ctx, uint64_t *out) {
     *out = ctx->kernel_launches;
     return IFR_OK;
 }
+
+int ifr_preload_victims() {
+    const void *fns[] = {
+        (const void *)timing_reset_kernel, (const void *)triad_kernel, (const void *)gemv_kernel,
+        (const void *)hist_kernel, (const void *)layernorm_kernel<256, 4>, (const void *)layernorm_kernel<256, 8>,
+        (const void *)layernorm_kernel<1024, 8>, (const void *)softmax_kernel<256, 4>,
+        (const void *)softmax_kernel<256, 8>, (const void *)softmax_kernel<1024, 8>};
+    for (const void *f : fns) {
+        int rc = ifr_preload(f);
+        if (rc) return rc;
+    }
+    return IFR_OK;
+}

@@ -24,6 +24,10 @@ the library's stressors and victims through the C ABI (no vLLM, cuBLAS or MPS):
             per-instance data: one kernel's slowdown against alone, and its solo rate.
   smem      Sec. 4.4.1, Fig. 4: BF16 GEMM victims (1024^3, 2048^3, 4096^3) beside the
             n-strided shared-memory stressor, n = 1, 2, 4, ..., 32: slowdown per n.
+  hol       Sec. 4.2, block-scheduler interference: a 10 ms sleep kernel (one 128-thread
+            block per SM) released together with victims of small and large per-block
+            footprints: victim latency from the release, alone and beside it, and
+            whether its first block had to wait for the sleep kernel to leave.
 
 Issue rates are warp instructions of the kernel's arithmetic (FFMA or DMUL) per cycle
 per SM at the maximum SM clock; the loop's few other instructions are not counted.
@@ -281,7 +285,60 @@ def exp_smem(ctx, repeats):
     }
 
 
-NAMES = ["pitfall1", "pitfall2", "ipc", "fp64", "l2", "smem"]
+def exp_hol(ctx, repeats):
+    S = ctx.info["num_sms"]
+    rounds, period = 100, 100_000  # 10 ms of sleep, as in the paper
+
+    def sleep(smem):
+        return stressor_cfg(A.IFR_S_SLEEP, sm_count=S, blocks_per_sm=1, block=128, period_ns=period,
+                            max_rounds=rounds, working_set_bytes=smem, seed=1)
+
+    keep = {}
+    R = 8192
+    keep["vA"] = I.torch_normal_bf16(13, R * R, "cuda").view(R, R)
+    keep["vx"] = I.torch_normal_bf16(14, R, "cuda")
+    keep["vy"] = torch.empty(R, device="cuda")
+    keep["s1"] = I.torch_uniform_pm1(16, 16384 * 4096, "cuda").view(16384, 4096)
+    keep["o1"] = torch.empty_like(keep["s1"])
+    keep["s2"] = I.torch_uniform_pm1(17, 4096 * 16384, "cuda").view(4096, 16384)
+    keep["o2"] = torch.empty_like(keep["s2"])
+    keep["gA"] = I.torch_normal_bf16(11, 4096 * 4096, "cuda").view(4096, 4096)
+    keep["gB"] = I.torch_normal_bf16(12, 4096 * 4096, "cuda").view(4096, 4096)
+    keep["gC"] = torch.empty(4096, 4096, device="cuda")
+    cases = [
+        ("gemv 8192x8192", 0, victim_cfg(A.IFR_V_GEMV, keep["vA"], keep["vx"], keep["vy"], m=R, k=R, repeats=16)),
+        ("softmax 16384x4096 (256-thread blocks)", 0,
+         victim_cfg(A.IFR_V_SOFTMAX, keep["s1"], None, keep["o1"], m=16384, n=4096, repeats=4)),
+        ("softmax 4096x16384 (1024-thread blocks)", 0,
+         victim_cfg(A.IFR_V_SOFTMAX, keep["s2"], None, keep["o2"], m=4096, n=16384, repeats=4)),
+        ("gemm 4096^3, sleep blocks hold no shared memory", 0,
+         victim_cfg(A.IFR_V_GEMM, keep["gA"], keep["gB"], keep["gC"], m=4096, n=4096, k=4096, repeats=4)),
+        ("gemm 4096^3, sleep blocks hold 96 KiB of shared memory", 96 * 1024,
+         victim_cfg(A.IFR_V_GEMM, keep["gA"], keep["gB"], keep["gC"], m=4096, n=4096, k=4096, repeats=4)),
+    ]
+    out = []
+    for name, smem, v in cases:
+        prof = ctx.victim_profile(v)
+        runs = [ctx.colocate(sleep(smem), v) for _ in range(repeats)]
+        med = lambda k: statistics.median(r[k] for r in runs)
+        out.append({
+            "victim": name, "block": prof["block"], "regs_per_thread": prof["regs_per_thread"],
+            "smem_per_block": prof["static_smem"] + prof["dynamic_smem"], "sleep_smem": smem,
+            "alone_us": round(med("victim_solo_ns") / 1e3, 1), "beside_sleep_us": round(med("victim_co_ns") / 1e3, 1),
+            "latency_ratio": round(med("victim_co_ns") / med("victim_solo_ns"), 3),
+            "blocked": sum(r["blocked"] for r in runs), "runs": len(runs),
+            "sleep_us": round(med("stress_co_ns") / 1e3, 1), "ok": all(r["status"] == A.IFR_OK for r in runs)})
+    sp = ctx.stressor_profile(sleep(0))
+    return {
+        "experiment": "hol", "paper": "Sec. 4.2 (H100: Llama3-8B decode TBT 7.53 -> 16.56 ms beside a 10 ms sleep "
+                                      "kernel; a 64512-register block cannot join a 2048-register sleep block)",
+        "sleep_kernel": "one 128-thread block per SM, %d registers per thread, %d x %d us" % (
+            sp["regs_per_thread"], rounds, period // 1000),
+        "victims": out,
+    }
+
+
+NAMES = ["pitfall1", "pitfall2", "ipc", "fp64", "l2", "smem", "hol"]
 
 
 def main(argv=None):
@@ -313,6 +370,8 @@ def main(argv=None):
             r = exp_fp64(ctx, a.repeats, pk[A.IFR_S_FP64][0])
         elif name == "l2":
             r = exp_l2(ctx, a.repeats)
+        elif name == "hol":
+            r = exp_hol(ctx, a.repeats)
         else:
             r = exp_smem(ctx, a.repeats)
         r["seconds"] = round(time.perf_counter() - t0, 2)

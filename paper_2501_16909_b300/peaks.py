@@ -26,10 +26,10 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 TILE_MMA_FLOP = 2 * 128 * 128 * 64
 FMA_STEPS = 4096
 UNIT = {A.IFR_S_HBM: "B", A.IFR_S_L2: "B", A.IFR_S_FMA: "flop", A.IFR_S_TENSOR: "flop", A.IFR_S_SMEM_CF: "wavefront",
-        A.IFR_S_SMEM_32W: "wavefront", A.IFR_S_SCHED: "block", A.IFR_S_FP64: "flop"}
+        A.IFR_S_SMEM_32W: "wavefront", A.IFR_S_SCHED: "block", A.IFR_S_FP64: "flop", A.IFR_S_SLEEP: "round"}
 # fixed-work rounds of one calibration run per kind (about a millisecond at full SMs)
 CAL_ROUNDS = {A.IFR_S_HBM: 64, A.IFR_S_L2: 256, A.IFR_S_FMA: 32, A.IFR_S_TENSOR: 32, A.IFR_S_SMEM_CF: 64,
-              A.IFR_S_SMEM_32W: 32, A.IFR_S_SCHED: 0, A.IFR_S_FP64: 16}
+              A.IFR_S_SMEM_32W: 32, A.IFR_S_SCHED: 0, A.IFR_S_FP64: 16, A.IFR_S_SLEEP: 10}
 
 
 def measured_peaks():
@@ -62,7 +62,7 @@ def work_units(cfg, res):
         return w * TILE_MMA_FLOP
     if k in (A.IFR_S_SMEM_CF, A.IFR_S_SMEM_32W):
         return w * (block // 32) * 2 * ways_of(cfg)
-    if k == A.IFR_S_SCHED:
+    if k in (A.IFR_S_SCHED, A.IFR_S_SLEEP):
         return w
     raise ValueError(k)
 

@@ -122,3 +122,48 @@ def test_pair_rejects_unbounded_or_scheduler_kinds(ctx):
         with pytest.raises(ifr.IfrError) as e:
             ctx.stressor_pair(a, b)
         assert e.value.status == A.IFR_ERR_ARG
+
+
+# ---------------------------------------------------------------- sleep kernel and ifr_colocate (Sec. 4.2)
+def _sleep(S, rounds, period_ns, smem=0):
+    return ifr.stressor_cfg(A.IFR_S_SLEEP, sm_count=S, blocks_per_sm=1, block=128, period_ns=period_ns,
+                            max_rounds=rounds, working_set_bytes=smem, seed=1)
+
+
+def test_sleep_stressor_rounds_and_span(ctx):
+    S = ctx.info["num_sms"]
+    res, logs = ctx.run_stressor(_sleep(S, 10, 20000))
+    assert res["status"] == A.IFR_OK and res["sms_used"] == S
+    assert all(L["rounds"] == 10 and L["work"] == 10 for L in logs)
+    assert all(L["t_end_ns"] - L["t_start_ns"] >= 10 * 20000 for L in logs)
+
+
+def test_colocate_small_victim_runs_beside_sleep(ctx):
+    import torch
+    import ifr_inputs as I
+    S = ctx.info["num_sms"]
+    A_ = I.torch_normal_bf16(41, 1024 * 4096, "cuda").view(1024, 4096)
+    x = I.torch_normal_bf16(42, 4096, "cuda")
+    y = torch.empty(1024, device="cuda")
+    v = ifr.victim_cfg(A.IFR_V_GEMV, A_, x, y, m=1024, k=4096, repeats=4)
+    r = ctx.colocate(_sleep(S, 20, 100000), v)  # 2 ms of sleep
+    assert r["status"] == A.IFR_OK and r["blocked"] == 0
+    assert r["victim_co_ns"] < 0.5 * r["stress_co_ns"]  # done long before the sleep kernel ends
+
+
+def test_colocate_register_file_victim_waits_for_sleep(ctx):
+    import torch
+    import ifr_inputs as I
+    S = ctx.info["num_sms"]
+    x = I.torch_uniform_pm1(43, 512 * 16384, "cuda").view(512, 16384)
+    y = torch.empty_like(x)
+    v = ifr.victim_cfg(A.IFR_V_SOFTMAX, x, None, y, m=512, n=16384, repeats=1)
+    vp, sp = ctx.victim_profile(v), ctx.stressor_profile(_sleep(S, 20, 100000))
+    regs = lambda p: p["block"] * (-(-p["regs_per_thread"] // 8) * 8)
+    # premise (Sec. 2.1): one victim block and one sleep block exceed the register file
+    assert regs(vp) + regs(sp) > ctx.info["regs_per_sm"]
+    r = ctx.colocate(_sleep(S, 20, 100000), v)
+    assert r["status"] == A.IFR_OK and r["blocked"] == 1
+    assert r["victim_co"]["t_start_ns"] >= r["stress_co"]["t_end_first_ns"]
+    # latency from the victim's release covers the rest of the 2 ms of sleep
+    assert r["stress_co_ns"] > 1.5e6 and r["victim_co_ns"] > 0.9 * r["stress_co_ns"]
