@@ -129,7 +129,9 @@ typedef struct {
     int32_t sched_launches;  /* SCHED: launches enqueued (0 = 64) */
     int32_t sched_cycles;    /* SCHED: busy cycles per block (0 = 100) */
     int32_t mask_mode;       /* 0: sm_count SMs spread evenly over the SM ids (%smid filter);
-                                1: green-context partition (IFR_ERR_UNSUPPORTED);
+                                1: any SM of the green-context partition that owns the launch
+                                   stream (needs an active ifr_partition; sm_count = SMs to
+                                   claim, at most the larger partition's count);
                                 2: exactly the SMs set in sm_mask (%smid filter), e.g. two
                                    disjoint partitions as in Sec. 4.3's inter-SM runs;
                                    sm_count must equal the number of bits set */
@@ -251,6 +253,26 @@ typedef struct {
  * then the call still synchronises).  Errors: IFR_ERR_ARG (shape, null or
  * misaligned pointer), IFR_ERR_LAUNCH, IFR_ERR_CUDA. */
 int ifr_victim_launch(ifr_ctx *ctx, const ifr_victim_cfg *cfg, void *stream, ifr_timing *out);
+
+/* ---- SM partitions (green contexts; Sec. 4.1 inter-SM colocation) ------ */
+/* The paper colocates across SMs with CUDA green contexts, each a disjoint SM set
+ * with its own stream (Sec. 4.1, 4.3).  ifr_partition splits the device's SMs into
+ * two such partitions: one of at least `victim_sms` SMs (rounded up to the split
+ * granularity) and one of the rest.  While the split is active the context's
+ * victim stream belongs to the first and its stressor stream to the second, so
+ * every sweep, ifr_colocate and ifr_stressor_pair run places victims and stressors
+ * (or pair A on the stressor side, pair B on the victim side) on disjoint SMs;
+ * stressors then use mask_mode 1.  flags: 1 = split each SM on its own (finer
+ * granularity, no SM co-scheduling guarantees), 0 = the driver's default split.
+ * Errors: IFR_ERR_ARG (victim_sms out of range, a split already active),
+ * IFR_ERR_UNSUPPORTED (no green-context support), IFR_ERR_CUDA. */
+typedef struct {
+    int32_t victim_sms;    /* SMs of the victim partition */
+    int32_t stressor_sms;  /* SMs of the stressor partition */
+} ifr_partition_info;
+int ifr_partition(ifr_ctx *ctx, int victim_sms, int flags, ifr_partition_info *out);
+/* Undo ifr_partition (after synchronising the device); no-op without a split. */
+int ifr_partition_release(ifr_ctx *ctx);
 
 /* ---- two stressors against each other (Sec. 3 pitfalls, Sec. 4.3, Sec. 4.4.3) -- */
 /* The paper's kernel-against-kernel experiments colocate two fixed-work kernels

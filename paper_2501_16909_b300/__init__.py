@@ -204,6 +204,16 @@ class Context:
             d[k] = _struct_dict(getattr(r, k))
         return d
 
+    def partition(self, victim_sms: int, fine: bool = False) -> dict:
+        """ifr_partition: green-context split, victims on one SM set, stressors on the other."""
+        self._sync()
+        info = _abi.ifr_partition_info()
+        check(self._L.ifr_partition(self._h, victim_sms, 1 if fine else 0, C.byref(info)), "ifr_partition")
+        return _struct_dict(info)
+
+    def partition_release(self):
+        check(self._L.ifr_partition_release(self._h), "ifr_partition_release")
+
     # -- victims
     def victim_launch(self, cfg: ifr_victim_cfg, stream=None) -> dict:
         self._sync()

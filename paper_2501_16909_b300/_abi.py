@@ -140,6 +140,10 @@ class ifr_colocate_result(C.Structure):
     ]
 
 
+class ifr_partition_info(C.Structure):
+    _fields_ = [("victim_sms", C.c_int32), ("stressor_sms", C.c_int32)]
+
+
 class ifr_corun_result(C.Structure):
     _fields_ = [
         ("victim_solo", ifr_timing), ("corunner_solo", ifr_timing), ("victim_corun", ifr_timing),
@@ -163,7 +167,7 @@ class ifr_mlp(C.Structure):
 
 STRUCTS = [ifr_device_info, ifr_stressor_cfg, ifr_stressor_result, ifr_block_log, ifr_victim_cfg, ifr_timing,
            ifr_sweep_plan, ifr_cell_result, ifr_sensitivity_out, ifr_kernel_profile, ifr_mlp, ifr_corun_result,
-           ifr_pair_result, ifr_colocate_result]
+           ifr_pair_result, ifr_colocate_result, ifr_partition_info]
 
 _lib = None
 
@@ -200,6 +204,8 @@ def load():
         "ifr_corun": (i32, [vp, P(ifr_victim_cfg), P(ifr_victim_cfg), i32, P(ifr_corun_result)]),
         "ifr_stressor_pair": (i32, [vp, P(ifr_stressor_cfg), P(ifr_stressor_cfg), P(ifr_pair_result)]),
         "ifr_colocate": (i32, [vp, P(ifr_stressor_cfg), P(ifr_victim_cfg), P(ifr_colocate_result)]),
+        "ifr_partition": (i32, [vp, i32, i32, P(ifr_partition_info)]),
+        "ifr_partition_release": (i32, [vp]),
         "ifr_victim_profile": (i32, [vp, P(ifr_victim_cfg), P(ifr_kernel_profile)]),
         "ifr_stressor_profile": (i32, [vp, P(ifr_stressor_cfg), P(ifr_kernel_profile)]),
         "ifr_mlp_forward": (i32, [vp, P(ifr_mlp), vp]),

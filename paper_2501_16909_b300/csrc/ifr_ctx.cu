@@ -136,6 +136,7 @@ extern "C" void ifr_shutdown(ifr_ctx *ctx) {
         if (ctx->slots[i].in_use && ctx->slots[i].d_state && ctx->h_one)
             cudaMemcpyAsync(&ctx->slots[i].d_state->stop, ctx->h_one, 4, cudaMemcpyHostToDevice, ctx->s_ctrl);
     cudaDeviceSynchronize();
+    ifr_partition_release(ctx);
     for (int i = 0; i < IFR_SLOTS; ++i) slot_free(ctx->slots[i]);
     if (ctx->d_timing) cudaFree(ctx->d_timing);
     if (ctx->d_progress) cudaFree(ctx->d_progress);

@@ -130,6 +130,12 @@ struct ifr_ctx {
     cudaEvent_t ev_a, ev_b;
     uint64_t kernel_launches;  // kernels enqueued (graph replays add their kernel nodes)
     uint64_t *d_progress;      // victim progress word (device)
+    // green-context split (ifr_partition): the victim / stressor streams above are
+    // the partitions' streams while it is active; the originals are kept here
+    int part_active;
+    int part_sms_v, part_sms_s;
+    void *green_v, *green_s;   // CUgreenCtx
+    cudaStream_t own_victim, own_stress;
 };
 
 // Prefer the maximum shared-memory carveout for every kernel of the library so

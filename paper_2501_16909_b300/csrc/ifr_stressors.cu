@@ -751,8 +751,12 @@ static int validate_cfg(ifr_ctx *ctx, const ifr_stressor_cfg *c) {
     if (c->kind == IFR_S_SLEEP &&
         (c->working_set_bytes < 0 || c->working_set_bytes > ctx->info.smem_per_block_optin - 1024 || c->period_ns < 0))
         return IFR_ERR_ARG;
-    if (c->mask_mode == 1) return IFR_ERR_UNSUPPORTED;
-    if (c->mask_mode == 2) {
+    if (c->mask_mode == 1) {
+        // the green context owning the launch stream confines the blocks
+        if (!ctx->part_active) return IFR_ERR_UNSUPPORTED;
+        const int most = ctx->part_sms_v > ctx->part_sms_s ? ctx->part_sms_v : ctx->part_sms_s;
+        if (c->sm_count > most) return IFR_ERR_ARG;
+    } else if (c->mask_mode == 2) {
         // explicit SM set: only ids of this device, exactly sm_count of them
         int bits = 0;
         for (int s = 0; s < IFR_MAX_SMS; ++s) {
@@ -782,6 +786,8 @@ int ifr_stressor_enqueue(ifr_ctx *ctx, const ifr_stressor_cfg *cfg, cudaStream_t
     p.bps = cfg->blocks_per_sm ? cfg->blocks_per_sm : kind_default_bps(kind);
     if (cfg->mask_mode == 2)
         memcpy(p.mask, cfg->sm_mask, sizeof p.mask);
+    else if (cfg->mask_mode == 1)
+        ifr_compute_mask(num_sms, num_sms, p.mask);  // every SM id: the partition confines
     else
         ifr_compute_mask(num_sms, cfg->sm_count, p.mask);
     p.planned = cfg->sm_count * p.bps;

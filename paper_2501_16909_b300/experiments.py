@@ -24,6 +24,9 @@ the library's stressors and victims through the C ABI (no vLLM, cuBLAS or MPS):
             per-instance data: one kernel's slowdown against alone, and its solo rate.
   smem      Sec. 4.4.1, Fig. 4: BF16 GEMM victims (1024^3, 2048^3, 4096^3) beside the
             n-strided shared-memory stressor, n = 1, 2, 4, ..., 32: slowdown per n.
+  bandwidth Sec. 4.3, Table 1: victims in one green-context partition (half the SMs)
+            beside a copy kernel in the other, 512-thread blocks on half its SMs, then 1,
+            2 and 3 per SM: victim slowdown and the copy's HBM bandwidth.
   hol       Sec. 4.2, block-scheduler interference: a 10 ms sleep kernel (one 128-thread
             block per SM) released together with victims of small and large per-block
             footprints: victim latency from the release, alone and beside it, and
@@ -338,7 +341,40 @@ def exp_hol(ctx, repeats):
     }
 
 
-NAMES = ["pitfall1", "pitfall2", "ipc", "fp64", "l2", "smem", "hol"]
+def exp_bandwidth(ctx, repeats, hbm_buf):
+    S = ctx.info["num_sms"]
+    info = ctx.partition(S // 2, fine=True)
+    try:
+        nv, ns = info["victim_sms"], info["stressor_sms"]
+        victims, _keep = _decode_victims()
+        # 512-thread blocks: up to three fit per SM at the stream kernel's 40 registers
+        # (two 1024-thread blocks would need 81 920 registers and never co-reside)
+        levels = [(max(1, ns // 2), 1), (ns, 1), (ns, 2), (ns, 3)]
+        row = [stressor_cfg(A.IFR_S_HBM, sm_count=n, blocks_per_sm=b, block=512, buf=hbm_buf,
+                            working_set_bytes=hbm_buf.numel() * 4, seed=1, mask_mode=1) for n, b in levels]
+        peak = P.measured_peaks()[0]["hbm_gbs"]
+        bw = []
+        for c in row:
+            rate, _ = P.solo_rate(ctx, c, rounds=64)
+            bw.append(round(rate / 1e9, 1))
+        cells = ctx.sweep([v for _, v in victims], [row], repeats=repeats, batched=False)
+        sl = slowdowns_from_cells(cells, len(victims), len(row))
+        touched = max(c.timing.sms_touched for c in cells)
+    finally:
+        ctx.partition_release()
+    return {
+        "experiment": "bandwidth",
+        "paper": "Sec. 4.3 Table 1 (H100 green contexts, 64 + 68 SMs: copy L2 util 37/68/87/95 %, memory "
+                 "bandwidth util 27/51/69/81 % at 34/68/102/136 blocks; decode TBT up to 1.3x)",
+        "partition": {"victim_sms": nv, "stressor_sms": ns, "victim_sms_touched_max": touched},
+        "copy_blocks_of_512": [n * b for n, b in levels], "copy_gbs": bw,
+        "copy_frac_of_hbm_peak": [round(x / peak, 3) for x in bw],
+        "victims": [{"victim": name, **s} for (name, _), s in zip(victims, sl)],
+        "note": "slowdown[0] is the zero-SM stressor (harness only); slowdown[i] is copy level i",
+    }
+
+
+NAMES = ["pitfall1", "pitfall2", "ipc", "fp64", "l2", "smem", "hol", "bandwidth"]
 
 
 def main(argv=None):
@@ -372,6 +408,9 @@ def main(argv=None):
             r = exp_l2(ctx, a.repeats)
         elif name == "hol":
             r = exp_hol(ctx, a.repeats)
+        elif name == "bandwidth":
+            hbm = hbm if hbm is not None else I.torch_u32_as_i32(1, (4 * GiB) // 4, "cuda")
+            r = exp_bandwidth(ctx, a.repeats, hbm)
         else:
             r = exp_smem(ctx, a.repeats)
         r["seconds"] = round(time.perf_counter() - t0, 2)

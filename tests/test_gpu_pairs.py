@@ -167,3 +167,40 @@ def test_colocate_register_file_victim_waits_for_sleep(ctx):
     assert r["victim_co"]["t_start_ns"] >= r["stress_co"]["t_end_first_ns"]
     # latency from the victim's release covers the rest of the 2 ms of sleep
     assert r["stress_co_ns"] > 1.5e6 and r["victim_co_ns"] > 0.9 * r["stress_co_ns"]
+
+
+# ---------------------------------------------------------------- green-context partitions (Sec. 4.1)
+def test_partition_confines_victims_and_stressors(ctx):
+    import torch
+    import ifr_inputs as I
+    S = ctx.info["num_sms"]
+    info = ctx.partition(S // 2, fine=True)
+    try:
+        nv, ns = info["victim_sms"], info["stressor_sms"]
+        assert nv >= S // 2 and nv + ns <= S and ns > 0
+        # a stressor on every SM of its partition (mask_mode 1) stays there
+        cfg = ifr.stressor_cfg(A.IFR_S_FMA, sm_count=ns, blocks_per_sm=1, block=128, ilp=4, seed=5, max_rounds=4,
+                               mask_mode=1)
+        res, logs = ctx.run_stressor(cfg)
+        assert res["status"] == A.IFR_OK and res["sms_used"] == ns
+        stress_sms = {L["smid"] for L in logs}
+        # a victim with more blocks than SMs touches only the victim partition's SMs
+        n = 1 << 22
+        b = I.torch_uniform_pm1(0, n, "cuda")
+        c = I.torch_uniform_pm1(0, n, "cuda", start=n)
+        a = torch.empty(n, device="cuda")
+        v = ifr.victim_cfg(A.IFR_V_TRIAD, b, c, a, n=n, scalar=1.5, repeats=2)
+        t = ctx.victim_launch(v)
+        assert t["status"] == A.IFR_OK and 0 < t["sms_touched"] <= nv
+        # a sweep cell: victim beside the stressor on disjoint SMs, both valid
+        lv = [[ifr.stressor_cfg(A.IFR_S_FMA, sm_count=ns, blocks_per_sm=1, block=128, ilp=4, seed=5, mask_mode=1)]]
+        cells = ctx.sweep([v], lv, repeats=1, batched=False)
+        co = [x for x in cells if x.stressor == 0 and x.level == 1]
+        assert co and all(x.valid for x in co)
+        assert co[0].stress.sms_used == ns and co[0].timing.sms_touched <= nv
+        assert len(stress_sms) == ns
+    finally:
+        ctx.partition_release()
+    # released: a full-SM stressor reaches every SM again
+    res, _ = ctx.run_stressor(ifr.stressor_cfg(A.IFR_S_FMA, sm_count=S, blocks_per_sm=1, block=128, max_rounds=1))
+    assert res["sms_used"] == S
