@@ -37,7 +37,7 @@
 extern "C" {
 #endif
 
-#define IFR_ABI_VERSION 2
+#define IFR_ABI_VERSION 3
 
 /* ---- status codes ------------------------------------------------------- */
 #define IFR_OK 0
@@ -236,6 +236,12 @@ typedef struct {
     void *out;             /* TRIAD a | GEMM C | GEMV y | LN/SOFTMAX y | HIST bins */
     int32_t grid;          /* blocks (0 = kind default) */
     int32_t block;         /* threads per block (0 = kind default) */
+    int32_t variant;       /* GEMM: 0 = colocation-friendly (3 TMA stages, 147 KiB of shared
+                              memory: leaves room for a stressor block, Sec. 5.3),
+                              1 = throughput (4 stages, 195 KiB: more operand bytes in
+                              flight, but no shared-memory stressor block fits beside it).
+                              Other kinds: 0. */
+    int32_t reserved;
 } ifr_victim_cfg;
 
 typedef struct {

@@ -79,7 +79,7 @@ class ifr_victim_cfg(C.Structure):
     _fields_ = [
         ("kind", C.c_int32), ("repeats", C.c_int32), ("m", C.c_int64), ("n", C.c_int64), ("k", C.c_int64),
         ("scalar", C.c_float), ("eps", C.c_float), ("in0", C.c_void_p), ("in1", C.c_void_p), ("out", C.c_void_p),
-        ("grid", C.c_int32), ("block", C.c_int32),
+        ("grid", C.c_int32), ("block", C.c_int32), ("variant", C.c_int32), ("reserved", C.c_int32),
     ]
 
 

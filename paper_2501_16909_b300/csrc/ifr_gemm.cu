@@ -38,17 +38,19 @@
 
 namespace {
 
-// Three stages (147 KiB of shared memory at BN = 256) leave room on the SM for a
-// stressor block (the tensor stressor needs 34 KiB, the shared-memory stressor
-// 2 x 33 KiB): a colocation-friendly configuration in the sense of Sec. 5.3.
-// Four stages (195 KiB) would make the GEMM and those stressors mutually exclusive.
-// One BN-column accumulator (not two) likewise leaves TMEM for the tensor stressor.
-constexpr int BM = 128, BK = 64, STAGES = 3, EPI_WARPS = 4, GEMM_THREADS = 64 + 32 * EPI_WARPS;
+// Two variants (Sec. 5.3: colocation-friendly kernel variants).  Three stages (147 KiB
+// of shared memory at BN = 256) leave room on the SM for a stressor block (the tensor
+// stressor needs 34 KiB, the shared-memory stressor 2 x 33 KiB).  Four stages
+// (195 KiB) keep a third more operand bytes in flight, which the single-CTA tile needs
+// to cover the L2 round trip, but make the GEMM and those stressors mutually
+// exclusive on an SM.  One BN-column accumulator (not two) leaves TMEM for the tensor
+// stressor in both.
+constexpr int BM = 128, BK = 64, EPI_WARPS = 4, GEMM_THREADS = 64 + 32 * EPI_WARPS;
 constexpr int RING = 4;  // tile indices in flight between the scheduler and the consumers
 constexpr uint64_t kGemmTimeoutNs = 4000000000ull;
 int g_num_sms = 0;  // persistent grid size (set from the context before each launch)
 
-template <int BN>
+template <int BN, int STAGES>
 struct GemmCfg {
     static constexpr int A_BYTES = BM * BK * 2;
     static constexpr int B_BYTES = BN * BK * 2;
@@ -82,12 +84,12 @@ __device__ __forceinline__ void store_row16(float *dst, const uint32_t (&r)[16])
                            __uint_as_float(r[4 * e + 3]));
 }
 
-template <int BN>
+template <int BN, int STAGES>
 __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_kernel(const __grid_constant__ CUtensorMap ta,
                                                                     const __grid_constant__ CUtensorMap tb,
                                                                     float *__restrict__ C, int M, int N, int K,
                                                                     DevTiming *tm) {
-    using Cf = GemmCfg<BN>;
+    using Cf = GemmCfg<BN, STAGES>;
     constexpr int CHUNKS = BN / 16;
     extern __shared__ uint8_t g_smem_raw[];
     uint8_t *base = (uint8_t *)(((uintptr_t)g_smem_raw + 1023u) & ~(uintptr_t)1023u);
@@ -283,23 +285,30 @@ int make_map(CUtensorMap *m, const void *ptr, int64_t rows, int64_t K, int box_r
     return r == CUDA_SUCCESS ? IFR_OK : IFR_ERR_ARG;
 }
 
-template <int BN>
-int launch_gemm(const ifr_victim_cfg *c, cudaStream_t stream, DevTiming *tm) {
+template <int BN, int ST>
+const void *gemm_fn() {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(gemm_bf16_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, GemmCfg<BN>::SMEM);
+        cudaFuncSetAttribute(gemm_bf16_kernel<BN, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             GemmCfg<BN, ST>::SMEM);
         attr = true;
     }
+    return (const void *)gemm_bf16_kernel<BN, ST>;
+}
+
+template <int BN, int ST>
+int launch_gemm(const ifr_victim_cfg *c, cudaStream_t stream, DevTiming *tm) {
+    gemm_fn<BN, ST>();
     CUtensorMap ta, tb;
     int rc = make_map(&ta, c->in0, c->m, c->k, BM);
     if (rc) return rc;
     rc = make_map(&tb, c->in1, c->n, c->k, BN);
     if (rc) return rc;
-    ifr_carveout((const void *)gemm_bf16_kernel<BN>);
+    ifr_carveout((const void *)gemm_bf16_kernel<BN, ST>);
     const int tiles = (int)((c->n / BN) * (c->m / BM));
     const int grid = tiles < g_num_sms ? tiles : g_num_sms;
-    gemm_bf16_kernel<BN><<<grid, GEMM_THREADS, GemmCfg<BN>::SMEM, stream>>>(ta, tb, (float *)c->out, (int)c->m,
-                                                                           (int)c->n, (int)c->k, tm);
+    gemm_bf16_kernel<BN, ST><<<grid, GEMM_THREADS, GemmCfg<BN, ST>::SMEM, stream>>>(
+        ta, tb, (float *)c->out, (int)c->m, (int)c->n, (int)c->k, tm);
     return IFR_OK;
 }
 
@@ -307,12 +316,13 @@ int launch_gemm(const ifr_victim_cfg *c, cudaStream_t stream, DevTiming *tm) {
 
 int ifr_gemm_shape(const ifr_victim_cfg *c, VictimShape *s) {
     if (g_num_sms == 0) cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, 0);
-    const bool wide = c->n % 256 == 0;
-    s->fn = wide ? (const void *)gemm_bf16_kernel<256> : (const void *)gemm_bf16_kernel<128>;
+    const bool wide = c->n % 256 == 0, deep = c->variant == 1;
+    s->fn = wide ? (deep ? gemm_fn<256, 4>() : gemm_fn<256, 3>()) : (deep ? gemm_fn<128, 4>() : gemm_fn<128, 3>());
     const int tiles = (int)((c->n / (wide ? 256 : 128)) * (c->m / BM));
     s->grid = tiles < g_num_sms ? tiles : g_num_sms;
     s->block = GEMM_THREADS;
-    s->smem = wide ? GemmCfg<256>::SMEM : GemmCfg<128>::SMEM;
+    s->smem = wide ? (deep ? GemmCfg<256, 4>::SMEM : GemmCfg<256, 3>::SMEM)
+                   : (deep ? GemmCfg<128, 4>::SMEM : GemmCfg<128, 3>::SMEM);
     s->tmem_cols = wide ? 256 : 128;
     s->uses_tensor = 1;
     s->flops = 2.0 * (double)c->m * (double)c->n * (double)c->k;
@@ -323,11 +333,16 @@ int ifr_gemm_shape(const ifr_victim_cfg *c, VictimShape *s) {
 int ifr_gemm_enqueue(ifr_ctx *ctx, const ifr_victim_cfg *c, cudaStream_t stream, DevTiming *tm) {
     g_num_sms = ctx->info.num_sms;
     if (c->m > 65535 * BM || c->n > (1ll << 30) || c->k > (1ll << 30)) return IFR_ERR_ARG;
-    if (c->n % 256 == 0) return launch_gemm<256>(c, stream, tm);
-    return launch_gemm<128>(c, stream, tm);
+    const bool deep = c->variant == 1;
+    if (c->n % 256 == 0) return deep ? launch_gemm<256, 4>(c, stream, tm) : launch_gemm<256, 3>(c, stream, tm);
+    return deep ? launch_gemm<128, 4>(c, stream, tm) : launch_gemm<128, 3>(c, stream, tm);
 }
 
 int ifr_preload_gemm() {
-    int rc = ifr_preload((const void *)gemm_bf16_kernel<128>);
-    return rc ? rc : ifr_preload((const void *)gemm_bf16_kernel<256>);
+    const void *fns[] = {gemm_fn<128, 3>(), gemm_fn<256, 3>(), gemm_fn<128, 4>(), gemm_fn<256, 4>()};
+    for (const void *f : fns) {
+        int rc = ifr_preload(f);
+        if (rc) return rc;
+    }
+    return IFR_OK;
 }

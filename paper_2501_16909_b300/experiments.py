@@ -27,6 +27,9 @@ the library's stressors and victims through the C ABI (no vLLM, cuBLAS or MPS):
   bandwidth Sec. 4.3, Table 1: victims in one green-context partition (half the SMs)
             beside a copy kernel in the other, 512-thread blocks on half its SMs, then 1,
             2 and 3 per SM: victim slowdown and the copy's HBM bandwidth.
+  variants  Sec. 5.3, colocation-friendly kernel variants: the BF16 GEMM with 3 TMA
+            stages (147 KiB of shared memory) and with 4 (195 KiB), alone and arriving
+            at each full-SM stressor: solo throughput against latency beside it.
   hol       Sec. 4.2, block-scheduler interference: a 10 ms sleep kernel (one 128-thread
             block per SM) released together with victims of small and large per-block
             footprints: victim latency from the release, alone and beside it, and
@@ -374,7 +377,52 @@ def exp_bandwidth(ctx, repeats, hbm_buf):
     }
 
 
-NAMES = ["pitfall1", "pitfall2", "ipc", "fp64", "l2", "smem", "hol", "bandwidth"]
+def exp_variants(ctx, repeats, hbm_buf):
+    S = ctx.info["num_sms"]
+    G = 4096
+    gA = I.torch_normal_bf16(11, G * G, "cuda").view(G, G)
+    gB = I.torch_normal_bf16(12, G * G, "cuda").view(G, G)
+    gC = torch.empty(G, G, device="cuda")
+    victims = [victim_cfg(A.IFR_V_GEMM, gA, gB, gC, m=G, n=G, k=G, repeats=4, variant=v) for v in (0, 1)]
+    kinds = [A.IFR_S_SMEM_CF, A.IFR_S_SMEM_32W, A.IFR_S_TENSOR, A.IFR_S_FMA, A.IFR_S_HBM]
+    from . import workloads as W
+    stressors = []
+    for k in kinds:
+        cfg = W.stressor_level_cfg(k, S, {"hbm": hbm_buf}, seed=3)
+        t_cal = P.solo_rate(ctx, cfg)[1]["elapsed_ms"]
+        rounds = max(1, round(P.CAL_ROUNDS[k] * 8.0 / max(t_cal, 1e-3)))  # about 8 ms of fixed work
+        stressors.append((A.STRESSOR_NAMES[k], P.copy_cfg(cfg, max_rounds=rounds)))
+    rows = []
+    for v in victims:
+        prof = ctx.victim_profile(v)
+        solo = ctx.victim_launch(_with_repeats(v, 20))
+        tf = 2.0 * G ** 3 * 20 / (solo["event_ms"] * 1e-3) / 1e12
+        beside = {}
+        for name, sc in stressors:
+            runs = [ctx.colocate(sc, v) for _ in range(repeats)]
+            ratio = statistics.median(r["victim_co_ns"] / r["victim_solo_ns"] for r in runs)
+            beside[name] = {"latency_ratio": round(ratio, 3), "blocked": sum(r["blocked"] for r in runs),
+                            "runs": len(runs)}
+        rows.append({"variant": v.variant, "stages": 3 + v.variant, "smem_per_block": prof["dynamic_smem"],
+                     "regs_per_thread": prof["regs_per_thread"], "solo_tflops": round(tf, 1), "beside": beside})
+    return {
+        "experiment": "variants", "paper": "Sec. 5.3 (colocation-friendly kernel variants trade single-kernel "
+                                           "speed for the chance to share an SM)",
+        "victim": "BF16 GEMM %d^3, 4 launches per measurement" % G,
+        "stressors": "full SMs, configuration-2 shapes, about 8 ms of fixed work", "variants": rows,
+    }
+
+
+def _with_repeats(v, repeats):
+    """Copy of a victim configuration with another launch count."""
+    c = victim_cfg(v.kind)
+    for name, _ in v._fields_:
+        setattr(c, name, getattr(v, name))
+    c.repeats = repeats
+    return c
+
+
+NAMES = ["pitfall1", "pitfall2", "ipc", "fp64", "l2", "smem", "hol", "bandwidth", "variants"]
 
 
 def main(argv=None):
@@ -408,6 +456,9 @@ def main(argv=None):
             r = exp_l2(ctx, a.repeats)
         elif name == "hol":
             r = exp_hol(ctx, a.repeats)
+        elif name == "variants":
+            hbm = hbm if hbm is not None else I.torch_u32_as_i32(1, (4 * GiB) // 4, "cuda")
+            r = exp_variants(ctx, a.repeats, hbm)
         elif name == "bandwidth":
             hbm = hbm if hbm is not None else I.torch_u32_as_i32(1, (4 * GiB) // 4, "cuda")
             r = exp_bandwidth(ctx, a.repeats, hbm)

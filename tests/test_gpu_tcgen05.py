@@ -21,17 +21,21 @@ def ctx():
     c.close()
 
 
-def _gemm(ctx, M, N, K, seed=11, repeats=1):
+def _gemm(ctx, M, N, K, seed=11, repeats=1, variant=0):
     Ab = I.torch_normal_bf16(seed, M * K, "cuda").view(M, K)
     Bb = I.torch_normal_bf16(seed + 1, N * K, "cuda").view(N, K)
     C = torch.full((M, N), float("nan"), device="cuda")
-    t = ctx.victim_launch(ifr.victim_cfg(A.IFR_V_GEMM, Ab, Bb, C, m=M, n=N, k=K, repeats=repeats))
+    t = ctx.victim_launch(ifr.victim_cfg(A.IFR_V_GEMM, Ab, Bb, C, m=M, n=N, k=K, repeats=repeats, variant=variant))
     return Ab, Bb, C, t
 
 
-@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (128, 256, 128), (256, 384, 192), (384, 512, 1024)])
-def test_gemm_small_all_entries(ctx, M, N, K):
-    Ab, Bb, C, t = _gemm(ctx, M, N, K)
+# the last two shapes have more output tiles than SMs (160 tiles of 128 x 256, 192 of
+# 128 x 128), so most tiles are handed out by the device counter
+@pytest.mark.parametrize("variant", [0, 1])  # colocation-friendly (3 stages) / throughput (4)
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (128, 256, 128), (256, 384, 192), (384, 512, 1024),
+                                   (2048, 2560, 128), (8192, 384, 64)])
+def test_gemm_small_all_entries(ctx, M, N, K, variant):
+    Ab, Bb, C, t = _gemm(ctx, M, N, K, variant=variant)
     assert t["status"] == 0
     ref = Ab.double().cpu() @ Bb.double().cpu().T
     got = C.double().cpu()
@@ -57,6 +61,19 @@ def test_gemm_full_size_sampled_vs_oracle(ctx):
     assert np.all(np.abs(got - ref) <= BF16_TOL * np.maximum(np.abs(ref), rms))
     assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref)
     assert torch.isfinite(C).all()
+
+
+def test_gemm_variant_profiles_and_bad_variant(ctx):
+    Ab = I.torch_normal_bf16(1, 256 * 256, "cuda").view(256, 256)
+    C = torch.empty(256, 256, device="cuda")
+    p0 = ctx.victim_profile(ifr.victim_cfg(A.IFR_V_GEMM, Ab, Ab, C, m=256, n=256, k=256, variant=0))
+    p1 = ctx.victim_profile(ifr.victim_cfg(A.IFR_V_GEMM, Ab, Ab, C, m=256, n=256, k=256, variant=1))
+    assert p1["dynamic_smem"] - p0["dynamic_smem"] == 128 * 64 * 2 + 256 * 64 * 2  # one more 48 KiB stage
+    assert p0["regs_per_thread"] <= 96 and p1["regs_per_thread"] <= 96
+    for bad in (ifr.victim_cfg(A.IFR_V_GEMM, Ab, Ab, C, m=256, n=256, k=256, variant=2),
+                ifr.victim_cfg(A.IFR_V_SOFTMAX, C, None, C, m=256, n=256, variant=1)):
+        with pytest.raises(ifr.IfrError):
+            ctx.victim_launch(bad)
 
 
 def test_gemm_rejects_bad_shapes(ctx):
