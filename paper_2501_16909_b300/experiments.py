@@ -225,8 +225,25 @@ def exp_fp64(ctx, repeats, fp64_peak):
         rows.append({"ilp": ilp, "issue_rate": round(issue_rate(rate, S, clk), 4),
                      "fp64_pipe_util": round(rate / fp64_peak, 4), "dmul_per_s": rate,
                      "speedup_seq_over_col": round(pr["speedup_seq_over_col"], 3), "pair": pr})
+    # ncu names one "shared pipe (fp64 + tensor)" on this part: does the fp64 kernel
+    # also slow tensor-core work?  The GEMM arriving at a running fp64 kernel (~8 ms).
+    G = 4096
+    gA = I.torch_normal_bf16(11, G * G, "cuda").view(G, G)
+    gB = I.torch_normal_bf16(12, G * G, "cuda").view(G, G)
+    gC = torch.empty(G, G, device="cuda")
+    gemm = victim_cfg(A.IFR_V_GEMM, gA, gB, gC, m=G, n=G, k=G, repeats=4)
+    beside = {}
+    for ilp in (1, 4):
+        sc = stressor_cfg(A.IFR_S_FP64, sm_count=S, blocks_per_sm=1, block=128, ilp=ilp, seed=5)
+        t8 = P.solo_rate(ctx, sc, rounds=8)[1]["elapsed_ms"]
+        sc.max_rounds = max(1, round(8 * 8.0 / max(t8, 1e-3)))
+        runs = [ctx.colocate(sc, gemm) for _ in range(repeats)]
+        beside["ilp%d" % ilp] = {"latency_ratio": round(statistics.median(r["victim_co_ns"] / r["victim_solo_ns"]
+                                                                         for r in runs), 3),
+                                 "blocked": sum(r["blocked"] for r in runs)}
     return {
         "experiment": "fp64", "paper": "Sec. 4.4.3 Table 3 (H100: util 24/48/69/91 %, speedup 1.93/1.87/1.33/1.03)",
+        "gemm_4096_beside_fp64": beside,
         "kernel": "fp64 multiply chains (__dmul_rn), one 128-thread block per SM, 8 rounds of 1024 multiplies",
         "fp64_peak_dmul_per_s": fp64_peak,
         "fp64_peak_per_sm_per_clock": round(fp64_peak / (S * clk), 3),

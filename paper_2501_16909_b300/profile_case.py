@@ -6,8 +6,8 @@ one kernel kind in isolation on a small case so that a profiler can capture it:
 
     python -m paper_2501_16909_b300.profile_case <case> [--repeat N]
 
-cases: hbm, l2, fma, tensor, smem_cf, smem_32w, sched, gemm, gemv, layernorm,
-softmax, hist, triad.  Inputs are the workloads' seeded inputs at the sizes
+cases: hbm, l2, fma, tensor, smem_cf, smem_32w, sched, fp64, sleep, gemm, gemv,
+layernorm, softmax, hist, triad.  Inputs are the workloads' seeded inputs at the sizes
 given below (the stream stressors use a 1 GiB / 48 MiB set; the victims use their
 full configuration-2 shapes).
 """
@@ -42,7 +42,8 @@ def main(argv=None):
     n_sm = max(1, round(a.sm_fraction * S))
     out = {"case": a.case, "sm_count": n_sm}
     stressors = {"hbm": A.IFR_S_HBM, "l2": A.IFR_S_L2, "fma": A.IFR_S_FMA, "tensor": A.IFR_S_TENSOR,
-                 "smem_cf": A.IFR_S_SMEM_CF, "smem_32w": A.IFR_S_SMEM_32W, "sched": A.IFR_S_SCHED}
+                 "smem_cf": A.IFR_S_SMEM_CF, "smem_32w": A.IFR_S_SMEM_32W, "sched": A.IFR_S_SCHED,
+                 "fp64": A.IFR_S_FP64, "sleep": A.IFR_S_SLEEP}
     if a.case in stressors:
         kind = stressors[a.case]
         bufs = {}
