@@ -24,10 +24,6 @@ __all__ = ["Context", "stressor_cfg", "victim_cfg", "ifr_sensitivity", "cells_to
            "STRESSOR_NAMES", "VICTIM_NAMES"]
 
 
-def _ptr(t):
-    return None if t is None else C.c_void_p(int(t.data_ptr()))
-
-
 def _stream_handle(stream):
     if stream is None:
         return None

@@ -24,7 +24,6 @@ from . import stressor_cfg
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 TILE_MMA_FLOP = 2 * 128 * 128 * 64
-FMA_STEPS = 4096
 UNIT = {A.IFR_S_HBM: "B", A.IFR_S_L2: "B", A.IFR_S_FMA: "flop", A.IFR_S_TENSOR: "flop", A.IFR_S_SMEM_CF: "wavefront",
         A.IFR_S_SMEM_32W: "wavefront", A.IFR_S_SCHED: "block", A.IFR_S_FP64: "flop", A.IFR_S_SLEEP: "round"}
 # fixed-work rounds of one calibration run per kind (about a millisecond at full SMs)

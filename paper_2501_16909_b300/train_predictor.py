@@ -122,10 +122,6 @@ def collect(ctx, repeats=2, log=print):
             "victim_kinds": np.array([A.VICTIM_NAMES[k] for k in vkinds])}
 
 
-def base_kind_of(kind, smem_ways=None):
-    return kind
-
-
 def sensitivity_curves(d, mask):
     """(victim, base kind) -> (x sorted, slowdown - 1) from the base rows in mask."""
     curves = {}

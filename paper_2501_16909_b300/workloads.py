@@ -50,10 +50,6 @@ class Workload:
         return self.repeats * len(self.victims) * (1 + ns * (nl + 1))
 
 
-def stream_chunk_bytes(block: int) -> int:
-    return block * 64
-
-
 def config1(num_sms: int, device="cuda", hbm_bytes: int = GiB, n: int = 1 << 22, repeats: int = 3,
             launches_per_measurement: int = 8) -> Workload:
     b = I.torch_uniform_pm1(0, n, device)
@@ -210,14 +206,3 @@ def config3_base_stressors(num_sms: int, bufs, kinds=None):
     kinds = kinds or [A.IFR_S_SCHED, A.IFR_S_FMA, A.IFR_S_TENSOR, A.IFR_S_SMEM_CF, A.IFR_S_SMEM_32W, A.IFR_S_L2,
                       A.IFR_S_HBM]
     return [stressor_level_cfg(k, num_sms, bufs, seed=r + 1) for r, k in enumerate(kinds)]
-
-
-def size_sched_launches(wl: Workload, solo_window_ns: float, t_launch_ns: float, margin: float = 4.0,
-                        cap: int = 4096):
-    """Enough scheduler-stressor launches to cover `margin` x the victim window."""
-    n = int(min(cap, max(4, margin * solo_window_ns / max(t_launch_ns, 1.0) + 2)))
-    for r, row in enumerate(wl.levels):
-        for cfg in row:
-            if cfg.kind == A.IFR_S_SCHED:
-                cfg.sched_launches = n
-    return n
