@@ -358,7 +358,9 @@ def cpu_baseline(budget_s=20.0):
     """Time the oracle (as it stands, single thread) recomputing one sweep cell of the
     config-2 workload on the host: per victim a sample of its outputs (scaled to the
     full output), per stressor the checksums of 1 ms of its full-intensity work on B300
-    (scaled from a sample of blocks), and the reduction.  Returns cells/s."""
+    (scaled from a sample of blocks), and the reduction.  Each of the 11 parts repeats
+    its sample for an equal share of `budget_s` seconds and is timed per repetition.
+    Returns cells/s."""
     import numpy as np
 
     import ifr_inputs as I
@@ -369,10 +371,20 @@ def cpu_baseline(budget_s=20.0):
     rng = np.random.default_rng(0)
     per = {}
 
+    share = budget_s / 11.0
+    reps = {}
+
     def timed(fn, scale):
         t0 = time.perf_counter()
-        fn()
-        return (time.perf_counter() - t0) * scale
+        n = 0
+        while True:
+            fn()
+            n += 1
+            el = time.perf_counter() - t0
+            if el >= share:
+                break
+        reps[len(reps)] = n
+        return el / n * scale
 
     G, RR = 4096, 8192
     gA = oracle.f32_bits_to_bf16_bits(I.np_normal_bf16(11, np.arange(64 * G))).reshape(64, G)
@@ -404,7 +416,8 @@ def cpu_baseline(budget_s=20.0):
     return {"value": round(1.0 / sec_per_cell, 5), "unit": "cells/s", "cores": 1, "kind": "oracle",
             "sample": "one config-2 cell estimated from samples (GEMM 256 of 16.8M entries, GEMV 64 rows, LN 64 rows, "
                       "softmax 16 rows, histogram 2^22 of 2^26 keys, 1 ms of each stressor's B300 work scaled from "
-                      "one block); seconds per full cell %.1f; sampling took %.1f s" % (sec_per_cell, el),
+                      "one block), each sample repeated for %.1f s (%d-%d repetitions); seconds per full cell %.1f; "
+                      "sampling took %.1f s" % (share, min(reps.values()), max(reps.values()), sec_per_cell, el),
             "seconds_per_component": {k: round(v, 3) for k, v in per.items()}}
 
 
@@ -414,8 +427,10 @@ def run_reference(args):
         return
     vals = []
     t0 = time.perf_counter()
+    # the whole --steps/--warmup run stays within about two and a half minutes
+    budget = min(args.cpu_budget, 150.0 / max(1, args.warmup + args.steps))
     for _ in range(args.warmup + args.steps):
-        vals.append(cpu_baseline(budget_s=args.cpu_budget))
+        vals.append(cpu_baseline(budget_s=budget))
     el = time.perf_counter() - t0
     timed = vals[args.warmup:]
     v = statistics.mean(x["value"] for x in timed)
