@@ -204,3 +204,24 @@ def test_partition_confines_victims_and_stressors(ctx):
     # released: a full-SM stressor reaches every SM again
     res, _ = ctx.run_stressor(ifr.stressor_cfg(A.IFR_S_FMA, sm_count=S, blocks_per_sm=1, block=128, max_rounds=1))
     assert res["sms_used"] == S
+
+
+def test_partition_argument_errors(ctx):
+    S = ctx.info["num_sms"]
+    ctx.partition_release()  # no split active: a no-op
+    for bad in (0, S, -1):
+        with pytest.raises(ifr.IfrError) as e:
+            ctx.partition(bad)
+        assert e.value.status == A.IFR_ERR_ARG
+    info = ctx.partition(S // 4)
+    try:
+        with pytest.raises(ifr.IfrError) as e:  # one split at a time
+            ctx.partition(S // 2)
+        assert e.value.status == A.IFR_ERR_ARG
+        too_many = ifr.stressor_cfg(A.IFR_S_FMA, sm_count=S, block=128, max_rounds=1, mask_mode=1)
+        with pytest.raises(ifr.IfrError) as e:  # more SMs than either partition has
+            ctx.stressor_launch(too_many)
+        assert e.value.status == A.IFR_ERR_ARG
+        assert info["victim_sms"] >= S // 4 and info["victim_sms"] + info["stressor_sms"] <= S
+    finally:
+        ctx.partition_release()
