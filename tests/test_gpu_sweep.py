@@ -92,3 +92,44 @@ def test_corun_two_kernels_valid_and_consistent(setup):
     assert r["victim_slowdown"] > 1.1
     assert r["blocked"] == 0 and r["corunner_corun"]["t_start_ns"] <= r["victim_release_ns"] <= vc["t_start_ns"]
 
+
+
+# ---------------------------------------------------------------- failure paths (bounded, no fault)
+def test_unreachable_residency_is_reported_not_waited_for(setup):
+    # two 1024-thread stream blocks per SM need 2 x 1024 x 40 registers: the second
+    # cannot become resident beside the first.  Whichever bounded wait ends first
+    # reports it: the stressor's head-of-line watch (50 ms without victim progress)
+    # or the victim's residency wait (200 ms); the sweep goes on.
+    import time
+    ctx, victims, _levels, (b, c, a, buf) = setup
+    S = ctx.info["num_sms"]
+    lv = [[ifr.stressor_cfg(A.IFR_S_HBM, sm_count=S, blocks_per_sm=2, block=1024, working_set_bytes=256 << 20,
+                            buf=buf, seed=1)]]
+    t0 = time.perf_counter()
+    cells = ctx.sweep(victims, lv, repeats=1, batched=False)
+    assert time.perf_counter() - t0 < 1.5
+    co = [x for x in cells if x.stressor == 0 and x.level == 1]
+    assert co and not co[0].valid
+    assert co[0].status in (A.IFR_ERR_NOT_RESIDENT, A.IFR_ERR_HOL)
+    solo = [x for x in cells if x.stressor < 0]
+    assert solo[0].valid  # the rest of the sweep is unaffected
+
+
+def test_head_of_line_blocked_cell_is_recorded(setup):
+    # a victim block that needs the whole register file cannot join a stressor block:
+    # the stressor sees no victim progress, gives up with IFR_ERR_HOL, the victim runs
+    # after it and the cell is recorded as invalid instead of stalling to the deadline
+    import time
+    ctx, _victims, _levels, (_b, _c, _a, buf) = setup
+    S = ctx.info["num_sms"]
+    x = I.torch_uniform_pm1(44, 256 * 16384, "cuda").view(256, 16384)
+    y = torch.empty_like(x)
+    v = ifr.victim_cfg(A.IFR_V_SOFTMAX, x, None, y, m=256, n=16384, repeats=1)
+    assert ctx.victim_profile(v)["block"] == 1024
+    lv = [[ifr.stressor_cfg(A.IFR_S_FMA, sm_count=S, blocks_per_sm=1, block=128, ilp=4, seed=2)]]
+    t0 = time.perf_counter()
+    cells = ctx.sweep([v], lv, repeats=1, batched=False)
+    assert time.perf_counter() - t0 < 1.5  # 50 ms head-of-line window, far below the 2 s deadline
+    co = [c for c in cells if c.stressor == 0 and c.level == 1]
+    assert co and not co[0].valid
+    assert co[0].stress.status == A.IFR_ERR_HOL and co[0].status == A.IFR_ERR_HOL
