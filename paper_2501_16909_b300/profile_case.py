@@ -7,7 +7,9 @@ one kernel kind in isolation on a small case so that a profiler can capture it:
     python -m paper_2501_16909_b300.profile_case <case> [--repeat N]
 
 cases: hbm, l2, fma, tensor, smem_cf, smem_32w, sched, fp64, sleep, gemm, gemv,
-layernorm, softmax, hist, triad.  Inputs are the workloads' seeded inputs at the sizes
+layernorm, softmax, hist, triad; and victim_bandwidth, which times every memory-bound
+configuration-2 victim alone over grids of 0 (default), 1, 2, 4, 8 and 16 blocks per
+SM (20 launches after a warm measurement) and prints one JSON line per run.  Inputs are the workloads' seeded inputs at the sizes
 given below (the stream stressors use a 1 GiB / 48 MiB set; the victims use their
 full configuration-2 shapes).
 """
@@ -44,6 +46,23 @@ def main(argv=None):
     stressors = {"hbm": A.IFR_S_HBM, "l2": A.IFR_S_L2, "fma": A.IFR_S_FMA, "tensor": A.IFR_S_TENSOR,
                  "smem_cf": A.IFR_S_SMEM_CF, "smem_32w": A.IFR_S_SMEM_32W, "sched": A.IFR_S_SCHED,
                  "fp64": A.IFR_S_FP64, "sleep": A.IFR_S_SLEEP}
+    if a.case == "victim_bandwidth":
+        victims, kinds, _t = W.config2_victims("cuda")
+        names = {A.IFR_V_GEMV: "gemv", A.IFR_V_LAYERNORM: "layernorm", A.IFR_V_SOFTMAX: "softmax",
+                 A.IFR_V_HIST: "hist"}
+        for v, k in zip(victims, kinds):
+            if k not in names:
+                continue
+            prof = ctx.victim_profile(v)
+            for g in (0, S, 2 * S, 4 * S, 8 * S, 16 * S):
+                v.grid, v.repeats = g, 20
+                ctx.victim_launch(v)
+                t = ctx.victim_launch(v)
+                us = t["event_ms"] * 1e3 / 20
+                print(json.dumps({"victim": names[k], "grid": g or prof["grid"], "us_per_launch": round(us, 2),
+                                  "gbs": round(prof["bytes_per_launch"] / (us * 1e-6) / 1e9, 1)}))
+        ctx.close()
+        return
     if a.case in stressors:
         kind = stressors[a.case]
         bufs = {}
