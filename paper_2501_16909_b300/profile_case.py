@@ -9,7 +9,9 @@ one kernel kind in isolation on a small case so that a profiler can capture it:
 cases: hbm, l2, fma, tensor, smem_cf, smem_32w, sched, fp64, sleep, gemm, gemv,
 layernorm, softmax, hist, triad; and victim_bandwidth, which times every memory-bound
 configuration-2 victim alone over grids of 0 (default), 1, 2, 4, 8 and 16 blocks per
-SM (20 launches after a warm measurement) and prints one JSON line per run.  Inputs are the workloads' seeded inputs at the sizes
+SM (20 launches after a warm measurement) and prints one JSON line per run; and
+l2_set_sweep, which times the stream kernel on every SM (256 rounds per block) over
+sets of 8..96 MiB for 2 x 512, 4 x 512 and 2 x 256 threads per SM.  Inputs are the workloads' seeded inputs at the sizes
 given below (the stream stressors use a 1 GiB / 48 MiB set; the victims use their
 full configuration-2 shapes).
 """
@@ -46,6 +48,16 @@ def main(argv=None):
     stressors = {"hbm": A.IFR_S_HBM, "l2": A.IFR_S_L2, "fma": A.IFR_S_FMA, "tensor": A.IFR_S_TENSOR,
                  "smem_cf": A.IFR_S_SMEM_CF, "smem_32w": A.IFR_S_SMEM_32W, "sched": A.IFR_S_SCHED,
                  "fp64": A.IFR_S_FP64, "sleep": A.IFR_S_SLEEP}
+    if a.case == "l2_set_sweep":
+        buf = I.torch_u32_as_i32(3, (96 << 20) // 4, "cuda")
+        for mib in (8, 16, 24, 32, 40, 48, 64, 96):
+            for block, bps in ((512, 2), (512, 4), (256, 2)):
+                cfg = ifr.stressor_cfg(A.IFR_S_L2, sm_count=S, blocks_per_sm=bps, block=block, buf=buf,
+                                       working_set_bytes=mib << 20)
+                rate, _res = P.solo_rate(ctx, cfg, rounds=256)
+                print(json.dumps({"mib": mib, "block": block, "blocks_per_sm": bps, "gbs": round(rate / 1e9, 1)}))
+        ctx.close()
+        return
     if a.case == "victim_bandwidth":
         victims, kinds, _t = W.config2_victims("cuda")
         names = {A.IFR_V_GEMV: "gemv", A.IFR_V_LAYERNORM: "layernorm", A.IFR_V_SOFTMAX: "softmax",
