@@ -377,15 +377,18 @@ extern "C" int ifr_colocate(ifr_ctx *ctx, const ifr_stressor_cfg *sc, const ifr_
         }
         if (run_v && run_s) {
             // the victim arrives at a running stressor: every stressor block resident
-            // first (bounded wait, 200 ms), then the release stamp
+            // first (bounded wait, 200 ms), then the release stamp.  A failure from here
+            // on still waits for the enqueued stressor and frees its slot below.
             rc = ifr_enqueue_wait_resident(ctx, slot, ctx->s_victim, tv, 200000000ull);
-            if (rc) return rc;
-            ifr_carveout((const void *)stamp_kernel);
-            stamp_kernel<<<1, 32, 0, ctx->s_victim>>>(vrel);
-            IFR_CUDA(cudaGetLastError());
-            ctx->kernel_launches += 1;
+            if (!rc) {
+                ifr_carveout((const void *)stamp_kernel);
+                stamp_kernel<<<1, 32, 0, ctx->s_victim>>>(vrel);
+                const cudaError_t e = cudaGetLastError();
+                rc = e == cudaSuccess ? IFR_OK : ifr_cuda_fail(e, "stamp_kernel", __FILE__, __LINE__);
+                ctx->kernel_launches += 1;
+            }
         }
-        if (run_v) {
+        if (run_v && !rc) {
             rc = ifr_victim_enqueue(ctx, vc, ctx->s_victim, tv);
             if (!rc) rc = cudaEventRecord(ctx->ev_b, ctx->s_victim) == cudaSuccess ? IFR_OK : IFR_ERR_CUDA;
         }
@@ -526,7 +529,11 @@ extern "C" int ifr_sweep(ifr_ctx *ctx, const ifr_sweep_plan *p, ifr_cell_result 
                 rc = ifr_cuda_fail(e, "cudaGraphLaunch", __FILE__, __LINE__);
                 break;
             }
-            IFR_CUDA(cudaEventRecord(ctx->ev_b, ctx->s_victim));
+            e = cudaEventRecord(ctx->ev_b, ctx->s_victim);
+            if (e != cudaSuccess) {
+                rc = ifr_cuda_fail(e, "cudaEventRecord", __FILE__, __LINE__);
+                break;
+            }
             rc = wait_event_bounded(ctx->ev_b, 120000);
             if (rc) break;
             e = cudaMemcpy(ht.data(), ctx->d_timing, sizeof(DevTiming) * (size_t)p->n_victims, cudaMemcpyDeviceToHost);
