@@ -289,7 +289,9 @@ int ifr_partition_release(ifr_ctx *ctx);
  * sequential/colocated tracks the summed pipe utilisation (Table 3).
  * ifr_stressor_pair runs A alone, B alone, then A and B released at the same
  * instant on two streams (both streams wait on one event recorded after a short
- * device-side gate, so neither starts first by a host launch latency).  Both
+ * device-side gate, so neither starts first by a host launch latency).  A runs on
+ * the context's stressor stream and B on its victim stream, alone and together, so
+ * under ifr_partition each stays in its own partition.  Both
  * configurations must be fixed-work (max_rounds > 0) persistent kinds (not
  * IFR_S_SCHED); their SM sets (mask_mode 0 or 2) may overlap or be disjoint.
  * Spans are %globaltimer first-block start to last-block end. */

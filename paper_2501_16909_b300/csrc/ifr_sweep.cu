@@ -293,8 +293,9 @@ extern "C" int ifr_stressor_pair(ifr_ctx *ctx, const ifr_stressor_cfg *a, const 
         return IFR_ERR_ARG;
     memset(out, 0, sizeof *out);
     IFR_CUDA(cudaDeviceSynchronize());
+    // each alone on the stream it co-runs on (under ifr_partition: its own partition)
     int rc = run_fixed(ctx, a, ctx->s_stress, &out->solo_a);
-    if (!rc) rc = run_fixed(ctx, b, ctx->s_stress, &out->solo_b);
+    if (!rc) rc = run_fixed(ctx, b, ctx->s_victim, &out->solo_b);
     if (rc) return rc;
     // co-run: both streams wait behind a 300 us gate, then run their reset and kernel
     const int sa = ifr_slot_alloc(ctx);

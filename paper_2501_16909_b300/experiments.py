@@ -22,6 +22,8 @@ the library's stressors and victims through the C ABI (no vLLM, cuBLAS or MPS):
             the speedup of running them together over running them back to back.
   l2        Sec. 4.3, Fig. 3: two copy kernels on disjoint SM halves over growing
             per-instance data: one kernel's slowdown against alone, and its solo rate.
+  l2_green  the same with the halves as two green-context partitions (the paper's
+            mechanism) instead of explicit SM masks.
   smem      Sec. 4.4.1, Fig. 4: BF16 GEMM victims (1024^3, 2048^3, 4096^3) beside the
             n-strided shared-memory stressor, n = 1, 2, 4, ..., 32: slowdown per n.
   bandwidth Sec. 4.3, Table 1: victims in one green-context partition (half the SMs)
@@ -251,10 +253,21 @@ def exp_fp64(ctx, repeats, fp64_peak):
     }
 
 
-def exp_l2(ctx, repeats):
+def exp_l2(ctx, repeats, green=False):
     S = ctx.info["num_sms"]
     half = S // 2
     ids_a, ids_b = list(range(half)), list(range(half, S))
+    if green:
+        part = ctx.partition(half, fine=True)
+        n_a, n_b = part["stressor_sms"], part["victim_sms"]  # A runs on the stressor side
+    try:
+        return _l2_sizes(ctx, repeats, S, half, ids_a, ids_b, (n_a, n_b) if green else None)
+    finally:
+        if green:
+            ctx.partition_release()
+
+
+def _l2_sizes(ctx, repeats, S, half, ids_a, ids_b, green):
     sizes_mib = [1, 2, 4, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256]
     top = sizes_mib[-1] * MiB
     buf_a = I.torch_u32_as_i32(21, top // 4, "cuda")
@@ -264,10 +277,16 @@ def exp_l2(ctx, repeats):
         nb = mib * MiB
         per_round = half * 4 * 16 * 1024  # 4 chunks of 16 B x 1024 threads per block per round
         rounds = max(256, math.ceil(8 * nb / per_round))
-        a = with_mask(stressor_cfg(A.IFR_S_L2, blocks_per_sm=1, block=1024, buf=buf_a, working_set_bytes=nb,
-                                   seed=1, max_rounds=rounds), ids_a)
-        b = with_mask(stressor_cfg(A.IFR_S_L2, blocks_per_sm=1, block=1024, buf=buf_b, working_set_bytes=nb,
-                                   seed=2, max_rounds=rounds), ids_b)
+        if green:
+            a = stressor_cfg(A.IFR_S_L2, sm_count=green[0], blocks_per_sm=1, block=1024, buf=buf_a,
+                             working_set_bytes=nb, seed=1, max_rounds=rounds, mask_mode=1)
+            b = stressor_cfg(A.IFR_S_L2, sm_count=green[1], blocks_per_sm=1, block=1024, buf=buf_b,
+                             working_set_bytes=nb, seed=2, max_rounds=rounds, mask_mode=1)
+        else:
+            a = with_mask(stressor_cfg(A.IFR_S_L2, blocks_per_sm=1, block=1024, buf=buf_a, working_set_bytes=nb,
+                                       seed=1, max_rounds=rounds), ids_a)
+            b = with_mask(stressor_cfg(A.IFR_S_L2, blocks_per_sm=1, block=1024, buf=buf_b, working_set_bytes=nb,
+                                       seed=2, max_rounds=rounds), ids_b)
         pr = run_pair(ctx, a, b, repeats)
         bytes_a = half * rounds * 4 * 16 * 1024
         out.append({"mib_per_instance": mib, "rounds": rounds, "slowdown_a": round(pr["slowdown_a"], 3),
@@ -276,10 +295,12 @@ def exp_l2(ctx, repeats):
                     "co_a_gbs": round(bytes_a / (pr["co_a_us"] * 1e3), 1), "ok": pr["all_ok"],
                     "overlapped": pr["all_overlapped"]})
     return {
-        "experiment": "l2", "paper": "Sec. 4.3 Fig. 3 (H100, 50 MB L2: no slowdown <= 8 MB, peak 2.15x at 16 MB, "
+        "experiment": "l2_green" if green else "l2", "paper": "Sec. 4.3 Fig. 3 (H100, 50 MB L2: no slowdown <= 8 MB, peak 2.15x at 16 MB, "
                                      "~1.12x beyond 26 MB)",
-        "kernels": "stream read (XOR fold) of its own set, one 1024-thread block per SM; instance A on SM ids "
-                   "0..%d, B on %d..%d (disjoint, mask_mode 2)" % (half - 1, half, S - 1),
+        "kernels": ("stream read (XOR fold) of its own set, one 1024-thread block per SM; " +
+                    ("instances A and B in two green-context partitions of %d and %d SMs (mask_mode 1)" % green
+                     if green else "instance A on SM ids 0..%d, B on %d..%d (disjoint, mask_mode 2)"
+                     % (half - 1, half, S - 1))),
         "l2_bytes": ctx.info["l2_bytes"], "sizes": out,
     }
 
@@ -439,7 +460,7 @@ def _with_repeats(v, repeats):
     return c
 
 
-NAMES = ["pitfall1", "pitfall2", "ipc", "fp64", "l2", "smem", "hol", "bandwidth", "variants"]
+NAMES = ["pitfall1", "pitfall2", "ipc", "fp64", "l2", "l2_green", "smem", "hol", "bandwidth", "variants"]
 
 
 def main(argv=None):
@@ -471,6 +492,8 @@ def main(argv=None):
             r = exp_fp64(ctx, a.repeats, pk[A.IFR_S_FP64][0])
         elif name == "l2":
             r = exp_l2(ctx, a.repeats)
+        elif name == "l2_green":
+            r = exp_l2(ctx, a.repeats, green=True)
         elif name == "hol":
             r = exp_hol(ctx, a.repeats)
         elif name == "variants":
