@@ -43,10 +43,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
-def decoder_kernels(num_sms, device="cuda"):
-    """{name: ifr_victim_cfg} for the prefill and decode kernel lists, plus the tensors.
-    Memory-bound kernels use 4 blocks of 256 threads per SM (half the SM's threads)
-    so that a partner kernel can be resident beside them."""
+def decoder_kernels(num_sms, device="cuda", phases=("prefill", "decode")):
+    """{name: ifr_victim_cfg} for the prefill and / or decode kernel lists, plus the
+    tensors.  Memory-bound kernels use 4 blocks of 256 threads per SM (half the SM's
+    threads) so that a partner kernel can be resident beside them."""
     import torch
 
     import ifr_inputs as I
@@ -86,7 +86,16 @@ def decoder_kernels(num_sms, device="cuda"):
         return victim_cfg(A.IFR_V_TRIAD, b, c, a, n=n, scalar=1.0, grid=4 * num_sms)
 
     T, H, F = 16384, 4096, 11008
-    k = {
+    k = {}
+    if "prefill" in phases:
+        k.update(_prefill(gemm, rows, triad, T, H, F, A))
+    if "decode" in phases:
+        k.update(_decode(gemm, gemv, rows, triad, H, F, A))
+    return k, t
+
+
+def _prefill(gemm, rows, triad, T, H, F, A):
+    return {
         "prefill.layernorm": rows(A.IFR_V_LAYERNORM, T, H),
         "prefill.qkv": gemm(T, 3 * H, H),
         "prefill.qk_head": gemm(2048, 2048, 128),
@@ -96,6 +105,11 @@ def decoder_kernels(num_sms, device="cuda"):
         "prefill.gate_up": gemm(T, F, H),
         "prefill.silu_mul": triad(T * F),
         "prefill.down": gemm(T, H, F),
+    }
+
+
+def _decode(gemm, gemv, rows, triad, H, F, A):
+    return {
         "decode.layernorm": rows(A.IFR_V_LAYERNORM, 64, H),
         "decode.qkv": gemm(128, 3 * H, H),
         "decode.qk": gemv(64 * 32 * 4096, 128),
@@ -106,7 +120,6 @@ def decoder_kernels(num_sms, device="cuda"):
         "decode.silu_mul": triad(64 * F),
         "decode.down": gemm(128, H, F),
     }
-    return k, t
 
 
 def set_launches(ctx, cfg, target_ns=100000.0, cap=256):

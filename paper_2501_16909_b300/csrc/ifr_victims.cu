@@ -283,6 +283,76 @@ __global__ void __launch_bounds__(256) gemv_kernel(const __nv_bfloat16 *__restri
     v_exit(tm);
 }
 
+// Short rows (cols <= 256): L = the power of two >= cols/8 lanes share one row (one
+// 16-byte load each), so a warp reduces 32/L rows at once and no lane idles; x is
+// read straight from global memory (each lane keeps its fixed 8-element slice).
+template <int L>
+__global__ void __launch_bounds__(256) gemv_short_kernel(const __nv_bfloat16 *__restrict__ A,
+                                                        const __nv_bfloat16 *__restrict__ x, float *__restrict__ y,
+                                                        int64_t rows, int cols, DevTiming *tm) {
+    v_enter(tm);
+    const int c8 = cols >> 3;
+    const int lane = threadIdx.x & 31, sub = lane % L, seg = lane / L;
+    const bool live = sub < c8;
+    float xf[8];
+    {
+        uint4 xv = make_uint4(0u, 0u, 0u, 0u);
+        if (live) xv = ((const uint4 *)x)[sub];
+        const __nv_bfloat162 *x2 = (const __nv_bfloat162 *)&xv;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float2 f = __bfloat1622float2(x2[e]);
+            xf[2 * e] = f.x;
+            xf[2 * e + 1] = f.y;
+        }
+    }
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t w0 = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    constexpr int RPW = 32 / L;  // rows per warp per step
+    for (int64_t r0 = w0 * RPW; r0 < rows; r0 += warps * RPW) {
+        const int64_t r = r0 + seg;
+        float acc = 0.f;
+        if (live && r < rows) {
+            int4 t;
+            asm volatile("ld.global.nc.L1::no_allocate.v4.s32 {%0,%1,%2,%3}, [%4];"
+                         : "=r"(t.x), "=r"(t.y), "=r"(t.z), "=r"(t.w)
+                         : "l"((const uint4 *)(A + r * cols) + sub));
+            const uint4 av = make_uint4((uint32_t)t.x, (uint32_t)t.y, (uint32_t)t.z, (uint32_t)t.w);
+            const __nv_bfloat162 *a2 = (const __nv_bfloat162 *)&av;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float2 af = __bfloat1622float2(a2[e]);
+                acc = fmaf(af.x, xf[2 * e], acc);
+                acc = fmaf(af.y, xf[2 * e + 1], acc);
+            }
+        }
+#pragma unroll
+        for (int o = L / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (sub == 0 && r < rows) y[r] = acc;
+    }
+    v_exit(tm);
+}
+
+// Lanes per row of the short-row GEMV (0 = use the one-warp-per-row kernel).
+int gemv_short_lanes(int64_t cols) {
+    const int64_t c8 = cols >> 3;
+    if (c8 > 32) return 0;
+    int l = 1;
+    while (l < c8) l <<= 1;
+    return l;
+}
+
+const void *gemv_short_fn(int lanes) {
+    switch (lanes) {
+        case 1: return (const void *)gemv_short_kernel<1>;
+        case 2: return (const void *)gemv_short_kernel<2>;
+        case 4: return (const void *)gemv_short_kernel<4>;
+        case 8: return (const void *)gemv_short_kernel<8>;
+        case 16: return (const void *)gemv_short_kernel<16>;
+        default: return (const void *)gemv_short_kernel<32>;
+    }
+}
+
 // ------------------------------------------------------------------ histogram
 // 256 bins of key & 255; one privatised shared-memory histogram per warp,
 // merged into the block's and then atomically into the global bins (which the
@@ -432,10 +502,19 @@ int ifr_victim_shape(ifr_ctx *ctx, const ifr_victim_cfg *c, VictimShape *s) {
             return IFR_OK;
         }
         case IFR_V_GEMV: {
-            s->fn = (const void *)gemv_kernel;
-            s->grid = c->grid ? c->grid : sms * 8;
-            if ((int64_t)s->grid * 8 > c->m) s->grid = (int)((c->m + 7) / 8);
-            s->smem = (int)(c->k * 2);
+            const int lanes = gemv_short_lanes(c->k);
+            if (lanes) {
+                s->fn = gemv_short_fn(lanes);
+                const int64_t rows_per_block = 8 * (32 / lanes);
+                const int64_t need = (c->m + rows_per_block - 1) / rows_per_block;
+                s->grid = c->grid ? c->grid : (int)(need < (int64_t)sms * 8 ? need : (int64_t)sms * 8);
+                s->smem = 0;
+            } else {
+                s->fn = (const void *)gemv_kernel;
+                s->grid = c->grid ? c->grid : sms * 8;
+                if ((int64_t)s->grid * 8 > c->m) s->grid = (int)((c->m + 7) / 8);
+                s->smem = (int)(c->k * 2);
+            }
             s->bytes = 2.0 * (double)c->m * (double)c->k + 2.0 * (double)c->k + 4.0 * (double)c->m;
             s->flops = 2.0 * (double)c->m * (double)c->k;
             return IFR_OK;
@@ -478,12 +557,22 @@ int ifr_victim_enqueue(ifr_ctx *ctx, const ifr_victim_cfg *c, cudaStream_t strea
                 break;
             }
             case IFR_V_GEMV: {
-                if (sh.smem > 48 * 1024)
-                    cudaFuncSetAttribute(gemv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sh.smem);
+                const auto *Ab = (const __nv_bfloat16 *)c->in0;
+                const auto *xb = (const __nv_bfloat16 *)c->in1;
+                float *yo = (float *)c->out;
                 ifr_carveout(sh.fn);
-                gemv_kernel<<<sh.grid, 256, sh.smem, stream>>>((const __nv_bfloat16 *)c->in0,
-                                                               (const __nv_bfloat16 *)c->in1, (float *)c->out, c->m,
-                                                               (int)c->k, tm);
+                switch (gemv_short_lanes(c->k)) {
+                    case 1: gemv_short_kernel<1><<<sh.grid, 256, 0, stream>>>(Ab, xb, yo, c->m, (int)c->k, tm); break;
+                    case 2: gemv_short_kernel<2><<<sh.grid, 256, 0, stream>>>(Ab, xb, yo, c->m, (int)c->k, tm); break;
+                    case 4: gemv_short_kernel<4><<<sh.grid, 256, 0, stream>>>(Ab, xb, yo, c->m, (int)c->k, tm); break;
+                    case 8: gemv_short_kernel<8><<<sh.grid, 256, 0, stream>>>(Ab, xb, yo, c->m, (int)c->k, tm); break;
+                    case 16: gemv_short_kernel<16><<<sh.grid, 256, 0, stream>>>(Ab, xb, yo, c->m, (int)c->k, tm); break;
+                    case 32: gemv_short_kernel<32><<<sh.grid, 256, 0, stream>>>(Ab, xb, yo, c->m, (int)c->k, tm); break;
+                    default:
+                        if (sh.smem > 48 * 1024)
+                            cudaFuncSetAttribute(gemv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sh.smem);
+                        gemv_kernel<<<sh.grid, 256, sh.smem, stream>>>(Ab, xb, yo, c->m, (int)c->k, tm);
+                }
                 break;
             }
             case IFR_V_HIST: {
@@ -568,6 +657,7 @@ extern "C" int ifr_launch_count(ifr_ctx *ctx, uint64_t *out) {
 int ifr_preload_victims() {
     const void *fns[] = {
         (const void *)timing_reset_kernel, (const void *)triad_kernel, (const void *)gemv_kernel,
+        gemv_short_fn(1), gemv_short_fn(2), gemv_short_fn(4), gemv_short_fn(8), gemv_short_fn(16), gemv_short_fn(32),
         (const void *)hist_kernel, (const void *)layernorm_kernel<256, 4>, (const void *)layernorm_kernel<256, 8>,
         (const void *)layernorm_kernel<1024, 8>, (const void *)softmax_kernel<256, 4>,
         (const void *)softmax_kernel<256, 8>, (const void *)softmax_kernel<1024, 8>};

@@ -32,6 +32,11 @@ the library's stressors and victims through the C ABI (no vLLM, cuBLAS or MPS):
   variants  Sec. 5.3, colocation-friendly kernel variants: the BF16 GEMM with 3 TMA
             stages (147 KiB of shared memory) and with 4 (195 KiB), alone and arriving
             at each full-SM stressor: solo throughput against latency beside it.
+  decode    Tables 1 and 2 in the paper's terms: one synthetic decoder layer's decode
+            kernels (batch 64, KV length 4096, hidden 4096) as the victim set, (a) beside
+            the compute kernel at S1..S4 on the same SMs, (b) in one green-context
+            partition beside the copy kernel in the other; per-kernel slowdowns (Fig. 5)
+            and the layer's step latency (the sum of its kernels' per-launch times).
   hol       Sec. 4.2, block-scheduler interference: a 10 ms sleep kernel (one 128-thread
             block per SM) released together with victims of small and large per-block
             footprints: victim latency from the release, alone and beside it, and
@@ -460,7 +465,63 @@ def _with_repeats(v, repeats):
     return c
 
 
-NAMES = ["pitfall1", "pitfall2", "ipc", "fp64", "l2", "l2_green", "smem", "hol", "bandwidth", "variants"]
+def _step(kernels, cells, row_len):
+    """Per-kernel slowdown rows and the decode step latency (us) at each level."""
+    per = lambda t: (t.t_end_ns - t.t_start_ns) / max(1, t.repeats)
+    sl = slowdowns_from_cells(cells, len(kernels), row_len)
+    step = []
+    for lv in range(row_len + 1):
+        tot = 0.0
+        for v, s in enumerate(sl):
+            x = s["slowdown"][lv]
+            tot += s["solo_us"] * (x if x is not None else float("nan"))
+        step.append(round(tot, 1))
+    return sl, step
+
+
+def exp_decode(ctx, repeats, hbm_buf):
+    from . import colocate_config5 as C5
+    S = ctx.info["num_sms"]
+    clk = ctx.info["sm_clock_khz"] * 1e3
+    kern, _keep = C5.decoder_kernels(S, "cuda", phases=("decode",))
+    names = sorted(kern)
+    victims = [kern[n] for n in names]
+    for v in victims:
+        C5.set_launches(ctx, v)
+    # (a) compute kernel S1..S4 on the same SMs (Table 2, Fig. 5)
+    ilps = [1, 2, 4, 8]
+    row = [stressor_cfg(A.IFR_S_FMA, sm_count=S, blocks_per_sm=1, block=128, ilp=i, seed=4) for i in ilps]
+    ipc = [round(issue_rate(P.solo_rate(ctx, c, rounds=32)[0] / 2, S, clk), 3) for c in row]
+    cells = ctx.sweep(victims, [row], repeats=repeats, batched=False)
+    sl_a, step_a = _step(victims, cells, len(row))
+    # (b) the copy kernel in the other green-context partition (Table 1)
+    part = ctx.partition(S // 2, fine=True)
+    try:
+        ns = part["stressor_sms"]
+        levels = [(max(1, ns // 2), 1), (ns, 1), (ns, 2), (ns, 3)]
+        row_b = [stressor_cfg(A.IFR_S_HBM, sm_count=n, blocks_per_sm=b, block=512, buf=hbm_buf,
+                              working_set_bytes=hbm_buf.numel() * 4, seed=1, mask_mode=1) for n, b in levels]
+        for v in victims:
+            C5.set_launches(ctx, v)  # alone on the victim partition
+        cells_b = ctx.sweep(victims, [row_b], repeats=repeats, batched=False)
+        sl_b, step_b = _step(victims, cells_b, len(row_b))
+    finally:
+        ctx.partition_release()
+    return {
+        "experiment": "decode",
+        "paper": "Table 2 (RTX3090 Gemma3-1B TBT 5.59 / 5.75 / 6.00 / 6.24 / 10.74 ms for S0-S4), Table 1 (H100 "
+                 "Llama3.1-8B decode up to 1.3x beside a copy in another green context), Fig. 5 (per-kernel)",
+        "kernels": names,
+        "compute": {"scenarios": ["S0"] + ["S%d (ILP %d)" % (i + 1, x) for i, x in enumerate(ilps)],
+                    "compute_issue_rate": [0.0] + ipc, "step_us": step_a,
+                    "per_kernel": {n: s for n, s in zip(names, sl_a)}},
+        "copy_partition": {"partition": part, "copy_blocks_of_512": [n * b for n, b in levels], "step_us": step_b,
+                           "per_kernel": {n: s for n, s in zip(names, sl_b)}},
+        "note": "step_us[0] is the zero-SM stressor level (harness only, = the kernels alone)",
+    }
+
+
+NAMES = ["pitfall1", "pitfall2", "ipc", "fp64", "l2", "l2_green", "smem", "hol", "bandwidth", "variants", "decode"]
 
 
 def main(argv=None):
@@ -496,6 +557,9 @@ def main(argv=None):
             r = exp_l2(ctx, a.repeats, green=True)
         elif name == "hol":
             r = exp_hol(ctx, a.repeats)
+        elif name == "decode":
+            hbm = hbm if hbm is not None else I.torch_u32_as_i32(1, (4 * GiB) // 4, "cuda")
+            r = exp_decode(ctx, a.repeats, hbm)
         elif name == "variants":
             hbm = hbm if hbm is not None else I.torch_u32_as_i32(1, (4 * GiB) // 4, "cuda")
             r = exp_variants(ctx, a.repeats, hbm)

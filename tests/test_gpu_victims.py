@@ -55,7 +55,9 @@ def test_softmax(ctx, rows, cols):
     assert_fp32_close(y.cpu().numpy()[sel], ref)
 
 
-@pytest.mark.parametrize("rows,cols", [(1, 8), (37, 1000), (300, 4096), (8192, 8192)])
+# rows of up to 256 columns take the short-row kernel (several rows per warp)
+@pytest.mark.parametrize("rows,cols", [(1, 8), (37, 1000), (300, 4096), (8192, 8192), (1000, 128), (77, 256),
+                                       (333, 200), (5, 64), (100003, 8)])
 def test_gemv(ctx, rows, cols):
     Ab = I.torch_normal_bf16(7, rows * cols, "cuda").view(rows, cols)
     xb = I.torch_normal_bf16(8, cols, "cuda")
