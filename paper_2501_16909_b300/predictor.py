@@ -293,6 +293,23 @@ def train(model, Xtr, ytr, Xva, yva, lr=1e-3, batch=512, max_epochs=500, patienc
     return hist
 
 
+def train_ensemble(ctx, Xtr, ytr, Xva, yva, members=5, seed=4, **kw):
+    """`members` MLPs that differ only in their initial weights and batch order
+    (seeds seed, seed + 1, ...), each trained like `train`."""
+    models = []
+    for i in range(members):
+        m = PredictorMLP(ctx, seed=seed + i)
+        train(m, Xtr, ytr, Xva, yva, seed=5 + i, **kw)
+        models.append(m)
+    return models
+
+
+def predict_ensemble(models, X):
+    """Geometric mean of the members' predicted slowdowns (the mean of their log)."""
+    logs = np.stack([np.log(predict(m, X)) for m in models])
+    return np.exp(logs.mean(axis=0))
+
+
 def predict(model, X, batch=512):
     X = torch.as_tensor(X, dtype=torch.float32, device=model.device)
     out = []

@@ -168,3 +168,17 @@ def test_training_reduces_error(ctx):
     hist = PR.train(model, X[:3000], y[:3000], X[3000:3500], y[3000:3500], max_epochs=40, patience=10)
     after = PR.mape(PR.predict(model, X[3500:]), y[3500:])
     assert after < 0.4 * before, (before, after, hist[-3:])
+
+
+def test_ensemble_is_geometric_mean_of_members(ctx):
+    rng = np.random.default_rng(12)
+    n = 2048
+    X = rng.standard_normal((n, 48))
+    y = np.exp(0.3 * np.tanh(X[:, 0] - X[:, 3]) + 0.1)
+    models = PR.train_ensemble(ctx, X[:1500], y[:1500], X[1500:1800], y[1500:1800], members=2, max_epochs=10,
+                               patience=5)
+    assert len(models) == 2
+    p0, p1 = PR.predict(models[0], X[1800:]), PR.predict(models[1], X[1800:])
+    assert not np.allclose(p0, p1)  # members start from different weights
+    pe = PR.predict_ensemble(models, X[1800:])
+    np.testing.assert_allclose(pe, np.sqrt(p0 * p1), rtol=1e-12)
