@@ -27,7 +27,7 @@ import numpy as np
 import torch
 
 from . import _abi as A
-from . import check, stressor_cfg
+from . import check
 
 FEATURES = [
     "frac_hbm", "frac_l2", "frac_tensor", "frac_fp32", "frac_smem", "frac_sched", "conflict_degree",
