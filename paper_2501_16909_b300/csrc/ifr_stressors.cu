@@ -28,8 +28,11 @@ constexpr int kStreamChunksPerRound = 4;  // L2/HBM: chunks per round
 constexpr int kFmaWork = 16384;
 // FP64: steps per chain per round = kFp64Work / ILP (1024 multiplies per thread per round)
 constexpr int kFp64Work = 1024;
-// SMEM: passes over the warp array per round = max(1, 8 / WAYS)
-constexpr int kSmemPassesCF = 8;
+// SMEM: passes over the warp array per round = max(1, 32 / WAYS), so that every
+// conflict degree spends the same 2048 wavefronts per warp per round (32 ld/st
+// pairs per lane per pass, WAYS wavefronts each) and the once-per-round stop /
+// deadline check costs the same small share of every variant
+constexpr int kSmemPassesCF = 32;
 constexpr int kSchedLcgSteps = 16;        // SCHED: LCG steps per block result
 constexpr uint32_t kMaxSpin = 1u << 22;   // iteration cap of every sleep loop
 
@@ -356,10 +359,23 @@ __global__ void __launch_bounds__(1024) sleep_stress_kernel(DevStress *st, Stres
 // Lane l = g*WAYS + r, iteration j: bank = g + (32/WAYS)*(j % WAYS),
 // row = r + WAYS*(j / WAYS), word = 32*row + bank.  For a fixed j the WAYS lanes
 // of a group hit one bank at WAYS distinct rows (WAYS-way conflict); over the 32
-// iterations every lane visits its own 32 words once.
+// iterations every lane visits its own 32 words once.  The conflict-free variant
+// (WAYS = 1) uses 16-byte accesses instead (see the kernel); the checksum does not
+// depend on which lane touches which word.
 template <int WAYS>
 __device__ __forceinline__ int smem_off(int j) {
     return 32 * WAYS * (j / WAYS) + (32 / WAYS) * (j % WAYS);
+}
+
+// 16-byte shared-memory load / store (conflict-free variant): a warp's request
+// covers 512 contiguous bytes, four conflict-free wavefronts per instruction.
+__device__ __forceinline__ void lds_v4(uint32_t addr, uint32_t (&v)[4]) {
+    asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]) : "r"(addr)
+                 : "memory");
+}
+__device__ __forceinline__ void sts_v4(uint32_t addr, const uint32_t (&v)[4]) {
+    asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};" ::"r"(addr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3])
+                 : "memory");
 }
 
 template <int WAYS>
@@ -387,7 +403,27 @@ __global__ void __launch_bounds__(1024) smem_stress_kernel(DevStress *st, Stress
         for (int pass = 0; pass < (WAYS >= kSmemPassesCF ? 1 : kSmemPassesCF / WAYS); ++pass, ++gpass) {
             // even passes update every word (LCG step), odd passes copy it back unchanged
             const uint32_t mul = (gpass & 1) ? 1u : 1664525u, add = (gpass & 1) ? 0u : 1013904223u;
-            if (gpass & 1) {
+            if constexpr (WAYS == 1) {
+                // conflict-free: lane l owns words 4l..4l+3 of every 128-word row, moved
+                // 16 bytes at a time, so the LSU issues one instruction per four
+                // wavefronts instead of one per wavefront; every word is still read and
+                // written once per pass
+                const uint32_t base = (uint32_t)__cvta_generic_to_shared((const void *)arr) + 16u * lane;
+#pragma unroll
+                for (int h = 0; h < 8; h += 4) {
+                    uint32_t v[4][4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) lds_v4(base + 512u * (h + i), v[i]);
+                    if (!(gpass & 1)) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) v[i][e] = v[i][e] * mul + add;
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) sts_v4(base + 512u * (h + i), v[i]);
+                }
+            } else if (gpass & 1) {
 #pragma unroll
                 for (int jb = 0; jb < 32; jb += 8) {
                     uint32_t v[8];

@@ -27,7 +27,7 @@ TILE_MMA_FLOP = 2 * 128 * 128 * 64
 UNIT = {A.IFR_S_HBM: "B", A.IFR_S_L2: "B", A.IFR_S_FMA: "flop", A.IFR_S_TENSOR: "flop", A.IFR_S_SMEM_CF: "wavefront",
         A.IFR_S_SMEM_32W: "wavefront", A.IFR_S_SCHED: "block", A.IFR_S_FP64: "flop", A.IFR_S_SLEEP: "round"}
 # fixed-work rounds of one calibration run per kind (about a millisecond at full SMs)
-CAL_ROUNDS = {A.IFR_S_HBM: 64, A.IFR_S_L2: 256, A.IFR_S_FMA: 32, A.IFR_S_TENSOR: 32, A.IFR_S_SMEM_CF: 64,
+CAL_ROUNDS = {A.IFR_S_HBM: 64, A.IFR_S_L2: 256, A.IFR_S_FMA: 32, A.IFR_S_TENSOR: 32, A.IFR_S_SMEM_CF: 16,
               A.IFR_S_SMEM_32W: 32, A.IFR_S_SCHED: 0, A.IFR_S_FP64: 16, A.IFR_S_SLEEP: 10}
 
 

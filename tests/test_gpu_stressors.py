@@ -118,7 +118,7 @@ def test_smem_stressor_matches_oracle(ctx, kind, ways):
     assert r["status"] == 0 and len(logs) == 2 * (S // 2)
     for L in logs:
         w = ways or (1 if kind == A.IFR_S_SMEM_CF else 32)
-        passes = max(1, 8 // w)  # passes over the warp array per round
+        passes = max(1, 32 // w)  # passes over the warp array per round
         assert L["checksum"] == oracle.smem_block(5, L["index"], 8, 3, passes)
         assert L["work"] == 3 * passes * 32
     assert {L["smid"] for L in logs} <= spread_mask(S, S // 2)

@@ -186,6 +186,23 @@ def smem_word(lane, j, ways):
     return row * 32 + bank
 
 
+def test_smem_conflict_free_vector_mapping():
+    # the conflict-free kernel: lane l, access i (0..7), word e (0..3) -> 128*i + 4*l + e.
+    # Every word of the warp's 1024 is visited once per pass, and each quarter-warp
+    # phase of a 16-byte request (8 lanes x 4 words) covers the 32 banks once.
+    seen = []
+    for i in range(8):
+        for quarter in range(4):
+            banks = set()
+            for l in range(8 * quarter, 8 * quarter + 8):
+                for e in range(4):
+                    w = 128 * i + 4 * l + e
+                    seen.append(w)
+                    banks.add(w % 32)
+            assert banks == set(range(32))
+    assert sorted(seen) == list(range(1024))
+
+
 @pytest.mark.parametrize("ways", [1, 2, 4, 8, 16, 32])
 def test_smem_mapping_bijective_and_conflict_degree(ways):
     seen = set()
