@@ -194,6 +194,9 @@ def main(argv=None):
     ap.add_argument("--pairs-npz", default=None, help="configuration-4 pairs saved by train_predictor --save")
     ap.add_argument("--save", default=None)
     ap.add_argument("--members", type=int, default=5, help="MLPs in the predictor ensemble")
+    ap.add_argument("--occupancy-csv", default=None,
+                    help="ncu achieved-occupancy capture of the kernels (profile_case config5_kernels): "
+                         "adds the Usher / Orion pairing rules' scores")
     a = ap.parse_args(argv)
     log = lambda *x: print(*x, file=sys.stderr)  # noqa: E731
     ctx = ifr.Context(0)
@@ -298,7 +301,17 @@ def main(argv=None):
         "mlp_mape_prefill_victims": round(PR.mape(pred[len(m_dp):], yt[len(m_dp):]), 4),
         "pairs": [{"victim": names[v], "corunner": names[c], "measured": round(s, 4), "mlp": round(float(p), 4),
                    "baseline": round(float(b), 4)} for (v, c, s), p, b in zip(pairs, pred, base_pred)],
+        "kernel_info": {n: {"flops": prof["flops_per_launch"], "bytes": prof["bytes_per_launch"],
+                            "uses_tensor": bool(prof["uses_tensor"])}
+                        for n, prof in ((n, ctx.victim_profile(c)) for n, c in zip(names, cfgs))},
+        "peaks": {"tensor": pk[A.IFR_S_TENSOR][0], "fp32": pk[A.IFR_S_FMA][0], "hbm": pk[A.IFR_S_HBM][0]},
     }
+    if a.occupancy_csv:
+        from paper_2501_16909_b300 import pairing
+
+        with open(a.occupancy_csv) as f:
+            occ = pairing.occupancy_by_kernel(names, pairing.parse_ncu_occupancy(f.read()))
+        out["pairing"] = pairing.evaluate(out["pairs"], out["kernel_info"], occ, out["peaks"])
     if a.save:
         np.savez(a.save, X=X, y=y, Xt=Xt, yt=yt, pred=pred, base=base_pred)
     ctx.close()

@@ -7,7 +7,8 @@ one kernel kind in isolation on a small case so that a profiler can capture it:
     python -m paper_2501_16909_b300.profile_case <case> [--repeat N]
 
 cases: hbm, l2, fma, tensor, smem_cf, smem_32w, sched, fp64, sleep, gemm, gemv,
-layernorm, softmax, hist, triad; and victim_bandwidth, which times every memory-bound
+layernorm, softmax, hist, triad; config5_kernels, one launch of each configuration-5
+decoder-layer kernel in order; and victim_bandwidth, which times every memory-bound
 configuration-2 victim alone over grids of 0 (default), 1, 2, 4, 8 and 16 blocks per
 SM (20 launches after a warm measurement) and prints one JSON line per run; and
 l2_set_sweep, which times the stream kernel on every SM (256 rounds per block) over
@@ -56,6 +57,19 @@ def main(argv=None):
                                        working_set_bytes=mib << 20)
                 rate, _res = P.solo_rate(ctx, cfg, rounds=256)
                 print(json.dumps({"mib": mib, "block": block, "blocks_per_sm": bps, "gbs": round(rate / 1e9, 1)}))
+        ctx.close()
+        return
+    if a.case == "config5_kernels":
+        # one launch of every configuration-5 decoder-layer kernel, in the order of
+        # colocate_config5's kernel list (an occupancy capture matches rows by order)
+        from paper_2501_16909_b300.colocate_config5 import decoder_kernels
+
+        kern, _t = decoder_kernels(S, "cuda")
+        for name, v in kern.items():
+            v.repeats = 1
+            t = ctx.victim_launch(v)
+            print(json.dumps({"kernel": name, "event_ms": round(t["event_ms"], 4), "status": t["status"]}))
+        torch.cuda.synchronize()
         ctx.close()
         return
     if a.case == "victim_bandwidth":
