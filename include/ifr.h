@@ -239,7 +239,10 @@ typedef struct {
     int32_t variant;       /* GEMM: 0 = colocation-friendly (3 TMA stages, 147 KiB of shared
                               memory: leaves room for a stressor block, Sec. 5.3),
                               1 = throughput (4 stages, 195 KiB: more operand bytes in
-                              flight, but no shared-memory stressor block fits beside it).
+                              flight, but no shared-memory stressor block fits beside it),
+                              2 = CTA pairs (a 2-CTA cluster per 256 x 256 tile with
+                              tcgen05 cta_group::2, 4 stages of 32 KiB per SM, 145 KiB;
+                              m and n must be multiples of 256, else IFR_ERR_ARG).
                               Other kinds: 0. */
     int32_t reserved;
 } ifr_victim_cfg;

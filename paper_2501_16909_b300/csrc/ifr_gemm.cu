@@ -258,6 +258,227 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_kernel(const __grid
     }
 }
 
+// ------------------------------------------------------------------ 2-SM pair tiles
+// Variant 2: a cluster of two CTAs on two SMs takes 256 x 256 output tiles with
+// tcgen05.mma.cta_group::2 (M = 256, N = 256, K = 16), issued by the even CTA (the
+// leader).  Each CTA loads its own 128 rows of A and its own 128 rows of B per 64-wide
+// K slice: 32 KiB per stage per SM where the single-CTA tile needs 48 KiB for the same
+// MMA work, and four stages fit in 128 KiB.  Each CTA holds its 128 rows of the
+// accumulator in 256 of its own TMEM columns and stores them.
+//   warp 0, lane 0   TMA producer in both CTAs; in the leader also the tile
+//                    scheduler, which writes each tile index into both CTAs' rings;
+//                    both producers complete their bytes on the leader's stage barrier
+//   warp 1           allocates the pair's TMEM (both CTAs); leader lane 0 issues the
+//                    MMAs and commits each stage and each finished tile to both CTAs
+//   warps 2..5       epilogue of the CTA's own 128 accumulator rows; the leader's
+//                    MMAs wait for both CTAs' epilogues before the next tile
+// Tiles are handed out as in the single-CTA kernel (first tile = cluster index, later
+// ones from the device counter).  Waits are bounded; a teardown cluster barrier
+// keeps each CTA resident until the other has finished touching its shared memory.
+constexpr int PAIR_M = 256, PAIR_N = 256, HALF = 128;
+
+template <int STAGES>
+struct PairCfg {
+    static constexpr int A_BYTES = HALF * BK * 2;
+    static constexpr int B_BYTES = HALF * BK * 2;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    // + alignment slack + barriers / ring + a 16 KiB guard band, which keeps every
+    // operand read that starts in the last stage inside the CTA's allocation
+    static constexpr int SMEM = STAGES * STAGE + 1024 + 256 + 16384;
+};
+
+template <int STAGES>
+__global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_pair_kernel(const __grid_constant__ CUtensorMap ta,
+                                                                         const __grid_constant__ CUtensorMap tb,
+                                                                         float *__restrict__ C, int M, int N,
+                                                                         int K, DevTiming *tm) {
+    using Cf = PairCfg<STAGES>;
+    constexpr int CHUNKS = PAIR_N / 16;
+    constexpr uint16_t kBoth = 3;
+    extern __shared__ uint8_t g_smem_raw[];
+    uint8_t *base = (uint8_t *)(((uintptr_t)g_smem_raw + 1023u) & ~(uintptr_t)1023u);
+    uint64_t *full = (uint64_t *)(base + STAGES * Cf::STAGE);  // [STAGES], used in the leader
+    uint64_t *empty = full + STAGES;                            // [STAGES], both CTAs
+    uint64_t *tfull = empty + STAGES;                           // both CTAs
+    uint64_t *tempty = tfull + 1;                               // leader
+    uint64_t *sfull = tempty + 1;                               // [RING], both CTAs
+    uint64_t *sempty = sfull + RING;                            // [RING], leader
+    int32_t *ring = (int32_t *)(sempty + RING);
+    uint32_t *tmem_slot = (uint32_t *)(ring + RING);
+    volatile int *fail = (volatile int *)(tmem_slot + 1);
+
+    if (tc::cluster_nctarank() != 2) {  // not launched as CTA pairs: touch nothing shared
+        if (threadIdx.x == 0) tm->status = IFR_ERR_LAUNCH;
+        return;
+    }
+    const uint32_t rank = tc::cluster_ctarank();
+    const bool leader = rank == 0;
+    if (threadIdx.x == 0) g_stamp(tm, true);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles_n = N / PAIR_N, n_tiles = (M / PAIR_M) * tiles_n;
+    const int KT = K / BK;
+    const uint64_t deadline = ifr_gtimer() + kGemmTimeoutNs;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            tc::mbar_init(&full[s], 2);   // both producers' expect_tx arrivals
+            tc::mbar_init(&empty[s], 1);  // the leader's MMA commit
+        }
+        for (int r = 0; r < RING; ++r) {
+            tc::mbar_init(&sfull[r], 1);
+            tc::mbar_init(&sempty[r], 2 * (1 + EPI_WARPS));  // leader MMA + peer producer + 2 x 4 epilogue warps
+        }
+        tc::mbar_init(tfull, 1);
+        tc::mbar_init(tempty, 2 * EPI_WARPS);
+        *fail = 0;
+        tc::fence_mbar_init();
+        tc::prefetch_tmap(&ta);
+        tc::prefetch_tmap(&tb);
+    }
+    if (warp == 1) {
+        tc::tmem_alloc_pair(tmem_slot, PAIR_N);
+        tc::tmem_relinquish_pair();
+    }
+    tc::fence_before();
+    tc::cluster_sync();  // both CTAs' barriers are initialised before any remote arrival
+    tc::fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        int64_t g = 0;
+        uint32_t next = blockIdx.x >> 1;  // leader: first tile = cluster index, later ones from the counter
+        for (int j = 0;; ++j) {
+            const int r = j % RING;
+            int tile;
+            if (leader) {
+                if (j >= RING && !tc::mbar_wait_cluster(&sempty[r], (uint32_t)((j / RING) - 1) & 1u, deadline))
+                    *fail = 1;
+                tile = (*fail || next >= (uint32_t)n_tiles) ? -1 : (int)next;
+                ring[r] = tile;
+                tc::st_remote_s32(tc::mapa(&ring[r], 1), tile);
+                tc::mbar_arrive(&sfull[r]);
+                tc::mbar_arrive_remote(tc::mapa(&sfull[r], 1));  // release: orders the remote ring store
+            } else {
+                const bool got = tc::mbar_wait_cluster(&sfull[r], (uint32_t)(j / RING) & 1u, deadline + 50000000ull);
+                tile = got ? ring[r] : -1;
+                if (!got) *fail = 1;
+                tc::mbar_arrive_remote(tc::mapa(&sempty[r], 0));
+            }
+            if (tile < 0) break;
+            const int m0 = (tile / tiles_n) * PAIR_M + (int)rank * HALF;
+            const int n0 = (tile % tiles_n) * PAIR_N + (int)rank * HALF;
+            for (int kt = 0; kt < KT; ++kt, ++g) {
+                const int s = (int)(g % STAGES);
+                if (leader && kt == KT - 1) next = (gridDim.x >> 1) + atomicAdd(&tm->tile_next, 1u);
+                if (g >= STAGES && !tc::mbar_wait_cluster(&empty[s], (uint32_t)((g / STAGES) - 1) & 1u, deadline)) {
+                    *fail = 1;
+                    break;
+                }
+                uint8_t *sa = base + s * Cf::STAGE;
+                const uint32_t fb = tc::mapa(&full[s], 0);
+                tc::mbar_arrive_expect_tx_remote(fb, (uint32_t)Cf::STAGE);
+                tc::tma_load_2d_pair(sa, &ta, fb, kt * BK, m0);
+                tc::tma_load_2d_pair(sa + Cf::A_BYTES, &tb, fb, kt * BK, n0);
+            }
+        }
+        // the leader's MMAs have read the last stages of this CTA's shared memory and
+        // their commits to this CTA's barriers have landed
+        for (int64_t q = g - STAGES < 0 ? 0 : g - STAGES; q < g; ++q)
+            tc::mbar_wait_cluster(&empty[q % STAGES], (uint32_t)(q / STAGES) & 1u, deadline + 100000000ull);
+    } else if (warp == 1 && lane == 0 && leader) {
+        constexpr uint32_t idesc = tc::idesc_bf16_f32(PAIR_M, PAIR_N);
+        int64_t g = 0;
+        for (int j = 0;; ++j) {
+            const int r = j % RING;
+            const bool got = tc::mbar_wait(&sfull[r], (uint32_t)(j / RING) & 1u, deadline + 50000000ull);
+            const int tile = got ? ring[r] : -1;
+            tc::mbar_arrive(&sempty[r]);
+            if (!got) *fail = 1;
+            if (tile < 0) break;
+            if (j > 0 && !tc::mbar_wait_cluster(tempty, (uint32_t)((j - 1) & 1), deadline)) {
+                *fail = 1;
+                tc::mma_commit_pair(tfull, kBoth);
+                continue;  // read the ring on to its end marker
+            }
+            tc::fence_after();
+            for (int kt = 0; kt < KT; ++kt, ++g) {
+                const int s = (int)(g % STAGES);
+                if (!tc::mbar_wait_cluster(&full[s], (uint32_t)(g / STAGES) & 1u, deadline)) {
+                    *fail = 1;
+                    break;
+                }
+                tc::fence_after();
+                const uint32_t sa = tc::smem_u32(base + s * Cf::STAGE);
+                const uint64_t adesc = tc::desc_sw128(sa);
+                const uint64_t bdesc = tc::desc_sw128(sa + Cf::A_BYTES);
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk)
+                    tc::mma_bf16_pair(tmem, adesc + 2ull * kk, bdesc + 2ull * kk, idesc, (uint32_t)((kt | kk) != 0));
+                tc::mma_commit_pair(&empty[s], kBoth);
+            }
+            tc::mma_commit_pair(tfull, kBoth);  // also on failure, so both epilogues' waits complete
+        }
+    } else if (warp >= 2) {
+        const int q = warp & 3;  // TMEM lane quadrant this warp may access
+        const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
+        for (int j = 0;; ++j) {
+            const int r = j % RING;
+            const bool got = tc::mbar_wait_cluster(&sfull[r], (uint32_t)(j / RING) & 1u, deadline + 50000000ull);
+            const int tile = got ? ring[r] : -1;
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive_remote(tc::mapa(&sempty[r], 0));
+            if (!__all_sync(0xffffffffu, got)) {
+                if (lane == 0) *fail = 1;
+                break;
+            }
+            if (tile < 0) break;
+            const bool ok = tc::mbar_wait_cluster(tfull, (uint32_t)(j & 1), deadline + 100000000ull);
+            tc::fence_after();
+            if (!__all_sync(0xffffffffu, ok && !*fail)) {
+                if (lane == 0) *fail = 1;
+                break;
+            }
+            const int m0 = (tile / tiles_n) * PAIR_M + (int)rank * HALF, n0 = (tile % tiles_n) * PAIR_N;
+            float *crow = C + (size_t)(m0 + q * 32 + lane) * (size_t)N + n0;
+            uint32_t ra[16], rb[16];
+            tc::tmem_ld16(trow, ra);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int c = 0; c < CHUNKS; c += 2) {
+                tc::tmem_ld16(trow + (uint32_t)((c + 1) * 16), rb);
+                store_row16(crow + c * 16, ra);
+                tc::tmem_ld_wait();
+                if (c + 2 < CHUNKS) {
+                    tc::tmem_ld16(trow + (uint32_t)((c + 2) * 16), ra);
+                    store_row16(crow + (c + 1) * 16, rb);
+                    tc::tmem_ld_wait();
+                } else {
+                    tc::fence_before();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive_remote(tc::mapa(tempty, 0));  // this half of the accumulator is drained
+                    store_row16(crow + (c + 1) * 16, rb);
+                }
+            }
+            if (warp == 2 && lane == 0) g_stamp(tm, false);
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::cluster_sync();  // every remote arrival and every MMA into this CTA's TMEM is done
+    if (warp == 1) {
+        tc::fence_after();
+        tc::tmem_dealloc_pair(tmem, PAIR_N);
+    }
+    if (threadIdx.x == 0 && *fail) tm->status = IFR_ERR_TIMEOUT;
+    g_exit(tm);
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&tm->tile_done, 1u) == gridDim.x - 1u) {
+            atomicExch(&tm->tile_next, 0u);
+            atomicExch(&tm->tile_done, 0u);
+        }
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -312,10 +533,88 @@ int launch_gemm(const ifr_victim_cfg *c, cudaStream_t stream, DevTiming *tm) {
     return IFR_OK;
 }
 
+constexpr int PAIR_STAGES = 4;
+
+const void *gemm_pair_fn() {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(gemm_bf16_pair_kernel<PAIR_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             PairCfg<PAIR_STAGES>::SMEM);
+        attr = true;
+    }
+    return (const void *)gemm_bf16_pair_kernel<PAIR_STAGES>;
+}
+
+void pair_launch_cfg(cudaLaunchConfig_t *cfg, cudaLaunchAttribute *at, int grid, cudaStream_t stream) {
+    memset(cfg, 0, sizeof(*cfg));
+    memset(at, 0, sizeof(*at));
+    cfg->gridDim = dim3((unsigned)grid);
+    cfg->blockDim = dim3(GEMM_THREADS);
+    cfg->dynamicSmemBytes = PairCfg<PAIR_STAGES>::SMEM;
+    cfg->stream = stream;
+    at->id = cudaLaunchAttributeClusterDimension;
+    at->val.clusterDim.x = 2;
+    at->val.clusterDim.y = 1;
+    at->val.clusterDim.z = 1;
+    cfg->attrs = at;
+    cfg->numAttrs = 1;
+}
+
+// CTA pairs the device can hold at once (pairs must sit in one GPC), asked once.
+int pair_clusters() {
+    static int n = 0;
+    if (n == 0) {
+        ifr_carveout(gemm_pair_fn());
+        cudaLaunchConfig_t cfg;
+        cudaLaunchAttribute at;
+        pair_launch_cfg(&cfg, &at, 2 * (g_num_sms / 2), nullptr);
+        int c = 0;
+        if (cudaOccupancyMaxActiveClusters(&c, gemm_bf16_pair_kernel<PAIR_STAGES>, &cfg) != cudaSuccess || c <= 0) {
+            cudaGetLastError();
+            c = g_num_sms / 2;
+        }
+        n = c < g_num_sms / 2 ? c : g_num_sms / 2;
+    }
+    return n;
+}
+
+int pair_grid(const ifr_victim_cfg *c) {
+    const int tiles = (int)((c->n / PAIR_N) * (c->m / PAIR_M));
+    const int cl = pair_clusters();
+    return 2 * (tiles < cl ? tiles : cl);
+}
+
+int launch_gemm_pair(const ifr_victim_cfg *c, cudaStream_t stream, DevTiming *tm) {
+    gemm_pair_fn();
+    CUtensorMap ta, tb;
+    int rc = make_map(&ta, c->in0, c->m, c->k, HALF);
+    if (rc) return rc;
+    rc = make_map(&tb, c->in1, c->n, c->k, HALF);
+    if (rc) return rc;
+    ifr_carveout(gemm_pair_fn());
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute at;
+    pair_launch_cfg(&cfg, &at, pair_grid(c), stream);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, gemm_bf16_pair_kernel<PAIR_STAGES>, ta, tb, (float *)c->out,
+                                             (int)c->m, (int)c->n, (int)c->k, tm);
+    return e == cudaSuccess ? IFR_OK : IFR_ERR_LAUNCH;
+}
+
 }  // namespace
 
 int ifr_gemm_shape(const ifr_victim_cfg *c, VictimShape *s) {
     if (g_num_sms == 0) cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, 0);
+    if (c->variant == 2) {
+        s->fn = gemm_pair_fn();
+        s->grid = pair_grid(c);
+        s->block = GEMM_THREADS;
+        s->smem = PairCfg<PAIR_STAGES>::SMEM;
+        s->tmem_cols = PAIR_N;
+        s->uses_tensor = 1;
+        s->flops = 2.0 * (double)c->m * (double)c->n * (double)c->k;
+        s->bytes = 2.0 * ((double)c->m + (double)c->n) * (double)c->k + 4.0 * (double)c->m * (double)c->n;
+        return IFR_OK;
+    }
     const bool wide = c->n % 256 == 0, deep = c->variant == 1;
     s->fn = wide ? (deep ? gemm_fn<256, 4>() : gemm_fn<256, 3>()) : (deep ? gemm_fn<128, 4>() : gemm_fn<128, 3>());
     const int tiles = (int)((c->n / (wide ? 256 : 128)) * (c->m / BM));
@@ -333,13 +632,15 @@ int ifr_gemm_shape(const ifr_victim_cfg *c, VictimShape *s) {
 int ifr_gemm_enqueue(ifr_ctx *ctx, const ifr_victim_cfg *c, cudaStream_t stream, DevTiming *tm) {
     g_num_sms = ctx->info.num_sms;
     if (c->m > 65535 * BM || c->n > (1ll << 30) || c->k > (1ll << 30)) return IFR_ERR_ARG;
+    if (c->variant == 2) return launch_gemm_pair(c, stream, tm);
     const bool deep = c->variant == 1;
     if (c->n % 256 == 0) return deep ? launch_gemm<256, 4>(c, stream, tm) : launch_gemm<256, 3>(c, stream, tm);
     return deep ? launch_gemm<128, 4>(c, stream, tm) : launch_gemm<128, 3>(c, stream, tm);
 }
 
 int ifr_preload_gemm() {
-    const void *fns[] = {gemm_fn<128, 3>(), gemm_fn<256, 3>(), gemm_fn<128, 4>(), gemm_fn<256, 4>()};
+    const void *fns[] = {gemm_fn<128, 3>(), gemm_fn<256, 3>(), gemm_fn<128, 4>(), gemm_fn<256, 4>(),
+                         gemm_pair_fn()};
     for (const void *f : fns) {
         int rc = ifr_preload(f);
         if (rc) return rc;
