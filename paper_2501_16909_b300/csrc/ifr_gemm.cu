@@ -75,6 +75,23 @@ __device__ __forceinline__ void g_exit(DevTiming *tm) {
     }
 }
 
+// Tile index -> (tile row, tile column) in groups of `group_m` tile rows: consecutive
+// tiles walk down a group's rows before moving one tile column right, so the tiles in
+// flight at once share a few A and B panels in L2 instead of sweeping every B panel
+// while they share one A panel.  group_m = 1 is row-major order, which the launch
+// keeps when A and B fit in L2 together (measured at 4096^3: grouping there read 20 %
+// more DRAM bytes).  Every tile is still computed the same way; only the order in
+// which tiles are handed out changes.
+constexpr int GROUP_M = 8;
+__device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, int group_m, int &tm, int &tn) {
+    const int per_group = group_m * tiles_n;
+    const int first_m = (tile / per_group) * group_m;
+    const int rows = tiles_m - first_m < group_m ? tiles_m - first_m : group_m;
+    const int in_group = tile % per_group;
+    tm = first_m + in_group % rows;
+    tn = in_group / rows;
+}
+
 // 16 consecutive fp32 values of one C row (64 B) as four 16-byte stores.
 __device__ __forceinline__ void store_row16(float *dst, const uint32_t (&r)[16]) {
     float4 *d = (float4 *)dst;
@@ -88,7 +105,7 @@ template <int BN, int STAGES>
 __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_kernel(const __grid_constant__ CUtensorMap ta,
                                                                     const __grid_constant__ CUtensorMap tb,
                                                                     float *__restrict__ C, int M, int N, int K,
-                                                                    DevTiming *tm) {
+                                                                    int group_m, DevTiming *tm) {
     using Cf = GemmCfg<BN, STAGES>;
     constexpr int CHUNKS = BN / 16;
     extern __shared__ uint8_t g_smem_raw[];
@@ -105,7 +122,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_kernel(const __grid
 
     if (threadIdx.x == 0) g_stamp(tm, true);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tiles_n = N / BN, n_tiles = (M / BM) * tiles_n;
+    const int tiles_m = M / BM, tiles_n = N / BN, n_tiles = tiles_m * tiles_n;
     const int KT = K / BK;
     const uint64_t deadline = ifr_gtimer() + kGemmTimeoutNs;
     if (threadIdx.x == 0) {
@@ -146,7 +163,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_kernel(const __grid
             ring[r] = tile;
             tc::mbar_arrive(&sfull[r]);  // release: the index is visible to the waiting roles
             if (tile < 0) break;
-            const int m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
+            int tmi, tni;
+            tile_coords(tile, tiles_m, tiles_n, group_m, tmi, tni);
+            const int m0 = tmi * BM, n0 = tni * BN;
             for (int kt = 0; kt < KT; ++kt, ++g) {
                 const int s = (int)(g % STAGES);
                 if (kt == KT - 1) next = gridDim.x + atomicAdd(&tm->tile_next, 1u);
@@ -216,7 +235,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_kernel(const __grid
                 if (lane == 0) *fail = 1;
                 break;
             }
-            const int m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
+            int tmi, tni;
+            tile_coords(tile, tiles_m, tiles_n, group_m, tmi, tni);
+            const int m0 = tmi * BM, n0 = tni * BN;
             float *crow = C + (size_t)(m0 + q * 32 + lane) * (size_t)N + n0;
             uint32_t ra[16], rb[16];
             tc::tmem_ld16(trow, ra);
@@ -259,15 +280,19 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_kernel(const __grid
 }
 
 // ------------------------------------------------------------------ 2-SM pair tiles
-// Variant 2: a cluster of two CTAs on two SMs takes 256 x 256 output tiles with
+// Variants 2 and 3: a cluster of two CTAs on two SMs takes 256 x 256 output tiles with
 // tcgen05.mma.cta_group::2 (M = 256, N = 256, K = 16), issued by the even CTA (the
 // leader).  Each CTA loads its own 128 rows of A and its own 128 rows of B per 64-wide
 // K slice: 32 KiB per stage per SM where the single-CTA tile needs 48 KiB for the same
-// MMA work, and four stages fit in 128 KiB.  Each CTA holds its 128 rows of the
-// accumulator in 256 of its own TMEM columns and stores them.
+// MMA work.  Variant 2 keeps four stages (129 KiB, room for a stressor block beside
+// it), variant 3 six (193 KiB, more bytes in flight).  Each CTA holds its 128 rows of
+// the accumulator in 256 of its own TMEM columns and stores them.
 //   warp 0, lane 0   TMA producer in both CTAs; in the leader also the tile
-//                    scheduler, which writes each tile index into both CTAs' rings;
-//                    both producers complete their bytes on the leader's stage barrier
+//                    scheduler, which writes each tile index into both CTAs' rings.
+//                    Both producers complete their bytes on the leader's stage
+//                    barrier, whose one arrival (the leader's) expects both CTAs'
+//                    bytes: the other CTA's copies may land first, the pending
+//                    arrival keeps the phase open until the leader has posted
 //   warp 1           allocates the pair's TMEM (both CTAs); leader lane 0 issues the
 //                    MMAs and commits each stage and each finished tile to both CTAs
 //   warps 2..5       epilogue of the CTA's own 128 accumulator rows; the leader's
@@ -282,16 +307,14 @@ struct PairCfg {
     static constexpr int A_BYTES = HALF * BK * 2;
     static constexpr int B_BYTES = HALF * BK * 2;
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    // + alignment slack + barriers / ring + a 16 KiB guard band, which keeps every
-    // operand read that starts in the last stage inside the CTA's allocation
-    static constexpr int SMEM = STAGES * STAGE + 1024 + 256 + 16384;
+    static constexpr int SMEM = STAGES * STAGE + 1024 + 256;  // + alignment slack + barriers / ring
 };
 
 template <int STAGES>
 __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_pair_kernel(const __grid_constant__ CUtensorMap ta,
                                                                          const __grid_constant__ CUtensorMap tb,
                                                                          float *__restrict__ C, int M, int N,
-                                                                         int K, DevTiming *tm) {
+                                                                         int K, int group_m, DevTiming *tm) {
     using Cf = PairCfg<STAGES>;
     constexpr int CHUNKS = PAIR_N / 16;
     constexpr uint16_t kBoth = 3;
@@ -315,12 +338,12 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_pair_kernel(const _
     const bool leader = rank == 0;
     if (threadIdx.x == 0) g_stamp(tm, true);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tiles_n = N / PAIR_N, n_tiles = (M / PAIR_M) * tiles_n;
+    const int tiles_m = M / PAIR_M, tiles_n = N / PAIR_N, n_tiles = tiles_m * tiles_n;
     const int KT = K / BK;
     const uint64_t deadline = ifr_gtimer() + kGemmTimeoutNs;
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
-            tc::mbar_init(&full[s], 2);   // both producers' expect_tx arrivals
+            tc::mbar_init(&full[s], 1);   // the leader's expect_tx for both CTAs' bytes
             tc::mbar_init(&empty[s], 1);  // the leader's MMA commit
         }
         for (int r = 0; r < RING; ++r) {
@@ -364,18 +387,19 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_pair_kernel(const _
                 tc::mbar_arrive_remote(tc::mapa(&sempty[r], 0));
             }
             if (tile < 0) break;
-            const int m0 = (tile / tiles_n) * PAIR_M + (int)rank * HALF;
-            const int n0 = (tile % tiles_n) * PAIR_N + (int)rank * HALF;
+            int tmi, tni;
+            tile_coords(tile, tiles_m, tiles_n, group_m, tmi, tni);
+            const int m0 = tmi * PAIR_M + (int)rank * HALF, n0 = tni * PAIR_N + (int)rank * HALF;
             for (int kt = 0; kt < KT; ++kt, ++g) {
                 const int s = (int)(g % STAGES);
                 if (leader && kt == KT - 1) next = (gridDim.x >> 1) + atomicAdd(&tm->tile_next, 1u);
-                if (g >= STAGES && !tc::mbar_wait_cluster(&empty[s], (uint32_t)((g / STAGES) - 1) & 1u, deadline)) {
+                if (g >= STAGES && !tc::mbar_wait(&empty[s], (uint32_t)((g / STAGES) - 1) & 1u, deadline)) {
                     *fail = 1;
                     break;
                 }
                 uint8_t *sa = base + s * Cf::STAGE;
                 const uint32_t fb = tc::mapa(&full[s], 0);
-                tc::mbar_arrive_expect_tx_remote(fb, (uint32_t)Cf::STAGE);
+                if (leader) tc::mbar_arrive_expect_tx(&full[s], 2u * (uint32_t)Cf::STAGE);
                 tc::tma_load_2d_pair(sa, &ta, fb, kt * BK, m0);
                 tc::tma_load_2d_pair(sa + Cf::A_BYTES, &tb, fb, kt * BK, n0);
             }
@@ -383,7 +407,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_pair_kernel(const _
         // the leader's MMAs have read the last stages of this CTA's shared memory and
         // their commits to this CTA's barriers have landed
         for (int64_t q = g - STAGES < 0 ? 0 : g - STAGES; q < g; ++q)
-            tc::mbar_wait_cluster(&empty[q % STAGES], (uint32_t)(q / STAGES) & 1u, deadline + 100000000ull);
+            tc::mbar_wait(&empty[q % STAGES], (uint32_t)(q / STAGES) & 1u, deadline + 100000000ull);
     } else if (warp == 1 && lane == 0 && leader) {
         constexpr uint32_t idesc = tc::idesc_bf16_f32(PAIR_M, PAIR_N);
         int64_t g = 0;
@@ -402,7 +426,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_pair_kernel(const _
             tc::fence_after();
             for (int kt = 0; kt < KT; ++kt, ++g) {
                 const int s = (int)(g % STAGES);
-                if (!tc::mbar_wait_cluster(&full[s], (uint32_t)(g / STAGES) & 1u, deadline)) {
+                if (!tc::mbar_wait(&full[s], (uint32_t)(g / STAGES) & 1u, deadline)) {
                     *fail = 1;
                     break;
                 }
@@ -431,13 +455,15 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_pair_kernel(const _
                 break;
             }
             if (tile < 0) break;
-            const bool ok = tc::mbar_wait_cluster(tfull, (uint32_t)(j & 1), deadline + 100000000ull);
+            const bool ok = tc::mbar_wait(tfull, (uint32_t)(j & 1), deadline + 100000000ull);
             tc::fence_after();
             if (!__all_sync(0xffffffffu, ok && !*fail)) {
                 if (lane == 0) *fail = 1;
                 break;
             }
-            const int m0 = (tile / tiles_n) * PAIR_M + (int)rank * HALF, n0 = (tile % tiles_n) * PAIR_N;
+            int tmi, tni;
+            tile_coords(tile, tiles_m, tiles_n, group_m, tmi, tni);
+            const int m0 = tmi * PAIR_M + (int)rank * HALF, n0 = tni * PAIR_N;
             float *crow = C + (size_t)(m0 + q * 32 + lane) * (size_t)N + n0;
             uint32_t ra[16], rb[16];
             tc::tmem_ld16(trow, ra);
@@ -518,7 +544,7 @@ const void *gemm_fn() {
 }
 
 template <int BN, int ST>
-int launch_gemm(const ifr_victim_cfg *c, cudaStream_t stream, DevTiming *tm) {
+int launch_gemm(const ifr_victim_cfg *c, cudaStream_t stream, int group_m, DevTiming *tm) {
     gemm_fn<BN, ST>();
     CUtensorMap ta, tb;
     int rc = make_map(&ta, c->in0, c->m, c->k, BM);
@@ -529,28 +555,28 @@ int launch_gemm(const ifr_victim_cfg *c, cudaStream_t stream, DevTiming *tm) {
     const int tiles = (int)((c->n / BN) * (c->m / BM));
     const int grid = tiles < g_num_sms ? tiles : g_num_sms;
     gemm_bf16_kernel<BN, ST><<<grid, GEMM_THREADS, GemmCfg<BN, ST>::SMEM, stream>>>(
-        ta, tb, (float *)c->out, (int)c->m, (int)c->n, (int)c->k, tm);
+        ta, tb, (float *)c->out, (int)c->m, (int)c->n, (int)c->k, group_m, tm);
     return IFR_OK;
 }
 
-constexpr int PAIR_STAGES = 4;
-
+template <int ST>
 const void *gemm_pair_fn() {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(gemm_bf16_pair_kernel<PAIR_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             PairCfg<PAIR_STAGES>::SMEM);
+        cudaFuncSetAttribute(gemm_bf16_pair_kernel<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             PairCfg<ST>::SMEM);
         attr = true;
     }
-    return (const void *)gemm_bf16_pair_kernel<PAIR_STAGES>;
+    return (const void *)gemm_bf16_pair_kernel<ST>;
 }
 
+template <int ST>
 void pair_launch_cfg(cudaLaunchConfig_t *cfg, cudaLaunchAttribute *at, int grid, cudaStream_t stream) {
     memset(cfg, 0, sizeof(*cfg));
     memset(at, 0, sizeof(*at));
     cfg->gridDim = dim3((unsigned)grid);
     cfg->blockDim = dim3(GEMM_THREADS);
-    cfg->dynamicSmemBytes = PairCfg<PAIR_STAGES>::SMEM;
+    cfg->dynamicSmemBytes = PairCfg<ST>::SMEM;
     cfg->stream = stream;
     at->id = cudaLaunchAttributeClusterDimension;
     at->val.clusterDim.x = 2;
@@ -561,15 +587,16 @@ void pair_launch_cfg(cudaLaunchConfig_t *cfg, cudaLaunchAttribute *at, int grid,
 }
 
 // CTA pairs the device can hold at once (pairs must sit in one GPC), asked once.
+template <int ST>
 int pair_clusters() {
     static int n = 0;
     if (n == 0) {
-        ifr_carveout(gemm_pair_fn());
+        ifr_carveout(gemm_pair_fn<ST>());
         cudaLaunchConfig_t cfg;
         cudaLaunchAttribute at;
-        pair_launch_cfg(&cfg, &at, 2 * (g_num_sms / 2), nullptr);
+        pair_launch_cfg<ST>(&cfg, &at, 2 * (g_num_sms / 2), nullptr);
         int c = 0;
-        if (cudaOccupancyMaxActiveClusters(&c, gemm_bf16_pair_kernel<PAIR_STAGES>, &cfg) != cudaSuccess || c <= 0) {
+        if (cudaOccupancyMaxActiveClusters(&c, gemm_bf16_pair_kernel<ST>, &cfg) != cudaSuccess || c <= 0) {
             cudaGetLastError();
             c = g_num_sms / 2;
         }
@@ -578,25 +605,27 @@ int pair_clusters() {
     return n;
 }
 
+template <int ST>
 int pair_grid(const ifr_victim_cfg *c) {
     const int tiles = (int)((c->n / PAIR_N) * (c->m / PAIR_M));
-    const int cl = pair_clusters();
+    const int cl = pair_clusters<ST>();
     return 2 * (tiles < cl ? tiles : cl);
 }
 
-int launch_gemm_pair(const ifr_victim_cfg *c, cudaStream_t stream, DevTiming *tm) {
-    gemm_pair_fn();
+template <int ST>
+int launch_gemm_pair(const ifr_victim_cfg *c, cudaStream_t stream, int group_m, DevTiming *tm) {
+    gemm_pair_fn<ST>();
     CUtensorMap ta, tb;
     int rc = make_map(&ta, c->in0, c->m, c->k, HALF);
     if (rc) return rc;
     rc = make_map(&tb, c->in1, c->n, c->k, HALF);
     if (rc) return rc;
-    ifr_carveout(gemm_pair_fn());
+    ifr_carveout(gemm_pair_fn<ST>());
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute at;
-    pair_launch_cfg(&cfg, &at, pair_grid(c), stream);
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, gemm_bf16_pair_kernel<PAIR_STAGES>, ta, tb, (float *)c->out,
-                                             (int)c->m, (int)c->n, (int)c->k, tm);
+    pair_launch_cfg<ST>(&cfg, &at, pair_grid<ST>(c), stream);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, gemm_bf16_pair_kernel<ST>, ta, tb, (float *)c->out,
+                                             (int)c->m, (int)c->n, (int)c->k, group_m, tm);
     return e == cudaSuccess ? IFR_OK : IFR_ERR_LAUNCH;
 }
 
@@ -604,11 +633,12 @@ int launch_gemm_pair(const ifr_victim_cfg *c, cudaStream_t stream, DevTiming *tm
 
 int ifr_gemm_shape(const ifr_victim_cfg *c, VictimShape *s) {
     if (g_num_sms == 0) cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, 0);
-    if (c->variant == 2) {
-        s->fn = gemm_pair_fn();
-        s->grid = pair_grid(c);
+    if (c->variant >= 2) {
+        const bool deep = c->variant == 3;
+        s->fn = deep ? gemm_pair_fn<6>() : gemm_pair_fn<4>();
+        s->grid = deep ? pair_grid<6>(c) : pair_grid<4>(c);
         s->block = GEMM_THREADS;
-        s->smem = PairCfg<PAIR_STAGES>::SMEM;
+        s->smem = deep ? PairCfg<6>::SMEM : PairCfg<4>::SMEM;
         s->tmem_cols = PAIR_N;
         s->uses_tensor = 1;
         s->flops = 2.0 * (double)c->m * (double)c->n * (double)c->k;
@@ -632,15 +662,18 @@ int ifr_gemm_shape(const ifr_victim_cfg *c, VictimShape *s) {
 int ifr_gemm_enqueue(ifr_ctx *ctx, const ifr_victim_cfg *c, cudaStream_t stream, DevTiming *tm) {
     g_num_sms = ctx->info.num_sms;
     if (c->m > 65535 * BM || c->n > (1ll << 30) || c->k > (1ll << 30)) return IFR_ERR_ARG;
-    if (c->variant == 2) return launch_gemm_pair(c, stream, tm);
+    const double operand_bytes = 2.0 * ((double)c->m + (double)c->n) * (double)c->k;
+    const int gm = operand_bytes > (double)ctx->info.l2_bytes ? GROUP_M : 1;
+    if (c->variant == 2) return launch_gemm_pair<4>(c, stream, gm, tm);
+    if (c->variant == 3) return launch_gemm_pair<6>(c, stream, gm, tm);
     const bool deep = c->variant == 1;
-    if (c->n % 256 == 0) return deep ? launch_gemm<256, 4>(c, stream, tm) : launch_gemm<256, 3>(c, stream, tm);
-    return deep ? launch_gemm<128, 4>(c, stream, tm) : launch_gemm<128, 3>(c, stream, tm);
+    if (c->n % 256 == 0) return deep ? launch_gemm<256, 4>(c, stream, gm, tm) : launch_gemm<256, 3>(c, stream, gm, tm);
+    return deep ? launch_gemm<128, 4>(c, stream, gm, tm) : launch_gemm<128, 3>(c, stream, gm, tm);
 }
 
 int ifr_preload_gemm() {
     const void *fns[] = {gemm_fn<128, 3>(), gemm_fn<256, 3>(), gemm_fn<128, 4>(), gemm_fn<256, 4>(),
-                         gemm_pair_fn()};
+                         gemm_pair_fn<4>(), gemm_pair_fn<6>()};
     for (const void *f : fns) {
         int rc = ifr_preload(f);
         if (rc) return rc;

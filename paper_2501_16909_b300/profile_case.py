@@ -41,7 +41,7 @@ def main(argv=None):
     ap.add_argument("case")
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--sm-fraction", type=float, default=1.0)
-    ap.add_argument("--variant", type=int, default=0, help="GEMM variant (0, 1, 2 = CTA-pair tiles)")
+    ap.add_argument("--variant", type=int, default=0, help="GEMM variant (0, 1; 2, 3 = CTA-pair tiles)")
     a = ap.parse_args(argv)
     ctx = ifr.Context(0)
     S = ctx.info["num_sms"]
