@@ -241,10 +241,11 @@ typedef struct {
                               1 = throughput (4 stages, 195 KiB: more operand bytes in
                               flight, but no shared-memory stressor block fits beside it),
                               2 = CTA pairs (a 2-CTA cluster per 256 x 256 tile with
-                              tcgen05 cta_group::2, 4 stages of 32 KiB per SM, 129 KiB),
-                              3 = CTA pairs with 6 stages (193 KiB: more bytes in flight,
-                              no shared-memory stressor block fits beside it).
-                              Variants 2 and 3: m and n multiples of 256, else IFR_ERR_ARG.
+                              tcgen05 cta_group::2, 4 stages of 32 KiB per SM, 129 KiB;
+                              m and n multiples of 256, else IFR_ERR_ARG).  The pair's
+                              TMEM allocation needs the same 256 columns free on both
+                              SMs: beside other TMEM users (the tensor stressor) it can
+                              wait until they exit, so it is for solo use.
                               Other kinds: 0. */
     int32_t reserved;
 } ifr_victim_cfg;

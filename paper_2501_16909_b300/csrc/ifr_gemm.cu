@@ -280,13 +280,15 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_kernel(const __grid
 }
 
 // ------------------------------------------------------------------ 2-SM pair tiles
-// Variants 2 and 3: a cluster of two CTAs on two SMs takes 256 x 256 output tiles with
+// Variant 2: a cluster of two CTAs on two SMs takes 256 x 256 output tiles with
 // tcgen05.mma.cta_group::2 (M = 256, N = 256, K = 16), issued by the even CTA (the
 // leader).  Each CTA loads its own 128 rows of A and its own 128 rows of B per 64-wide
 // K slice: 32 KiB per stage per SM where the single-CTA tile needs 48 KiB for the same
-// MMA work.  Variant 2 keeps four stages (129 KiB, room for a stressor block beside
-// it), variant 3 six (193 KiB, more bytes in flight).  Each CTA holds its 128 rows of
-// the accumulator in 256 of its own TMEM columns and stores them.
+// MMA work, and four stages take 129 KiB (six stages measured no faster).  Each CTA
+// holds its 128 rows of the accumulator in 256 of its own TMEM columns and stores
+// them.  The paired allocation needs the same 256 columns free on both SMs, which
+// other TMEM users of those SMs (a tensor stressor) can withhold until they exit, so
+// this variant is not a victim beside them.
 //   warp 0, lane 0   TMA producer in both CTAs; in the leader also the tile
 //                    scheduler, which writes each tile index into both CTAs' rings.
 //                    Both producers complete their bytes on the leader's stage
@@ -633,12 +635,11 @@ int launch_gemm_pair(const ifr_victim_cfg *c, cudaStream_t stream, int group_m, 
 
 int ifr_gemm_shape(const ifr_victim_cfg *c, VictimShape *s) {
     if (g_num_sms == 0) cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, 0);
-    if (c->variant >= 2) {
-        const bool deep = c->variant == 3;
-        s->fn = deep ? gemm_pair_fn<6>() : gemm_pair_fn<4>();
-        s->grid = deep ? pair_grid<6>(c) : pair_grid<4>(c);
+    if (c->variant == 2) {
+        s->fn = gemm_pair_fn<4>();
+        s->grid = pair_grid<4>(c);
         s->block = GEMM_THREADS;
-        s->smem = deep ? PairCfg<6>::SMEM : PairCfg<4>::SMEM;
+        s->smem = PairCfg<4>::SMEM;
         s->tmem_cols = PAIR_N;
         s->uses_tensor = 1;
         s->flops = 2.0 * (double)c->m * (double)c->n * (double)c->k;
@@ -665,7 +666,6 @@ int ifr_gemm_enqueue(ifr_ctx *ctx, const ifr_victim_cfg *c, cudaStream_t stream,
     const double operand_bytes = 2.0 * ((double)c->m + (double)c->n) * (double)c->k;
     const int gm = operand_bytes > (double)ctx->info.l2_bytes ? GROUP_M : 1;
     if (c->variant == 2) return launch_gemm_pair<4>(c, stream, gm, tm);
-    if (c->variant == 3) return launch_gemm_pair<6>(c, stream, gm, tm);
     const bool deep = c->variant == 1;
     if (c->n % 256 == 0) return deep ? launch_gemm<256, 4>(c, stream, gm, tm) : launch_gemm<256, 3>(c, stream, gm, tm);
     return deep ? launch_gemm<128, 4>(c, stream, gm, tm) : launch_gemm<128, 3>(c, stream, gm, tm);
@@ -673,7 +673,7 @@ int ifr_gemm_enqueue(ifr_ctx *ctx, const ifr_victim_cfg *c, cudaStream_t stream,
 
 int ifr_preload_gemm() {
     const void *fns[] = {gemm_fn<128, 3>(), gemm_fn<256, 3>(), gemm_fn<128, 4>(), gemm_fn<256, 4>(),
-                         gemm_pair_fn<4>(), gemm_pair_fn<6>()};
+                         gemm_pair_fn<4>()};
     for (const void *f : fns) {
         int rc = ifr_preload(f);
         if (rc) return rc;

@@ -30,9 +30,10 @@ the library's stressors and victims through the C ABI (no vLLM, cuBLAS or MPS):
             beside a copy kernel in the other, 512-thread blocks on half its SMs, then 1,
             2 and 3 per SM: victim slowdown and the copy's HBM bandwidth.
   variants  Sec. 5.3, colocation-friendly kernel variants: the BF16 GEMM with 3 TMA
-            stages (147 KiB of shared memory), with 4 (195 KiB), and on CTA pairs (256 x
-            256 tiles over two SMs, 4 or 6 stages of 32 KiB: 129 / 193 KiB), alone and
-            arriving at each full-SM stressor: solo throughput against latency beside it.
+            stages (147 KiB of shared memory) and with 4 (195 KiB), alone and arriving
+            at each full-SM stressor: solo throughput against latency beside it.  (The
+            CTA-pair variant is left out: its paired TMEM allocation can wait for the
+            tensor stressor to end.)
   decode    Tables 1 and 2 in the paper's terms: one synthetic decoder layer's decode
             kernels (batch 64, KV length 4096, hidden 4096) as the victim set, (a) beside
             the compute kernel at S1..S4 on the same SMs, (b) in one green-context
@@ -427,7 +428,7 @@ def exp_variants(ctx, repeats, hbm_buf):
     gA = I.torch_normal_bf16(11, G * G, "cuda").view(G, G)
     gB = I.torch_normal_bf16(12, G * G, "cuda").view(G, G)
     gC = torch.empty(G, G, device="cuda")
-    victims = [victim_cfg(A.IFR_V_GEMM, gA, gB, gC, m=G, n=G, k=G, repeats=4, variant=v) for v in (0, 1, 2, 3)]
+    victims = [victim_cfg(A.IFR_V_GEMM, gA, gB, gC, m=G, n=G, k=G, repeats=4, variant=v) for v in (0, 1)]
     kinds = [A.IFR_S_SMEM_CF, A.IFR_S_SMEM_32W, A.IFR_S_TENSOR, A.IFR_S_FMA, A.IFR_S_HBM]
     from . import workloads as W
     stressors = []
@@ -447,8 +448,7 @@ def exp_variants(ctx, repeats, hbm_buf):
             ratio = statistics.median(r["victim_co_ns"] / r["victim_solo_ns"] for r in runs)
             beside[name] = {"latency_ratio": round(ratio, 3), "blocked": sum(r["blocked"] for r in runs),
                             "runs": len(runs)}
-        rows.append({"variant": v.variant, "stages": (3, 4, 4, 6)[v.variant],
-                     "tile": "256 x 256 on a CTA pair" if v.variant >= 2 else "128 x 256",
+        rows.append({"variant": v.variant, "stages": 3 + v.variant,
                      "smem_per_block": prof["dynamic_smem"],
                      "regs_per_thread": prof["regs_per_thread"], "solo_tflops": round(tf, 1), "beside": beside})
     return {

@@ -41,7 +41,8 @@ def main(argv=None):
     ap.add_argument("case")
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--sm-fraction", type=float, default=1.0)
-    ap.add_argument("--variant", type=int, default=0, help="GEMM variant (0, 1; 2, 3 = CTA-pair tiles)")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="GEMM variant (0, 1, 2 = CTA-pair tiles; default: the workload's)")
     a = ap.parse_args(argv)
     ctx = ifr.Context(0)
     S = ctx.info["num_sms"]
@@ -114,7 +115,8 @@ def main(argv=None):
             raise SystemExit("unknown case %r" % a.case)
         v = pick[0]
         v.repeats = 1
-        v.variant = a.variant if a.case == "gemm" else 0
+        if a.case == "gemm" and a.variant is not None:
+            v.variant = a.variant
         for _ in range(a.repeat):
             t = ctx.victim_launch(v)
         out.update(event_ms=t["event_ms"], status=t["status"])
