@@ -90,7 +90,7 @@ class ClockSampler:
 NCU_DRAM_BYTES = {
     "smem_32w": 19968,  # smem_32w_stressor_148sm.md
     "hbm": 2486113792,  # hbm_stream_stressor_1GiB_148sm.md (same blocks and rounds; set > L2)
-    "gemm": None,  # gemm_bf16_tcgen05_4096.md: the kernel gained its tile-order parameter since
+    "gemm": 113009920,  # gemm_bf16_tcgen05_4096.md
 }
 
 

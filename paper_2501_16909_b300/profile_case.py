@@ -6,8 +6,9 @@ one kernel kind in isolation on a small case so that a profiler can capture it:
 
     python -m paper_2501_16909_b300.profile_case <case> [--repeat N]
 
-cases: hbm, l2, fma, tensor, smem_cf, smem_32w, sched, fp64, sleep, gemm, gemv,
-layernorm, softmax, hist, triad; config5_kernels, one launch of each configuration-5
+cases: hbm, l2, fma, tensor, smem_cf, smem_32w, sched, fp64, sleep, gemm (--variant),
+gemv, layernorm, softmax, hist, triad; gemm_variants, the solo throughput of every GEMM
+variant at four shapes; config5_kernels, one launch of each configuration-5
 decoder-layer kernel in order; and victim_bandwidth, which times every memory-bound
 configuration-2 victim alone over grids of 0 (default), 1, 2, 4, 8 and 16 blocks per
 SM (20 launches after a warm measurement) and prints one JSON line per run; and
@@ -59,6 +60,23 @@ def main(argv=None):
                                        working_set_bytes=mib << 20)
                 rate, _res = P.solo_rate(ctx, cfg, rounds=256)
                 print(json.dumps({"mib": mib, "block": block, "blocks_per_sm": bps, "gbs": round(rate / 1e9, 1)}))
+        ctx.close()
+        return
+    if a.case == "gemm_variants":
+        # solo throughput of every GEMM variant at four shapes: 3 warm launches, then 20
+        # launches timed with CUDA events on the victim stream
+        for M, N, K in ((4096, 4096, 4096), (8192, 8192, 8192), (16384, 12288, 4096), (16384, 4096, 11008)):
+            ga = I.torch_normal_bf16(1, M * K, "cuda").view(M, K)
+            gb = I.torch_normal_bf16(2, N * K, "cuda").view(N, K)
+            gc = torch.empty(M, N, device="cuda")
+            for var in (0, 1, 2):
+                cfg = ifr.victim_cfg(A.IFR_V_GEMM, ga, gb, gc, m=M, n=N, k=K, repeats=3, variant=var)
+                ctx.victim_launch(cfg)
+                cfg.repeats = 20
+                t = ctx.victim_launch(cfg)
+                print(json.dumps({"m": M, "n": N, "k": K, "variant": var, "status": t["status"],
+                                  "tflops": round(2.0 * M * N * K * 20 / (t["event_ms"] * 1e-3) / 1e12, 1)}))
+            del ga, gb, gc
         ctx.close()
         return
     if a.case == "config5_kernels":
