@@ -236,9 +236,9 @@ typedef struct {
     void *out;             /* TRIAD a | GEMM C | GEMV y | LN/SOFTMAX y | HIST bins */
     int32_t grid;          /* blocks (0 = kind default) */
     int32_t block;         /* threads per block (0 = kind default) */
-    int32_t variant;       /* GEMM: 0 = colocation-friendly (3 TMA stages, 147 KiB of shared
+    int32_t variant;       /* GEMM: 0 = colocation-friendly (3 TMA stages, 145 KiB of shared
                               memory: leaves room for a stressor block, Sec. 5.3),
-                              1 = throughput (4 stages, 195 KiB: more operand bytes in
+                              1 = throughput (4 stages, 193 KiB: more operand bytes in
                               flight, but no shared-memory stressor block fits beside it),
                               2 = CTA pairs (a 2-CTA cluster per 256 x 256 tile with
                               tcgen05 cta_group::2, 4 stages of 32 KiB per SM, 129 KiB;

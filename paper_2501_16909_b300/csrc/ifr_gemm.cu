@@ -38,10 +38,10 @@
 
 namespace {
 
-// Two variants (Sec. 5.3: colocation-friendly kernel variants).  Three stages (147 KiB
+// Two variants (Sec. 5.3: colocation-friendly kernel variants).  Three stages (145 KiB
 // of shared memory at BN = 256) leave room on the SM for a stressor block (the tensor
 // stressor needs 34 KiB, the shared-memory stressor 2 x 33 KiB).  Four stages
-// (195 KiB) keep a third more operand bytes in flight, which the single-CTA tile needs
+// (193 KiB) keep a third more operand bytes in flight, which the single-CTA tile needs
 // to cover the L2 round trip, but make the GEMM and those stressors mutually
 // exclusive on an SM.  One BN-column accumulator (not two) leaves TMEM for the tensor
 // stressor in both.

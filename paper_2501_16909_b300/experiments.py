@@ -30,7 +30,7 @@ the library's stressors and victims through the C ABI (no vLLM, cuBLAS or MPS):
             beside a copy kernel in the other, 512-thread blocks on half its SMs, then 1,
             2 and 3 per SM: victim slowdown and the copy's HBM bandwidth.
   variants  Sec. 5.3, colocation-friendly kernel variants: the BF16 GEMM with 3 TMA
-            stages (147 KiB of shared memory) and with 4 (195 KiB), alone and arriving
+            stages (145 KiB of shared memory) and with 4 (193 KiB), alone and arriving
             at each full-SM stressor: solo throughput against latency beside it.  (The
             CTA-pair variant is left out: its paired TMEM allocation can wait for the
             tensor stressor to end.)
