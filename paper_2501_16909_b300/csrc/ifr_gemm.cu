@@ -4,10 +4,11 @@
 // shared-memory stressor (Sec. 4.4.1); this is the library's own GEMM.
 //
 // Persistent: one CTA per SM takes 128 x BN output tiles (BN = 256, or 128 when N is
-// not a multiple of 256) in row-major tile order until none are left: its first tile
-// is its own index, every later one comes from a device counter.  Handing tiles out on demand keeps the load balance of a one-CTA-per-tile
-// launch: a CTA on an SM that a stressor slows takes fewer tiles instead of holding
-// up the grid with a fixed share.  192 threads:
+// not a multiple of 256) until none are left: its first tile is its own index, every
+// later one comes from a device counter (tile order: see tile_coords).  Handing tiles
+// out on demand keeps the load balance of a one-CTA-per-tile launch: a CTA on an SM
+// that a stressor slows takes fewer tiles instead of holding up the grid with a fixed
+// share.  A second kernel below runs 256 x 256 tiles on CTA pairs.  192 threads:
 //   warp 0, lane 0   tile scheduler and TMA producer: takes tile blockIdx.x first and
 //                    then claims tiles gridDim.x, gridDim.x + 1, ... from the counter; publishes
 //                    its index in a 4-entry shared ring for the other roles, and loads
@@ -38,7 +39,8 @@
 
 namespace {
 
-// Two variants (Sec. 5.3: colocation-friendly kernel variants).  Three stages (145 KiB
+// Variants 0 and 1 (Sec. 5.3: colocation-friendly kernel variants; variant 2, the
+// CTA-pair kernel, is described with it).  Three stages (145 KiB
 // of shared memory at BN = 256) leave room on the SM for a stressor block (the tensor
 // stressor needs 34 KiB, the shared-memory stressor 2 x 33 KiB).  Four stages
 // (193 KiB) keep a third more operand bytes in flight, which the single-CTA tile needs
