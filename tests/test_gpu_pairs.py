@@ -206,6 +206,32 @@ def test_partition_confines_victims_and_stressors(ctx):
     assert res["sms_used"] == S
 
 
+def test_partition_isolates_sm_private_stressors(ctx):
+    """Harness invariant (Sec. 4.1, Sec. 4.3): stressors of resources private to an SM
+    (the FP32 pipe, the tensor pipe, shared memory) confined to the other green-context
+    partition leave an HBM-bound victim's latency within its solo noise.  The 3 % floor
+    allows for the SM clock, which both partitions share under the power cap."""
+    import torch
+    import ifr_inputs as I
+    S = ctx.info["num_sms"]
+    n = 1 << 24  # three 64 MiB vectors: more than L2, so the triad streams from HBM
+    b = I.torch_uniform_pm1(0, n, "cuda")
+    c = I.torch_uniform_pm1(0, n, "cuda", start=n)
+    a = torch.empty(n, device="cuda")
+    kinds = [A.IFR_S_FMA, A.IFR_S_TENSOR, A.IFR_S_SMEM_32W]
+    info = ctx.partition(S // 2)
+    try:
+        v = ifr.victim_cfg(A.IFR_V_TRIAD, b, c, a, n=n, scalar=1.5, repeats=4)
+        lv = [[ifr.stressor_cfg(k, sm_count=info["stressor_sms"], seed=3, mask_mode=1)] for k in kinds]
+        cells = ctx.sweep([v], lv, repeats=5, batched=False)
+    finally:
+        ctx.partition_release()
+    red = R.sensitivity(ifr.cells_to_dicts(cells), 0, len(kinds), 1)
+    for r, k in enumerate(kinds):
+        sd = red["slowdown"][r][1]
+        assert sd <= 1.0 + max(3.0 * red["noise"], 0.03), (A.STRESSOR_NAMES[k], sd, red["noise"])
+
+
 def test_partition_argument_errors(ctx):
     S = ctx.info["num_sms"]
     ctx.partition_release()  # no split active: a no-op
