@@ -245,7 +245,9 @@ typedef struct {
                               m and n multiples of 256, else IFR_ERR_ARG).  The pair's
                               TMEM allocation needs the same 256 columns free on both
                               SMs: beside other TMEM users (the tensor stressor) it can
-                              wait until they exit, so it is for solo use.
+                              wait until they exit, so it is for solo use
+                              (ifr_victim_launch); ifr_sweep, ifr_corun and ifr_colocate
+                              refuse it with IFR_ERR_ARG.
                               Other kinds: 0. */
     int32_t reserved;
 } ifr_victim_cfg;

@@ -172,6 +172,13 @@ int read_timing(ifr_ctx *ctx, int slot, int repeats, ifr_timing *out) {
     return IFR_OK;
 }
 
+// The CTA-pair GEMM (variant 2) allocates the same TMEM columns on two SMs at once;
+// beside other TMEM users (the tensor stressor, another pair) that allocation can
+// wait until they exit, so the measurements that colocate kernels refuse it.
+int colocatable(const ifr_victim_cfg *c) {
+    return (c->kind == IFR_V_GEMM && c->variant == 2) ? IFR_ERR_ARG : IFR_OK;
+}
+
 }  // namespace
 
 extern "C" int ifr_corun(ifr_ctx *ctx, const ifr_victim_cfg *victim, const ifr_victim_cfg *corunner,
@@ -179,6 +186,8 @@ extern "C" int ifr_corun(ifr_ctx *ctx, const ifr_victim_cfg *victim, const ifr_v
     if (!ctx || !out || corunner_launches < 0 || corunner_launches > 100000) return IFR_ERR_ARG;
     int rc = ifr_victim_validate(ctx, victim);
     if (!rc) rc = ifr_victim_validate(ctx, corunner);
+    if (!rc) rc = colocatable(victim);
+    if (!rc) rc = colocatable(corunner);
     if (rc) return rc;
     memset(out, 0, sizeof *out);
     rc = ifr_ensure_timing(ctx, 3);
@@ -350,6 +359,7 @@ extern "C" int ifr_colocate(ifr_ctx *ctx, const ifr_stressor_cfg *sc, const ifr_
     if (!ctx || !sc || !vc || !out) return IFR_ERR_ARG;
     if (sc->max_rounds <= 0 || sc->kind == IFR_S_SCHED) return IFR_ERR_ARG;
     int rc = ifr_victim_validate(ctx, vc);
+    if (!rc) rc = colocatable(vc);
     if (rc) return rc;
     memset(out, 0, sizeof *out);
     rc = ifr_ensure_timing(ctx, 3);
@@ -446,6 +456,7 @@ extern "C" int ifr_sweep(ifr_ctx *ctx, const ifr_sweep_plan *p, ifr_cell_result 
     *n_out = 0;
     for (int v = 0; v < p->n_victims; ++v) {
         int rc = ifr_victim_validate(ctx, &p->victims[v]);
+        if (!rc) rc = colocatable(&p->victims[v]);
         if (rc) return rc;
     }
     const size_t need = (size_t)p->repeats * p->n_victims * (1 + (size_t)p->n_stressors * (p->n_levels + 1));

@@ -91,6 +91,21 @@ def test_gemm_variant_profiles_and_bad_variant(ctx):
             ctx.victim_launch(bad)
 
 
+def test_pair_gemm_refused_where_kernels_are_colocated(ctx):
+    # the CTA pair's TMEM allocation can wait on other TMEM users: solo launches only
+    Ab = I.torch_normal_bf16(1, 256 * 256, "cuda").view(256, 256)
+    C = torch.empty(256, 256, device="cuda")
+    pair = ifr.victim_cfg(A.IFR_V_GEMM, Ab, Ab, C, m=256, n=256, k=256, variant=2)
+    single = ifr.victim_cfg(A.IFR_V_GEMM, Ab, Ab, C, m=256, n=256, k=256, variant=0)
+    fma = ifr.stressor_cfg(A.IFR_S_FMA, sm_count=1, block=128, max_rounds=1)
+    for call in (lambda: ctx.sweep([pair], [], repeats=1), lambda: ctx.corun(pair, single),
+                 lambda: ctx.corun(single, pair), lambda: ctx.colocate(fma, pair)):
+        with pytest.raises(ifr.IfrError) as e:
+            call()
+        assert e.value.status == A.IFR_ERR_ARG
+    assert ctx.victim_launch(pair)["status"] == 0
+
+
 def test_gemm_rejects_bad_shapes(ctx):
     import ctypes as C
 
