@@ -37,7 +37,7 @@
 extern "C" {
 #endif
 
-#define IFR_ABI_VERSION 3
+#define IFR_ABI_VERSION 4
 
 /* ---- status codes ------------------------------------------------------- */
 #define IFR_OK 0
@@ -203,7 +203,10 @@ int ifr_stressor_release(ifr_ctx *ctx, int handle);
  * array of logs_cap >= sm_count * blocks_per_sm records, written in active-index
  * order (unclaimed slots keep index -1).  Asynchronous: synchronise `stream`
  * before reading logs_out.  The first call on a device looks up the array's
- * device address with that device current, so make it before any stream capture.
+ * device address with that device current and loads the entry point's kernels,
+ * so make it before any stream capture.  `stream` must belong to the current
+ * device.  The looked-up address is kept for the life of the process: calls after
+ * a cudaDeviceReset of that device are not supported.
  * All calls share the array, which keeps the last call's contents (the call
  * clears it on the stream first): calls whose kernels overlap on the GPU race.
  * Errors: IFR_ERR_ARG (kind, pointer, alignment, size, rounds), IFR_ERR_CAPACITY
@@ -451,14 +454,20 @@ typedef struct {
                                    before the whole co-runner chain had finished */
     uint64_t victim_release_ns; /* %globaltimer when the victim was released (a co-runner
                                    block was running); latency = victim end - release */
+    double victim_slowdown;     /* (victim_corun span / K) / (victim_solo span / K), spans =
+                                   last block exit - first block entry (Sec. 4.3 slowdown);
+                                   NaN when a span is empty */
+    double corunner_slowdown;   /* the same for the co-runner chain: its per-launch time during
+                                   the co-run over its solo launch time */
 } ifr_corun_result;
 
 /* Colocate two workloads on concurrent streams: the co-runner runs as a chain of
  * back-to-back launches on the context's stressor stream (long enough to cover
  * 4x the victim's solo window when corunner_launches = 0), the victim's K
  * launches start on the victim stream once a co-runner block is running (bounded
- * wait), and every launch stamps %globaltimer.  The victim's slowdown is
- * (victim_corun span / K) / (victim_solo span / K).  Both configurations are
+ * wait), and every launch stamps %globaltimer.  The call reduces the raw stamps
+ * to victim_slowdown = (victim_corun span / K) / (victim_solo span / K) and the
+ * co-runner's slowdown likewise (Sec. 4.3, 4.4.1).  Both configurations are
  * validated as in ifr_victim_launch.  Errors: IFR_ERR_ARG, IFR_ERR_CUDA,
  * IFR_ERR_TIMEOUT (host wait). */
 int ifr_corun(ifr_ctx *ctx, const ifr_victim_cfg *victim, const ifr_victim_cfg *corunner, int corunner_launches,

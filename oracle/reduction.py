@@ -115,6 +115,13 @@ def sensitivity(cells, victim: int, n_stressors: int, n_levels: int, intensity=N
     }
 
 
+def corun_slowdown(solo, corun) -> float:
+    """Slowdown of one kernel colocated with another (Sec. 4.3, 4.4.1): its per-launch
+    time during the co-run over its per-launch time alone.  Both arguments are
+    measurements with keys t_start, t_end, k (rule 1 above)."""
+    return duration(corun) / duration(solo)
+
+
 def corun_speedup(t_a: float, t_b: float, start_a: float, end_a: float, start_b: float, end_b: float) -> float:
     """Sequential over colocated time of two kernels (Table 3's seq/col speedup)."""
     return (t_a + t_b) / (max(end_a, end_b) - min(start_a, start_b))

@@ -221,19 +221,12 @@ class Context:
     # -- kernel-with-kernel colocation
     def corun(self, victim: ifr_victim_cfg, corunner: ifr_victim_cfg, corunner_launches: int = 0) -> dict:
         """Victim K launches beside a chain of co-runner launches; returns the raw
-        timings plus the victim's slowdown and the chain's."""
+        timings plus the victim's slowdown and the chain's (reduced by ifr_corun)."""
         self._sync()
         r = _abi.ifr_corun_result()
         check(self._L.ifr_corun(self._h, C.byref(victim), C.byref(corunner), corunner_launches, C.byref(r)),
               "ifr_corun")
-        d = _struct_dict(r)
-
-        def per(t):
-            return (t["t_end_ns"] - t["t_start_ns"]) / max(1, t["repeats"])
-
-        d["victim_slowdown"] = per(d["victim_corun"]) / per(d["victim_solo"])
-        d["corunner_slowdown"] = per(d["corunner_corun"]) / per(d["corunner_solo"])
-        return d
+        return _struct_dict(r)
 
     # -- sweep
     def sweep(self, victims, levels, repeats: int = 3, batched: bool = False):

@@ -149,6 +149,7 @@ class ifr_corun_result(C.Structure):
         ("victim_solo", ifr_timing), ("corunner_solo", ifr_timing), ("victim_corun", ifr_timing),
         ("corunner_corun", ifr_timing), ("valid", C.c_int32), ("status", C.c_int32),
         ("corunner_launches", C.c_int32), ("blocked", C.c_int32), ("victim_release_ns", C.c_uint64),
+        ("victim_slowdown", C.c_double), ("corunner_slowdown", C.c_double),
     ]
 
 

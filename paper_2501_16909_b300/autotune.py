@@ -8,8 +8,9 @@ full-intensity rate, i.e. all SMs at duty 1), find for each f a configuration
      smallest count whose rate reaches the target; the count just below replaces it
      when that one is closer and within the tolerance; a target of 1 takes all SMs;
   2. if that overshoots by more than the tolerance, lower the duty cycle
-     (active fraction of each period) by the measured ratio, and correct once
-     more with the secant between the two duty points.
+     (active fraction of each period): start at the measured ratio, then keep a
+     bracket around the target and refine by regula falsi (bisecting when the
+     secant leaves the bracket), up to eight probes.
 
 Every probe is one solo run through the C ABI (ifr_stressor_launch with
 max_rounds, CUDA events on the stressor stream); results are cached per
@@ -58,6 +59,33 @@ class Tuner:
             self.probes += 1
         return self.cache[key]
 
+    def tune_duty(self, n: int, target: float, r_full: float, max_probes: int = 8):
+        """Duty cycle at n SMs whose rate is within the tolerance of `target`.  The rate
+        rises with the duty (0 at duty 0, r_full at 1) but not in proportion: every
+        on-phase starts with an empty pipeline, so short on-phases deliver less.  The
+        search keeps a bracket [lo, hi] around the target and takes the secant
+        (regula falsi) inside it, bisecting when the secant leaves the bracket; it
+        returns the closest probe."""
+        lo_d, lo_r, hi_d, hi_r = 0.0, 0.0, 1.0, r_full
+        best = (abs(r_full / target - 1), 1.0, r_full)
+        d = max(0.02, min(1.0, target / r_full))
+        for _ in range(max_probes):
+            rd = self.rate(n, d)
+            err = abs(rd / target - 1)
+            if err < best[0]:
+                best = (err, d, rd)
+            if err <= self.tol:
+                break
+            if rd > target:
+                hi_d, hi_r = d, rd
+            else:
+                lo_d, lo_r = d, rd
+            nd = lo_d + (target - lo_r) * (hi_d - lo_d) / (hi_r - lo_r) if hi_r > lo_r else 0.5 * (lo_d + hi_d)
+            if not lo_d < nd < hi_d:
+                nd = 0.5 * (lo_d + hi_d)
+            d = max(0.02, nd)
+        return best[1], best[2]
+
     def tune(self, fractions):
         rmax = self.rate(self.S)
         out = []
@@ -82,18 +110,7 @@ class Tuner:
                 n -= 1
             duty, r = 1.0, self.rate(n)
             if self.base.kind != A.IFR_S_SCHED and r > target * (1 + self.tol):
-                d1 = max(0.05, min(1.0, target / r))
-                r1 = self.rate(n, d1)
-                duty, r = d1, r1
-                if abs(r1 / target - 1) > self.tol:
-                    # secant between (1, rate(n)) and (d1, r1)
-                    r0 = self.rate(n)
-                    slope = (r0 - r1) / (1.0 - d1) if d1 < 1.0 else 0.0
-                    if slope > 0:
-                        d2 = max(0.05, min(1.0, d1 + (target - r1) / slope))
-                        r2 = self.rate(n, d2)
-                        if abs(r2 / target - 1) < abs(r1 / target - 1):
-                            duty, r = d2, r2
+                duty, r = self.tune_duty(n, target, r)
             out.append(Level(f, n, duty, r, r / rmax, r / self.peak if self.peak else float("nan"),
                              self.probes - p0))
         return rmax, out

@@ -89,6 +89,8 @@ struct StressParams {
     uint64_t deadline_ns; // per-block, relative to its own start
     float duty;
     uint32_t period_ns;
+    uint32_t duty_on_ns;  // active part of each period (0 = no duty cycle)
+    float duty_inv_period; // 1 / period_ns
     const int4 *buf;      // L2/HBM
     int64_t n_chunks;     // L2/HBM chunks (chunk = blockDim * 4 int4)
     int32_t ilp;          // FMA

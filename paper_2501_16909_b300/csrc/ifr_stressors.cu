@@ -51,6 +51,17 @@ struct BlockCtl {
     int status;
 };
 
+// Duty-cycle state of a block (thread 0 only): start of the next period, the
+// active time the block may still spend (each period adds its share, each round
+// takes its duration, so what a round overran or left unused carries over), and
+// the start of the running round.  It lives in shared memory, so the round loops
+// keep their registers.
+struct DutyState {
+    uint64_t next;
+    int64_t budget;
+    uint64_t t_rs;
+};
+
 __device__ __forceinline__ bool sm_allowed(const StressParams &p, uint32_t sm) {
     return sm < IFR_MAX_SMS && ((p.mask[sm >> 5] >> (sm & 31)) & 1u);
 }
@@ -99,6 +110,7 @@ __device__ int claim_slot(DevStress *st, const StressParams &p, uint32_t sm) {
 // Thread 0 only: should the block run round `round`?  Sleeps through the
 // off phase of the duty cycle.
 __device__ int round_decision(DevStress *st, const StressParams &p, int64_t round, BlockCtl &c) {
+    __shared__ DutyState s_duty;
     if (p.max_rounds > 0 && round >= p.max_rounds) return 0;
     if (ifr_ld_volatile(&st->stop)) return 0;
     uint64_t now = ifr_gtimer();
@@ -115,24 +127,49 @@ __device__ int round_decision(DevStress *st, const StressParams &p, int64_t roun
             return 0;
         }
     }
-    if (p.duty > 0.f && p.duty < 1.f) {
-        const uint64_t per = p.period_ns ? p.period_ns : 100000u;
-        const uint64_t on = (uint64_t)((double)per * (double)p.duty);
-        uint64_t ph = now % per;
-        if (ph >= on) {
-            const uint64_t target = now - ph + per;
-            uint32_t it = 0;
-            while (now < target) {
+    if (p.duty_on_ns) {
+        // Duty cycle D over period P: the periods are aligned on %globaltimer, so every
+        // block of the launch is active in the same on-phase (the resource sees the full
+        // stressor for D*P, then nothing).  A round that has started runs to its end;
+        // each period adds D*P to the block's budget and each round takes its duration,
+        // so the active fraction averages to D whatever the round length (the budget is
+        // bounded by one period either way).  The first period adds only the share of
+        // D*P for the part of it left after the block starts.
+        DutyState &d = s_duty;
+        const uint32_t per = p.period_ns;
+        const int64_t on = p.duty_on_ns, lim = per;
+        if (round == 0) {
+            d.next = now - now % per + per;
+            d.budget = (int64_t)((float)on * (float)(d.next - now) * p.duty_inv_period);
+            d.t_rs = 0;
+        }
+        if (d.t_rs) {
+            d.budget -= (int64_t)(now - d.t_rs);
+            d.t_rs = 0;
+        }
+        uint32_t it = 0;
+        for (;;) {
+            if (now >= d.next) {
+                d.budget += on;
+                d.next += per;
+                if (d.budget > lim) d.budget = lim;
+                if (d.budget < -lim) d.budget = -lim;
+                if (++it > kMaxSpin) return 0;
+                continue;
+            }
+            if (d.budget > 0) break;
+            while (now < d.next) {
                 if (now >= c.deadline) {
                     c.status = IFR_ERR_TIMEOUT;
                     return 0;
                 }
                 if (ifr_ld_volatile(&st->stop) || ++it > kMaxSpin) return 0;
-                uint64_t left = target - now;
+                const uint64_t left = d.next - now;
                 __nanosleep((unsigned)(left > 20000u ? 20000u : left));
                 now = ifr_gtimer();
             }
         }
+        d.t_rs = now;
     }
     return 1;
 }
@@ -272,7 +309,7 @@ __global__ void __launch_bounds__(1024) fma_stress_kernel(DevStress *st, StressP
 // The compute kernel of Sec. 4.4.3 on fp64 multiplication (__dmul_rn): ILP
 // independent chains x <- x * a per thread, one launch-wide multiplier just below 1.
 template <int ILP>
-__global__ void __launch_bounds__(1024) fp64_stress_kernel(DevStress *st, StressParams p) {
+__global__ void __launch_bounds__(1024, 1) fp64_stress_kernel(DevStress *st, StressParams p) {
     __shared__ int s_k;
     __shared__ uint64_t s_t0;
     __shared__ int s_go[2];
@@ -832,6 +869,9 @@ int ifr_stressor_enqueue(ifr_ctx *ctx, const ifr_stressor_cfg *cfg, cudaStream_t
     p.deadline_ns = cfg->deadline_ns ? cfg->deadline_ns : 2000000000ull;
     p.duty = cfg->duty;
     p.period_ns = cfg->period_ns > 0 ? (uint32_t)cfg->period_ns : 100000u;
+    p.duty_on_ns = (cfg->duty > 0.f && cfg->duty < 1.f) ? (uint32_t)((double)p.period_ns * (double)cfg->duty) : 0u;
+    if (cfg->duty > 0.f && cfg->duty < 1.f && p.duty_on_ns == 0u) p.duty_on_ns = 1u;
+    p.duty_inv_period = 1.0f / (float)p.period_ns;
     p.ilp = cfg->ilp ? cfg->ilp : 4;
     {
         // FMA constants: a = 1 - 2^-12 - (u0 >> 53) 2^-23, b = ((u1 >> 40) - 2^23) 2^-29
@@ -1122,9 +1162,16 @@ extern "C" int ifr_stream_stressor_noalloc(int kind, const void *buf, int64_t wo
         std::lock_guard<std::mutex> g(g_noalloc_mu);
         if (!g_noalloc_addr[dev]) {
             // first call on this device: look up the array's device address with
-            // the device current (host code cannot use the symbol itself)
+            // the device current (host code cannot use the symbol itself), and load
+            // the three kernels now rather than lazily at their first launch
             void *ptr = nullptr;
             IFR_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+            const void *fns[] = {(const void *)stress_reset_kernel, (const void *)stream_stress_kernel,
+                                 (const void *)noalloc_logs_clear_kernel};
+            for (const void *f : fns) {
+                int rc = ifr_preload(f);
+                if (rc) return rc;
+            }
             g_noalloc_addr[dev] = ptr;
         }
         scratch = g_noalloc_addr[dev];
@@ -1141,6 +1188,7 @@ extern "C" int ifr_stream_stressor_noalloc(int kind, const void *buf, int64_t wo
     p.deadline_ns = deadline_ns ? deadline_ns : 2000000000ull;
     p.duty = 1.f;
     p.period_ns = 100000u;
+    p.duty_on_ns = 0u;
     p.logs = logs_out;
     p.buf = (const int4 *)buf;
     p.n_chunks = working_set_bytes / chunk;

@@ -172,6 +172,14 @@ int read_timing(ifr_ctx *ctx, int slot, int repeats, ifr_timing *out) {
     return IFR_OK;
 }
 
+// Slowdown of one measurement against another (Sec. 4.3: colocated over isolated
+// latency), each as (last block exit - first block entry) / K; NaN without a span.
+double per_launch_ratio(const ifr_timing &co, const ifr_timing &solo) {
+    const double kc = co.repeats > 0 ? co.repeats : 1, ks = solo.repeats > 0 ? solo.repeats : 1;
+    if (co.t_end_ns <= co.t_start_ns || solo.t_end_ns <= solo.t_start_ns) return NAN;
+    return (((double)co.t_end_ns - (double)co.t_start_ns) / kc) / (((double)solo.t_end_ns - (double)solo.t_start_ns) / ks);
+}
+
 // The CTA-pair GEMM (variant 2) allocates the same TMEM columns on two SMs at once;
 // beside other TMEM users (the tensor stressor, another pair) that allocation can
 // wait until they exit, so the measurements that colocate kernels refuse it.
@@ -241,6 +249,8 @@ extern "C" int ifr_corun(ifr_ctx *ctx, const ifr_victim_cfg *victim, const ifr_v
     if (rc) return rc;
     IFR_CUDA(cudaMemcpy(&out->victim_release_ns, release, sizeof(uint64_t), cudaMemcpyDeviceToHost));
     const ifr_timing &a = out->victim_corun, &b = out->corunner_corun;
+    out->victim_slowdown = per_launch_ratio(out->victim_corun, out->victim_solo);
+    out->corunner_slowdown = per_launch_ratio(out->corunner_corun, out->corunner_solo);
     out->valid = a.status == IFR_OK && b.status == IFR_OK && b.t_start_ns <= a.t_start_ns && b.t_end_ns >= a.t_end_ns;
     out->blocked = a.status == IFR_OK && a.t_start_ns >= b.t_end_ns;
     out->status = a.status != IFR_OK ? a.status : (out->valid ? IFR_OK : (out->blocked ? IFR_ERR_HOL : IFR_ERR_INVALID_CELL));

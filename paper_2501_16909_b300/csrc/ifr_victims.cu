@@ -53,6 +53,42 @@ __device__ __forceinline__ void st_f4_stream(float4 *p, float4 v) {
                  : "memory");
 }
 
+__device__ __forceinline__ float ld_f1_stream(const float *p) {
+    float v;
+    asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
+// Slot j (four consecutive columns 4j..4j+3) of a row.  VEC: the row is 16-byte
+// aligned and cols % 4 == 0, one 16-byte load; otherwise four 4-byte loads, and
+// columns past the row's end read as `pad`.
+template <bool VEC>
+__device__ __forceinline__ float4 ld_slot(const float *row, int j, int cols, float pad) {
+    if constexpr (VEC) {
+        return ld_f4_stream((const float4 *)row + j);
+    } else {
+        const int e = 4 * j;
+        float4 v;
+        v.x = e < cols ? ld_f1_stream(row + e) : pad;
+        v.y = e + 1 < cols ? ld_f1_stream(row + e + 1) : pad;
+        v.z = e + 2 < cols ? ld_f1_stream(row + e + 2) : pad;
+        v.w = e + 3 < cols ? ld_f1_stream(row + e + 3) : pad;
+        return v;
+    }
+}
+template <bool VEC>
+__device__ __forceinline__ void st_slot(float *row, int j, int cols, float4 v) {
+    if constexpr (VEC) {
+        st_f4_stream((float4 *)row + j, v);
+    } else {
+        const int e = 4 * j;
+        if (e < cols) row[e] = v.x;
+        if (e + 1 < cols) row[e + 1] = v.y;
+        if (e + 2 < cols) row[e + 2] = v.z;
+        if (e + 3 < cols) row[e + 3] = v.w;
+    }
+}
+
 // ------------------------------------------------------------------ triad
 // a[i] = b[i] + s * c[i] (STREAM triad).  Grid-stride over float4 with 4
 // independent float4 per thread per step; scalar tail.
@@ -126,22 +162,24 @@ __device__ __forceinline__ float block_max(float v, float *red) {
 }
 
 // LayerNorm, no affine, biased variance, two passes over the register-held row.
-// NT threads, VPT float4 per thread: cols <= NT*VPT*4, cols % 4 == 0.
-template <int NT, int VPT>
+// NT threads, VPT four-column slots per thread: cols <= NT*VPT*4.  VEC: cols % 4 == 0
+// and 16-byte aligned rows; otherwise (any width) the last slot is padded with the
+// row mean, which adds nothing to the variance, and stores are per column.
+template <int NT, int VPT, bool VEC>
 __global__ void __launch_bounds__(NT) layernorm_kernel(const float *__restrict__ x, float *__restrict__ y,
                                                        int64_t rows, int cols, float eps, DevTiming *tm) {
     __shared__ float red[32];
     v_enter(tm);
-    const int c4 = cols >> 2;
+    const int c4 = (cols + 3) >> 2;
     const float inv_n = 1.0f / (float)cols;
     for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
-        const float4 *xr = (const float4 *)(x + r * cols);
+        const float *xr = x + r * cols;
         float4 v[VPT];
         float s = 0.f;
 #pragma unroll
         for (int u = 0; u < VPT; ++u) {
             const int j = threadIdx.x + u * NT;
-            v[u] = j < c4 ? ld_f4_stream(xr + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+            v[u] = j < c4 ? ld_slot<VEC>(xr, j, cols, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
             s += (v[u].x + v[u].y) + (v[u].z + v[u].w);
         }
         const float mean = block_sum<NT>(s, red) * inv_n;
@@ -150,13 +188,19 @@ __global__ void __launch_bounds__(NT) layernorm_kernel(const float *__restrict__
         for (int u = 0; u < VPT; ++u) {
             const int j = threadIdx.x + u * NT;
             if (j < c4) {
+                if constexpr (!VEC) {
+                    const int e = 4 * j;
+                    if (e + 1 >= cols) v[u].y = mean;
+                    if (e + 2 >= cols) v[u].z = mean;
+                    if (e + 3 >= cols) v[u].w = mean;
+                }
                 const float a = v[u].x - mean, b = v[u].y - mean, c = v[u].z - mean, d = v[u].w - mean;
                 q += (a * a + b * b) + (c * c + d * d);
             }
         }
         const float var = block_sum<NT>(q, red) * inv_n;
         const float inv = 1.0f / sqrtf(var + eps);
-        float4 *yr = (float4 *)(y + r * cols);
+        float *yr = y + r * cols;
 #pragma unroll
         for (int u = 0; u < VPT; ++u) {
             const int j = threadIdx.x + u * NT;
@@ -166,29 +210,30 @@ __global__ void __launch_bounds__(NT) layernorm_kernel(const float *__restrict__
                 o.y = (v[u].y - mean) * inv;
                 o.z = (v[u].z - mean) * inv;
                 o.w = (v[u].w - mean) * inv;
-                st_f4_stream(yr + j, o);
+                st_slot<VEC>(yr, j, cols, o);
             }
         }
     }
     v_exit(tm);
 }
 
-// Row softmax: max, sum of exp(x - max), divide.  Same layout as layernorm.
-template <int NT, int VPT>
+// Row softmax: max, sum of exp(x - max), divide.  Same layout as layernorm; columns
+// past the row's end read as -inf, so they add nothing to the max or the sum.
+template <int NT, int VPT, bool VEC>
 __global__ void __launch_bounds__(NT) softmax_kernel(const float *__restrict__ x, float *__restrict__ y,
                                                      int64_t rows, int cols, DevTiming *tm) {
     __shared__ float red[32];
     v_enter(tm);
-    const int c4 = cols >> 2;
+    const int c4 = (cols + 3) >> 2;
     for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
-        const float4 *xr = (const float4 *)(x + r * cols);
+        const float *xr = x + r * cols;
         float4 v[VPT];
         float m = -INFINITY;
 #pragma unroll
         for (int u = 0; u < VPT; ++u) {
             const int j = threadIdx.x + u * NT;
             if (j < c4) {
-                v[u] = ld_f4_stream(xr + j);
+                v[u] = ld_slot<VEC>(xr, j, cols, -INFINITY);
                 m = fmaxf(m, fmaxf(fmaxf(v[u].x, v[u].y), fmaxf(v[u].z, v[u].w)));
             }
         }
@@ -206,7 +251,7 @@ __global__ void __launch_bounds__(NT) softmax_kernel(const float *__restrict__ x
             }
         }
         const float inv = 1.0f / block_sum<NT>(s, red);
-        float4 *yr = (float4 *)(y + r * cols);
+        float *yr = y + r * cols;
 #pragma unroll
         for (int u = 0; u < VPT; ++u) {
             const int j = threadIdx.x + u * NT;
@@ -216,7 +261,7 @@ __global__ void __launch_bounds__(NT) softmax_kernel(const float *__restrict__ x
                 o.y = v[u].y * inv;
                 o.z = v[u].z * inv;
                 o.w = v[u].w * inv;
-                st_f4_stream(yr + j, o);
+                st_slot<VEC>(yr, j, cols, o);
             }
         }
     }
@@ -405,16 +450,27 @@ __global__ void __launch_bounds__(256) hist_kernel(const int32_t *__restrict__ k
 
 inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
-template <int NT, int VPT>
-void launch_ln(int grid, cudaStream_t st, const ifr_victim_cfg *c, DevTiming *tm) {
-    ifr_carveout((const void *)layernorm_kernel<NT, VPT>);
-    layernorm_kernel<NT, VPT><<<grid, NT, 0, st>>>((const float *)c->in0, (float *)c->out, c->m, (int)c->n,
-                                                   c->eps > 0.f ? c->eps : 1e-5f, tm);
+// The 16-byte path needs cols % 4 == 0 and 16-byte aligned input and output rows.
+inline bool rows_vec(const ifr_victim_cfg *c) { return c->n % 4 == 0 && aligned16(c->in0) && aligned16(c->out); }
+
+template <int NT, int VPT, bool VEC>
+void launch_row(bool ln, int grid, cudaStream_t st, const ifr_victim_cfg *c, DevTiming *tm) {
+    if (ln) {
+        ifr_carveout((const void *)layernorm_kernel<NT, VPT, VEC>);
+        layernorm_kernel<NT, VPT, VEC><<<grid, NT, 0, st>>>((const float *)c->in0, (float *)c->out, c->m, (int)c->n,
+                                                            c->eps > 0.f ? c->eps : 1e-5f, tm);
+    } else {
+        ifr_carveout((const void *)softmax_kernel<NT, VPT, VEC>);
+        softmax_kernel<NT, VPT, VEC><<<grid, NT, 0, st>>>((const float *)c->in0, (float *)c->out, c->m, (int)c->n,
+                                                          tm);
+    }
 }
-template <int NT, int VPT>
-void launch_sm(int grid, cudaStream_t st, const ifr_victim_cfg *c, DevTiming *tm) {
-    ifr_carveout((const void *)softmax_kernel<NT, VPT>);
-    softmax_kernel<NT, VPT><<<grid, NT, 0, st>>>((const float *)c->in0, (float *)c->out, c->m, (int)c->n, tm);
+
+template <bool VEC>
+const void *row_fn(bool ln, int c4) {
+    if (c4 <= 256 * 4) return ln ? (const void *)layernorm_kernel<256, 4, VEC> : (const void *)softmax_kernel<256, 4, VEC>;
+    if (c4 <= 256 * 8) return ln ? (const void *)layernorm_kernel<256, 8, VEC> : (const void *)softmax_kernel<256, 8, VEC>;
+    return ln ? (const void *)layernorm_kernel<1024, 8, VEC> : (const void *)softmax_kernel<1024, 8, VEC>;
 }
 
 }  // namespace
@@ -448,8 +504,8 @@ int ifr_victim_validate(ifr_ctx *ctx, const ifr_victim_cfg *c) {
             return IFR_OK;
         case IFR_V_LAYERNORM:
         case IFR_V_SOFTMAX:
-            if (c->m <= 0 || c->n <= 0 || c->n % 4 || c->n > 32768) return IFR_ERR_ARG;
-            if (!aligned16(c->in0) || !aligned16(c->out)) return IFR_ERR_ARG;
+            if (c->m <= 0 || c->n <= 0 || c->n > 32768) return IFR_ERR_ARG;
+            if (((uintptr_t)c->in0 & 3u) || ((uintptr_t)c->out & 3u)) return IFR_ERR_ARG;
             return IFR_OK;
         case IFR_V_GEMV:
             if (!c->in1 || c->m <= 0 || c->k <= 0 || c->k % 8 || c->k > 24576) return IFR_ERR_ARG;
@@ -485,16 +541,12 @@ int ifr_victim_shape(ifr_ctx *ctx, const ifr_victim_cfg *c, VictimShape *s) {
         case IFR_V_LAYERNORM:
         case IFR_V_SOFTMAX: {
             const int64_t rows = c->m;
-            const int c4 = (int)c->n / 4;
+            const int c4 = (int)((c->n + 3) / 4);
             const bool ln = c->kind == IFR_V_LAYERNORM;
-            if (c4 <= 256 * 4) {
-                s->fn = ln ? (const void *)layernorm_kernel<256, 4> : (const void *)softmax_kernel<256, 4>;
-                s->grid = c->grid ? c->grid : (int)(rows < (int64_t)sms * 8 ? rows : (int64_t)sms * 8);
-            } else if (c4 <= 256 * 8) {
-                s->fn = ln ? (const void *)layernorm_kernel<256, 8> : (const void *)softmax_kernel<256, 8>;
+            s->fn = rows_vec(c) ? row_fn<true>(ln, c4) : row_fn<false>(ln, c4);
+            if (c4 <= 256 * 8) {
                 s->grid = c->grid ? c->grid : (int)(rows < (int64_t)sms * 8 ? rows : (int64_t)sms * 8);
             } else {
-                s->fn = ln ? (const void *)layernorm_kernel<1024, 8> : (const void *)softmax_kernel<1024, 8>;
                 s->block = 1024;
                 s->grid = c->grid ? c->grid : (int)(rows < (int64_t)sms * 2 ? rows : (int64_t)sms * 2);
             }
@@ -546,14 +598,16 @@ int ifr_victim_enqueue(ifr_ctx *ctx, const ifr_victim_cfg *c, cudaStream_t strea
             }
             case IFR_V_LAYERNORM:
             case IFR_V_SOFTMAX: {
-                const int c4 = (int)c->n / 4;
+                const int c4 = (int)((c->n + 3) / 4);
                 const bool ln = c->kind == IFR_V_LAYERNORM;
-                if (c4 <= 256 * 4) {
-                    if (ln) launch_ln<256, 4>(sh.grid, stream, c, tm); else launch_sm<256, 4>(sh.grid, stream, c, tm);
-                } else if (c4 <= 256 * 8) {
-                    if (ln) launch_ln<256, 8>(sh.grid, stream, c, tm); else launch_sm<256, 8>(sh.grid, stream, c, tm);
+                if (rows_vec(c)) {
+                    if (c4 <= 256 * 4) launch_row<256, 4, true>(ln, sh.grid, stream, c, tm);
+                    else if (c4 <= 256 * 8) launch_row<256, 8, true>(ln, sh.grid, stream, c, tm);
+                    else launch_row<1024, 8, true>(ln, sh.grid, stream, c, tm);
                 } else {
-                    if (ln) launch_ln<1024, 8>(sh.grid, stream, c, tm); else launch_sm<1024, 8>(sh.grid, stream, c, tm);
+                    if (c4 <= 256 * 4) launch_row<256, 4, false>(ln, sh.grid, stream, c, tm);
+                    else if (c4 <= 256 * 8) launch_row<256, 8, false>(ln, sh.grid, stream, c, tm);
+                    else launch_row<1024, 8, false>(ln, sh.grid, stream, c, tm);
                 }
                 break;
             }
@@ -659,9 +713,10 @@ int ifr_preload_victims() {
     const void *fns[] = {
         (const void *)timing_reset_kernel, (const void *)triad_kernel, (const void *)gemv_kernel,
         gemv_short_fn(1), gemv_short_fn(2), gemv_short_fn(4), gemv_short_fn(8), gemv_short_fn(16), gemv_short_fn(32),
-        (const void *)hist_kernel, (const void *)layernorm_kernel<256, 4>, (const void *)layernorm_kernel<256, 8>,
-        (const void *)layernorm_kernel<1024, 8>, (const void *)softmax_kernel<256, 4>,
-        (const void *)softmax_kernel<256, 8>, (const void *)softmax_kernel<1024, 8>};
+        (const void *)hist_kernel, row_fn<true>(true, 1), row_fn<true>(true, 2048), row_fn<true>(true, 4096),
+        row_fn<true>(false, 1), row_fn<true>(false, 2048), row_fn<true>(false, 4096), row_fn<false>(true, 1),
+        row_fn<false>(true, 2048), row_fn<false>(true, 4096), row_fn<false>(false, 1), row_fn<false>(false, 2048),
+        row_fn<false>(false, 4096)};
     for (const void *f : fns) {
         int rc = ifr_preload(f);
         if (rc) return rc;

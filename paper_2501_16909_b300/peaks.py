@@ -76,12 +76,16 @@ def copy_cfg(cfg, **over):
 
 
 def solo_rate(ctx, cfg, rounds=None, launches=8):
-    """Run a fixed-work copy of cfg alone; returns (rate in UNIT/s, result)."""
+    """Run a fixed-work copy of cfg alone; returns (rate in UNIT/s, result).
+
+    A duty-cycled run (0 < duty < 1) does four times the rounds: a fixed-work run
+    ends inside its last period, so its rate differs from the long-run rate by up to
+    (1 - duty) x period over the run's length, which a longer run keeps small."""
     over = {}
     if cfg.kind == A.IFR_S_SCHED:
         over["sched_launches"] = launches
     else:
-        over["max_rounds"] = rounds or CAL_ROUNDS[cfg.kind]
+        over["max_rounds"] = (rounds or CAL_ROUNDS[cfg.kind]) * (4 if 0.0 < cfg.duty < 1.0 else 1)
     res, _ = ctx.run_stressor(copy_cfg(cfg, **over), 30000)
     ms = res["elapsed_ms"]
     return (work_units(cfg, res) / (ms * 1e-3) if ms > 0 else 0.0), res

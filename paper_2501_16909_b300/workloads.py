@@ -169,11 +169,19 @@ def config3_shapes(seed: int = 3):
     return shapes
 
 
-def config3_victims(device="cuda", seed: int = 3, launches: int = 1):
-    """Allocate and fill the 64 config-3 victims (inputs seeded per victim index)."""
+def config3_seeds(i: int) -> int:
+    """Input seed of config-3 victim i (its second input uses the next seed)."""
+    return 100 + 4 * i
+
+
+def config3_victims(device="cuda", seed: int = 3, launches: int = 1, only=None):
+    """Allocate and fill the 64 config-3 victims (inputs seeded per victim index),
+    or only the victims whose indices are listed in `only` (same shapes and seeds)."""
     t, victims, kinds = {}, [], []
     for i, (kind, a, b, c) in enumerate(config3_shapes(seed)):
-        s = 100 + 4 * i
+        if only is not None and i not in only:
+            continue
+        s = config3_seeds(i)
         if kind == "gemm":
             M, N, K = a, b, c
             A_ = I.torch_normal_bf16(s, M * K, device).view(M, K)

@@ -65,7 +65,7 @@ def test_struct_layouts_match_header(tmp_path, lib):
 
 
 def test_strerror_and_version(lib):
-    assert lib.ifr_abi_version() == 3
+    assert lib.ifr_abi_version() == 4
     assert lib.ifr_strerror(0) == b"ok"
     assert b"deadline" in lib.ifr_strerror(-3)
 

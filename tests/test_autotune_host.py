@@ -88,3 +88,22 @@ def test_probes_are_cached(monkeypatch):
     calls = _install(monkeypatch, lambda n, d: n * d)
     _tune(A.IFR_S_FMA)
     assert len(calls) == len(set(calls))
+
+
+@pytest.mark.parametrize("shape", ["offset", "concave", "noisy_step"])
+def test_duty_search_handles_nonproportional_rates(monkeypatch, shape):
+    # below one SM's share only the duty cycle can reach the target, and the rate is not
+    # proportional to the duty (each on-phase starts with an empty pipeline)
+    def duty_part(d):
+        if shape == "offset":
+            return max(0.0, (d - 0.08) / 0.92)
+        if shape == "concave":
+            return d ** 0.6
+        return max(0.0, d - 0.05) + (0.01 if d > 0.3 else 0.0)
+
+    _install(monkeypatch, lambda n, d: n * (duty_part(d) if d < 1.0 else 1.0))
+    t = T.Tuner(FakeCtx(), ifr.stressor_cfg(A.IFR_S_HBM, sm_count=S), peak=1.0, tol=0.05)
+    _rmax, levels = t.tune([0.002, 0.004, 0.5])
+    for lv in levels:
+        assert abs(lv.frac_of_max / lv.target - 1) <= 0.05, (shape, lv)
+    assert levels[0].sm_count == 1 and levels[0].duty < 1.0

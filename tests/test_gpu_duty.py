@@ -1,0 +1,120 @@
+"""GPU tests of the duty-cycle intensity control (the third intensity knob beside
+the SM mask and the grid).
+
+A stressor at duty D over a period P is active for D*P of every P (the periods are
+aligned on %globaltimer, so all its blocks are on together) and carries the
+difference made by rounds that overrun the window into the next period.  For a
+fixed-work run the checks are:
+
+* the work is unchanged: every block's checksum equals the oracle's;
+* the achieved rate (algorithmic work over the first-start to last-end span) is
+  D times the duty-1 rate within +-10 %;
+* a run without a round limit ends within one period of its stop request: all
+  blocks end within P of the first block to end (the first one ends only because
+  it saw the stop flag).
+"""
+import time
+
+import numpy as np
+import pytest
+
+import ifr_inputs as I
+import oracle
+import paper_2501_16909_b300 as ifr
+from paper_2501_16909_b300 import _abi as A
+from paper_2501_16909_b300 import peaks as P
+from tests.gpu_common import need_gpu, spread_mask
+
+pytestmark = pytest.mark.gpu
+
+DUTIES = [0.25, 0.5, 0.75]
+PERIOD_NS = 50_000
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    need_gpu()
+    c = ifr.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def hbm_buf():
+    need_gpu()
+    return I.torch_u32_as_i32(1, (1 << 30) // 4, "cuda")
+
+
+def _cases(ctx, hbm_buf):
+    S = ctx.info["num_sms"]
+    return {
+        # full SMs, 2 blocks of 512 per SM, 1 GiB set: a round is 4 chunks of 32 KiB per block
+        "hbm": ifr.stressor_cfg(A.IFR_S_HBM, sm_count=S, blocks_per_sm=2, block=512, buf=hbm_buf,
+                                working_set_bytes=1 << 30, max_rounds=128, seed=0),
+        # 16 SMs, one warp of 4 chains each (the oracle recomputes every chain of every block)
+        "fma": ifr.stressor_cfg(A.IFR_S_FMA, sm_count=16, blocks_per_sm=1, block=32, ilp=4, max_rounds=64, seed=7),
+        # full SMs, 2 blocks of 256 per SM, conflict-free
+        "smem_cf": ifr.stressor_cfg(A.IFR_S_SMEM_CF, sm_count=S, blocks_per_sm=2, block=256, max_rounds=64, seed=5),
+    }
+
+
+def _check_blocks(ctx, name, cfg, logs, hbuf):
+    S = ctx.info["num_sms"]
+    planned = cfg.sm_count * cfg.blocks_per_sm
+    assert len(logs) == planned
+    assert {L["smid"] for L in logs} <= spread_mask(S, cfg.sm_count)
+    for L in logs:
+        assert L["status"] == 0 and L["rounds"] == cfg.max_rounds, L
+        if name == "hbm":
+            assert L["checksum"] == oracle.stream_block_checksum(hbuf, cfg.block * 16, planned, L["index"], L["work"])
+            assert L["work"] == 4 * cfg.max_rounds
+        elif name == "fma":
+            steps = 16384 // cfg.ilp
+            r0, fin = oracle.fma_block(cfg.seed, L["index"], cfg.block, cfg.ilp, steps, cfg.max_rounds)
+            assert (L["checksum"], L["checksum2"]) == (r0, fin)
+        else:
+            passes = 32  # conflict-free: 32 passes over the warp array per round
+            assert L["checksum"] == oracle.smem_block(cfg.seed, L["index"], cfg.block // 32, cfg.max_rounds, passes)
+
+
+def _rate(cfg, res):
+    span = res["t_end_ns"] - res["t_start_ns"]
+    assert span > 0
+    return P.work_units(cfg, res) / (span * 1e-9)
+
+
+@pytest.mark.parametrize("name", ["hbm", "fma", "smem_cf"])
+def test_duty_cycle_rate_and_checksums(ctx, hbm_buf, name):
+    cfg = _cases(ctx, hbm_buf)[name]
+    hbuf = hbm_buf.cpu().numpy().view(np.uint32) if name == "hbm" else None
+    rates = {}
+    for d in [1.0] + DUTIES:
+        c = P.copy_cfg(cfg, duty=0.0 if d == 1.0 else d, period_ns=PERIOD_NS)
+        rs = []
+        for _ in range(2):
+            res, logs = ctx.run_stressor(c, 20000)
+            assert res["status"] == 0
+            _check_blocks(ctx, name, c, logs, hbuf)
+            rs.append(_rate(c, res))
+        rates[d] = sum(rs) / len(rs)
+    for d in DUTIES:
+        ratio = rates[d] / rates[1.0]
+        assert abs(ratio / d - 1.0) <= 0.10, (name, d, ratio, rates)
+
+
+@pytest.mark.parametrize("name", ["hbm", "fma"])
+def test_duty_cycle_stops_within_one_period(ctx, hbm_buf, name):
+    period = 1_000_000
+    cfg = P.copy_cfg(_cases(ctx, hbm_buf)[name], max_rounds=0, duty=0.5, period_ns=period, deadline_ns=5_000_000_000)
+    h = ctx.stressor_launch(cfg)
+    time.sleep(0.03)
+    ctx.stressor_stop(h)
+    res = ctx.stressor_wait(h, 20000)
+    logs = ctx.stressor_block_logs(h)
+    ctx.stressor_release(h)
+    assert res["status"] == 0 and len(logs) == cfg.sm_count * cfg.blocks_per_sm
+    assert all(L["status"] == 0 and L["rounds"] > 0 for L in logs)
+    ends = sorted(L["t_end_ns"] for L in logs)
+    assert ends[-1] - ends[0] <= period, (ends[-1] - ends[0])
+    # the run lasted until the stop (about 30 ms), not until the 5 s deadline
+    assert 20_000_000 <= res["t_end_ns"] - res["t_start_ns"] <= 1_000_000_000

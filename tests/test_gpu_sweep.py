@@ -87,8 +87,15 @@ def test_corun_two_kernels_valid_and_consistent(setup):
     vs, vc = r["victim_solo"], r["victim_corun"]
     assert vc["t_start_ns"] >= r["corunner_corun"]["t_start_ns"]
     assert vc["t_end_ns"] <= r["corunner_corun"]["t_end_ns"]
-    want = ((vc["t_end_ns"] - vc["t_start_ns"]) / vc["repeats"]) / ((vs["t_end_ns"] - vs["t_start_ns"]) / vs["repeats"])
+
+    def meas(t):
+        return dict(t_start=t["t_start_ns"], t_end=t["t_end_ns"], k=t["repeats"])
+
+    # the library reduces the raw stamps itself; the oracle's definition on the same stamps
+    want = R.corun_slowdown(meas(vs), meas(vc))
     assert math.isclose(r["victim_slowdown"], want, rel_tol=1e-12)
+    want_c = R.corun_slowdown(meas(r["corunner_solo"]), meas(r["corunner_corun"]))
+    assert math.isclose(r["corunner_slowdown"], want_c, rel_tol=1e-12)
     assert r["victim_slowdown"] > 1.1
     assert r["blocked"] == 0 and r["corunner_corun"]["t_start_ns"] <= r["victim_release_ns"] <= vc["t_start_ns"]
 

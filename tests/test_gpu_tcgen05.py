@@ -125,7 +125,7 @@ def test_tensor_stressor_bit_exact(ctx, sm_frac, bps, rounds):
     r, logs = ctx.run_stressor(cfg, 20000)
     assert r["status"] == 0 and len(logs) == n_sm * bps
     assert {L["smid"] for L in logs} <= spread_mask(S, n_sm)
-    for L in logs[:: max(1, len(logs) // 8)]:
+    for L in logs:
         assert L["rounds"] == rounds and L["work"] == rounds * 64
         assert L["checksum"] == oracle.tensor_block(12, L["index"], 64), L
 

@@ -31,28 +31,90 @@ def test_triad(ctx, n):
     assert_fp32_close(a.cpu().numpy(), ref)
 
 
-@pytest.mark.parametrize("rows,cols", [(1, 4), (7, 1000), (33, 4096), (5, 6000), (3, 12000), (16384, 4096)])
-def test_layernorm(ctx, rows, cols):
-    x = I.torch_uniform_pm1(4, rows * cols, "cuda").view(rows, cols)
+# every row is compared, up to the full 16384 x 4096 (and 8192 x 8192 softmax)
+# workloads; widths that are not a multiple of 4, and rows that do not start on a
+# 16-byte boundary (offset 1: the base pointer is 4 bytes past an aligned one), take
+# the column-by-column path
+LN_SHAPES = [(1, 4), (7, 1000), (33, 4096), (5, 6000), (3, 12000), (16384, 4096), (37, 4095), (5, 13), (1, 1),
+             (1000, 1001), (3, 32767), (9, 30)]
+
+
+def _rows_input(seed, rows, cols, offset, scale=1.0):
+    full = I.torch_uniform_pm1(seed, rows * cols + offset, "cuda") * scale
+    x = full[offset:].view(rows, cols)
+    ref = (I.np_uniform_pm1(seed, np.arange(rows * cols + offset)) * np.float32(scale))[offset:].reshape(rows, cols)
+    return full, x, ref
+
+
+@pytest.mark.parametrize("rows,cols", LN_SHAPES)
+@pytest.mark.parametrize("offset", [0, 1])
+def test_layernorm_every_row(ctx, rows, cols, offset):
+    if offset and rows * cols > 1 << 22:
+        pytest.skip("the unaligned path is covered on the smaller shapes")
+    full, x, xs = _rows_input(4, rows, cols, offset)
+    yfull = torch.empty(rows * cols + offset, device="cuda")
+    y = yfull[offset:].view(rows, cols)
+    t = ctx.victim_launch(ifr.victim_cfg(A.IFR_V_LAYERNORM, x, None, y, m=rows, n=cols))
+    assert t["status"] == 0
+    ref = oracle.layernorm_rows(xs, np.arange(rows), 1e-5)
+    assert_fp32_close(y.cpu().numpy(), ref)
+
+
+def test_layernorm_constant_rows(ctx):
+    """Rows of one repeated value have zero variance: the output is 0 (up to the
+    rounding of the fp32 mean, far inside the tolerance's rms floor)."""
+    rows, cols = 64, 4096
+    xs = I.np_uniform_pm1(21, np.arange(rows * cols)).reshape(rows, cols).copy()
+    consts = [0.0, 0.1, 3.0, -2.5, 1e-20, 7.25e3]
+    for i, c in enumerate(consts):
+        xs[5 * i] = np.float32(c)
+    x = torch.tensor(xs, device="cuda")
     y = torch.empty_like(x)
     t = ctx.victim_launch(ifr.victim_cfg(A.IFR_V_LAYERNORM, x, None, y, m=rows, n=cols))
     assert t["status"] == 0
-    sel = np.unique(np.linspace(0, rows - 1, min(rows, 24)).astype(np.int64))
-    xs = I.np_uniform_pm1(4, np.arange(rows * cols)).reshape(rows, cols)
-    ref = oracle.layernorm_rows(xs, sel, 1e-5)
-    assert_fp32_close(y.cpu().numpy()[sel], ref)
+    ref = oracle.layernorm_rows(xs, np.arange(rows), 1e-5)
+    for i in range(len(consts)):
+        assert np.all(ref[5 * i] == 0.0)
+    assert_fp32_close(y.cpu().numpy(), ref)
 
 
-@pytest.mark.parametrize("rows,cols", [(1, 4), (9, 1000), (17, 8192), (4, 20000), (8192, 8192)])
-def test_softmax(ctx, rows, cols):
-    x = (I.torch_uniform_pm1(6, rows * cols, "cuda") * 4).view(rows, cols)
+SM_SHAPES = [(1, 4), (9, 1000), (17, 8192), (4, 20000), (8192, 8192), (37, 4095), (5, 13), (1, 1), (1000, 1001),
+             (2, 32767)]
+
+
+@pytest.mark.parametrize("rows,cols", SM_SHAPES)
+@pytest.mark.parametrize("offset", [0, 1])
+def test_softmax_every_row(ctx, rows, cols, offset):
+    if offset and rows * cols > 1 << 22:
+        pytest.skip("the unaligned path is covered on the smaller shapes")
+    full, x, xs = _rows_input(6, rows, cols, offset, scale=4.0)
+    yfull = torch.empty(rows * cols + offset, device="cuda")
+    y = yfull[offset:].view(rows, cols)
+    t = ctx.victim_launch(ifr.victim_cfg(A.IFR_V_SOFTMAX, x, None, y, m=rows, n=cols))
+    assert t["status"] == 0
+    ref = oracle.softmax_rows(xs, np.arange(rows))
+    assert_fp32_close(y.cpu().numpy(), ref)
+    assert np.allclose(y.double().sum(dim=1).cpu().numpy(), 1.0, rtol=0, atol=1e-5)
+
+
+@pytest.mark.parametrize("cols", [4096, 1001])
+def test_softmax_wide_dynamic_range(ctx, cols):
+    """Rows spanning +-80 (exp(x - max) down to e^-160, far below the fp32 range)
+    and rows with one dominant entry."""
+    rows = 256
+    xs = (I.np_uniform_pm1(23, np.arange(rows * cols)) * np.float32(80.0)).reshape(rows, cols).copy()
+    xs[7] = np.float32(-80.0)
+    xs[7, 100] = np.float32(80.0)
+    xs[11] = np.float32(0.0)
+    x = torch.tensor(xs, device="cuda")
     y = torch.empty_like(x)
     t = ctx.victim_launch(ifr.victim_cfg(A.IFR_V_SOFTMAX, x, None, y, m=rows, n=cols))
     assert t["status"] == 0
-    sel = np.unique(np.linspace(0, rows - 1, min(rows, 16)).astype(np.int64))
-    xs = (I.np_uniform_pm1(6, np.arange(rows * cols)) * 4).reshape(rows, cols)
-    ref = oracle.softmax_rows(xs, sel)
-    assert_fp32_close(y.cpu().numpy()[sel], ref)
+    ref = oracle.softmax_rows(xs, np.arange(rows))
+    got = y.cpu().numpy()
+    assert_fp32_close(got, ref)
+    assert got[7, 100] == 1.0 and np.all(np.delete(got[7], 100) == 0.0)
+    assert np.allclose(got[11], 1.0 / cols, rtol=1e-6)
 
 
 # rows of up to 256 columns take the short-row kernel (several rows per warp)
@@ -64,7 +126,7 @@ def test_gemv(ctx, rows, cols):
     y = torch.empty(rows, device="cuda")
     t = ctx.victim_launch(ifr.victim_cfg(A.IFR_V_GEMV, Ab, xb, y, m=rows, k=cols))
     assert t["status"] == 0
-    sel = np.unique(np.linspace(0, rows - 1, min(rows, 64)).astype(np.int64))
+    sel = np.arange(rows)  # every row
     A_np = oracle.f32_bits_to_bf16_bits(I.np_normal_bf16(7, np.arange(rows * cols))).reshape(rows, cols)
     x_np = oracle.f32_bits_to_bf16_bits(I.np_normal_bf16(8, np.arange(cols)))
     assert np.array_equal(bf16_bits(xb), x_np)
@@ -87,6 +149,16 @@ def test_histogram_bit_exact(ctx, n):
     assert int(got.sum()) == n
 
 
+class _Ptr:
+    """A raw device address in the shape victim_cfg expects (something with data_ptr())."""
+
+    def __init__(self, p):
+        self.p = p
+
+    def data_ptr(self):
+        return self.p
+
+
 def test_victim_bad_args(ctx):
     import ctypes as C
 
@@ -95,7 +167,9 @@ def test_victim_bad_args(ctx):
     t = A.ifr_timing()
     bad = [
         ifr.victim_cfg(A.IFR_V_TRIAD, x, x, x, n=0),
-        ifr.victim_cfg(A.IFR_V_LAYERNORM, x, None, x, m=2, n=30),  # cols not a multiple of 4
+        ifr.victim_cfg(A.IFR_V_LAYERNORM, x, None, x, m=2, n=40000),  # wider than a row can be held
+        ifr.victim_cfg(A.IFR_V_SOFTMAX, x, None, x, m=0, n=8),                # no rows
+        ifr.victim_cfg(A.IFR_V_SOFTMAX, _Ptr(x.data_ptr() + 2), None, x, m=2, n=8),  # not 4-byte aligned
         ifr.victim_cfg(A.IFR_V_GEMV, x, x, x, m=2, k=12),          # cols not a multiple of 8
         ifr.victim_cfg(A.IFR_V_TRIAD, x[1:], x, x, n=8),           # misaligned
         ifr.victim_cfg(17, x, x, x, n=8),

@@ -97,3 +97,14 @@ def test_register_admission_paper_example():
     victim = dict(threads=1024, regs=kv["victim_regs_per_block"], smem=0)
     assert admission.admits(sm, [stress], victim) == bool(kv["expected_admitted"])
     assert admission.admits(sm, [], victim)
+
+
+def test_corun_slowdown_forged_logs():
+    # a victim whose 3 launches take 2x as long beside the co-runner, counted per launch
+    alone = dict(t_start=100, t_end=100 + 3 * 500, k=3)
+    both = dict(t_start=9000, t_end=9000 + 3 * 1000, k=3)
+    assert R.corun_slowdown(alone, both) == 2.0
+    # different launch counts on the two sides: per-launch times, not spans
+    chain_alone = dict(t_start=0, t_end=700, k=1)
+    chain_co = dict(t_start=0, t_end=10 * 770, k=10)
+    assert math.isclose(R.corun_slowdown(chain_alone, chain_co), 1.1, rel_tol=1e-12)

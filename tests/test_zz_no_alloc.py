@@ -7,7 +7,10 @@ ifr_stream_stressor_noalloc, whose control state lives in a file-scope device
 array.  Its per-block results must equal those of the context-based entry point
 (ifr_stressor_launch + ifr_stressor_wait + ifr_stressor_block_logs) for the same
 fixed-work configuration, on two calls in a row (the second call must clear what
-the first left in the shared array).  This file is collected last.
+the first left in the shared array); every block's checksum must also equal the
+oracle's, so that a fault shared by both entry points is still caught; and calls
+after the first must leave the device's free memory unchanged.  This file is
+collected last.
 """
 import ctypes as C
 
@@ -16,6 +19,7 @@ import pytest
 import torch
 
 import ifr_inputs as I
+import oracle
 import paper_2501_16909_b300 as ifr
 from paper_2501_16909_b300 import _abi as A
 
@@ -49,10 +53,23 @@ def test_noalloc_matches_context_entry_point_twice():
         assert r["status"] == 0
         want = {lg["index"]: (lg["checksum"], lg["work"], lg["rounds"], lg["status"]) for lg in logs}
     assert len(want) == sm_count * bps
+    hbuf = buf.cpu().numpy().view(np.uint32)
+    planned = sm_count * bps
+    for k, (cs, work, rnd, status) in want.items():
+        assert status == 0 and rnd == rounds
+        assert cs == oracle.stream_block_checksum(hbuf, block * 16, planned, k, work), k
     stream = torch.cuda.Stream()
-    for _ in range(2):
+    free_before = None
+    for call in range(3):
         got = _noalloc_logs(L, kind, buf, nbytes, sm_count, bps, block, rounds, stream)
-        assert got == want
+        assert got == want, call
+        torch.cuda.synchronize()
+        free = torch.cuda.mem_get_info()[0]
+        if free_before is None:
+            # the first call may load the entry point's kernels; later calls change nothing
+            free_before, alloc_before = free, torch.cuda.memory_allocated()
+        else:
+            assert free == free_before and torch.cuda.memory_allocated() == alloc_before, call
 
 
 def test_noalloc_rejects_bad_sizes():
