@@ -38,7 +38,7 @@ def lib():
         L.or_splitmix64.restype = u64
         L.or_splitmix64.argtypes = [u64, u64]
         L.or_stream_block_checksum.restype = u32
-        L.or_stream_block_checksum.argtypes = [p, i64, i64, i64, i64, i64]
+        L.or_stream_block_checksum.argtypes = [p, i64, i64, i64, i64, i64, i32]
         L.or_fma_block.restype = None
         L.or_fma_block.argtypes = [u64, i64, i32, i32, i32, i64, p, p]
         L.or_fp64_block.restype = None
@@ -77,9 +77,16 @@ def splitmix64(s0: int, i: int) -> int:
 
 
 # ------------------------------------------------------------------ stressors
-def stream_block_checksum(buf_u32: np.ndarray, chunk_elems: int, active_planned: int, k: int, count: int) -> int:
+# fold of the L2 / HBM stream stressor's checksum: by vector loads into registers
+# (first word of every 16-byte group) or by bulk copies into shared memory (quarter
+# pass mod 4 of each chunk); see ifr_oracle.c
+FOLD_LOADS, FOLD_BULK = 0, 1
+
+
+def stream_block_checksum(buf_u32: np.ndarray, chunk_elems: int, active_planned: int, k: int, count: int,
+                          fold: int = FOLD_LOADS) -> int:
     b = np.ascontiguousarray(buf_u32, dtype=np.uint32)
-    return int(lib().or_stream_block_checksum(_ptr(b), b.size, chunk_elems, active_planned, k, count))
+    return int(lib().or_stream_block_checksum(_ptr(b), b.size, chunk_elems, active_planned, k, count, fold))
 
 
 def fma_block(seed: int, k: int, block: int, ilp: int, steps: int, rounds: int):

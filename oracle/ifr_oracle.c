@@ -47,18 +47,23 @@ static uint32_t f32_bits(float f) {
 /* ------------------------------------------------------------------------- */
 /* L2 / HBM stream stressor (the paper's copy kernel, Sec. 3 Pitfall 2 and     */
 /* Sec. 4.3).  The buffer of n int32 words is cut into chunks of chunk_elems   */
-/* (a multiple of 4), each split into four contiguous quarters.  Active block  */
-/* k of A (planned) reads the chunks c = k, k+A, k+2A, ... (m_k of them) in    */
-/* that order, cycling; its j-th chunk read (j = 0..count-1) is chunk          */
-/* c_j = k + (j mod m_k)*A in pass p_j = floor(j / m_k).  The kernel reads     */
-/* every word of every chunk but folds one quarter per read: the block's       */
-/* checksum is XOR_j rotl(X(c_j, p_j mod 4), p_j mod 32) where X(c, q) is the  */
-/* XOR of the words of quarter q of chunk c.  Four consecutive passes fold     */
-/* every word of the block's chunks once.                                     */
+/* (a multiple of 4).  Active block k of A (planned) reads the chunks          */
+/* c = k, k+A, k+2A, ... (m_k of them) in that order, cycling; its j-th chunk  */
+/* read (j = 0..count-1) is chunk c_j = k + (j mod m_k)*A in pass              */
+/* p_j = floor(j / m_k).  The kernel reads every word of every chunk and folds */
+/* a part of it, by `fold`:                                                   */
+/*   fold 0 (loads into registers): the first word of every 16-byte group,    */
+/*          words 4i of the chunk, so every 16-byte load enters the fold;     */
+/*   fold 1 (bulk copies into shared memory): quarter p_j mod 4 of the chunk  */
+/*          (the chunk's four contiguous quarters), so four consecutive       */
+/*          passes fold every word once.                                      */
+/* The block's checksum is XOR_j rotl(F(c_j, p_j), p_j mod 32) where F is the */
+/* XOR of the folded words.                                                   */
 /* ------------------------------------------------------------------------- */
 uint32_t or_stream_block_checksum(const uint32_t *buf, int64_t n_elems, int64_t chunk_elems,
-                                  int64_t active_planned, int64_t k, int64_t count) {
+                                  int64_t active_planned, int64_t k, int64_t count, int fold) {
     if (chunk_elems <= 0 || chunk_elems % 4 || active_planned <= 0 || k < 0 || count <= 0) return 0u;
+    if (fold != 0 && fold != 1) return 0u;
     int64_t n_chunks = n_elems / chunk_elems;
     if (k >= n_chunks) return 0u;
     int64_t m_k = (n_chunks - k + active_planned - 1) / active_planned;
@@ -67,9 +72,14 @@ uint32_t or_stream_block_checksum(const uint32_t *buf, int64_t n_elems, int64_t 
     for (int64_t j = 0; j < count; ++j) {
         int64_t c = k + (j % m_k) * active_planned;
         int64_t p = j / m_k;
-        int64_t q = p % 4;
+        const uint32_t *w = buf + c * chunk_elems;
         uint32_t x = 0u;
-        for (int64_t e = q * quarter; e < (q + 1) * quarter; ++e) x ^= buf[c * chunk_elems + e];
+        if (fold == 0) {
+            for (int64_t e = 0; e < chunk_elems; e += 4) x ^= w[e];
+        } else {
+            int64_t q = p % 4;
+            for (int64_t e = q * quarter; e < (q + 1) * quarter; ++e) x ^= w[e];
+        }
         acc ^= rotl32(x, (unsigned)(p & 31));
     }
     return acc;

@@ -15,67 +15,98 @@ def rotl(x, r):
 
 
 # ---------------------------------------------------------------- stream (L2/HBM)
-def _stream_brute(buf, chunk, A, k, count):
+def _stream_brute(buf, chunk, A, k, count, fold):
     """Written a second way: the block's chunk list in reading order, and for every
-    chunk the XOR of each of its four quarters, looked up by the pass number."""
+    chunk the XOR of its first-of-16-bytes words and of each of its four quarters,
+    looked up by the pass number."""
     n_chunks = buf.size // chunk
     mine = [c for c in range(n_chunks) if c % A == k]
     if not mine:
         return 0
     q = chunk // 4
+    X0 = [int(np.bitwise_xor.reduce(buf[c * chunk:(c + 1) * chunk][0::4])) for c in range(n_chunks)]
     XQ = [[int(np.bitwise_xor.reduce(buf[c * chunk + i * q:c * chunk + (i + 1) * q])) for i in range(4)]
           for c in range(n_chunks)]
     acc = 0
     for j in range(count):
         p = j // len(mine)
-        acc ^= rotl(XQ[mine[j % len(mine)]][p % 4], p)
+        c = mine[j % len(mine)]
+        acc ^= rotl(X0[c] if fold == 0 else XQ[c][p % 4], p)
     return acc
 
 
+@pytest.mark.parametrize("fold", [oracle.FOLD_LOADS, oracle.FOLD_BULK])
 @pytest.mark.parametrize("A,k,count", [(3, 0, 1), (3, 2, 7), (5, 4, 40), (7, 1, 0), (4, 3, 13), (16, 9, 3),
                                        (2, 1, 77)])
-def test_stream_checksum_brute(A, k, count):
+def test_stream_checksum_brute(A, k, count, fold):
     buf = I.np_u32(1, np.arange(64 * 37))
-    assert oracle.stream_block_checksum(buf, 64, A, k, count) == _stream_brute(buf, 64, A, k, count)
+    assert oracle.stream_block_checksum(buf, 64, A, k, count, fold) == _stream_brute(buf, 64, A, k, count, fold)
 
 
-def test_stream_checksum_four_and_eight_passes_closed_form():
-    # four passes fold quarter p of every chunk in pass p: the checksum is
+def _block_chunks(A, k, n):
+    return [c for c in range(n) if c % A == k]
+
+
+def test_stream_checksum_loads_fold_two_passes_closed_form():
+    # fold 0 folds the same words every pass: two passes give Y ^ rotl(Y, 1), Y the XOR
+    # of the words 4i of the block's chunks
+    buf = I.np_u32(11, np.arange(128 * 20))
+    A, k = 4, 1
+    mine = _block_chunks(A, k, 20)
+    Y = 0
+    for c in mine:
+        Y ^= int(np.bitwise_xor.reduce(buf[c * 128:(c + 1) * 128:4]))
+    assert oracle.stream_block_checksum(buf, 128, A, k, 2 * len(mine), oracle.FOLD_LOADS) == Y ^ rotl(Y, 1)
+    # a flipped first word of a 16-byte group changes it, a flipped second word does not
+    n = len(mine)
+    b0 = buf.copy()
+    b0[mine[1] * 128 + 8] ^= 1
+    assert oracle.stream_block_checksum(b0, 128, A, k, n, oracle.FOLD_LOADS) != oracle.stream_block_checksum(
+        buf, 128, A, k, n, oracle.FOLD_LOADS)
+    b1 = buf.copy()
+    b1[mine[1] * 128 + 9] ^= 1
+    assert oracle.stream_block_checksum(b1, 128, A, k, 3 * n, oracle.FOLD_LOADS) == oracle.stream_block_checksum(
+        buf, 128, A, k, 3 * n, oracle.FOLD_LOADS)
+
+
+def test_stream_checksum_bulk_fold_four_and_eight_passes_closed_form():
+    # fold 1, four passes fold quarter p of every chunk in pass p: the checksum is
     # rotl(Y0, 0) ^ rotl(Y1, 1) ^ rotl(Y2, 2) ^ rotl(Y3, 3), Y_q the XOR of quarter q
     # over the block's chunks; eight passes repeat the quarters with shifts 4..7
     buf = I.np_u32(11, np.arange(128 * 20))
     A, k = 4, 1
-    mine = [c for c in range(20) if c % A == k]
+    mine = _block_chunks(A, k, 20)
     Y = [0, 0, 0, 0]
     for c in mine:
         for q in range(4):
             Y[q] ^= int(np.bitwise_xor.reduce(buf[c * 128 + 32 * q:c * 128 + 32 * (q + 1)]))
     want4 = Y[0] ^ rotl(Y[1], 1) ^ rotl(Y[2], 2) ^ rotl(Y[3], 3)
-    assert oracle.stream_block_checksum(buf, 128, A, k, 4 * len(mine)) == want4
+    assert oracle.stream_block_checksum(buf, 128, A, k, 4 * len(mine), oracle.FOLD_BULK) == want4
     want8 = want4 ^ rotl(Y[0], 4) ^ rotl(Y[1], 5) ^ rotl(Y[2], 6) ^ rotl(Y[3], 7)
-    assert oracle.stream_block_checksum(buf, 128, A, k, 8 * len(mine)) == want8
+    assert oracle.stream_block_checksum(buf, 128, A, k, 8 * len(mine), oracle.FOLD_BULK) == want8
 
 
-def test_stream_checksum_covers_the_folded_quarter_only():
+def test_stream_checksum_bulk_fold_covers_the_pass_quarter_only():
     buf = I.np_u32(11, np.arange(128 * 20))
     A, k = 4, 1
-    mine = [c for c in range(20) if c % A == k]
-    one_pass = oracle.stream_block_checksum(buf, 128, A, k, len(mine))
+    mine = _block_chunks(A, k, 20)
+    F = oracle.FOLD_BULK
+    one_pass = oracle.stream_block_checksum(buf, 128, A, k, len(mine), F)
     # pass 0 folds quarter 0: a flipped word there changes the checksum ...
     b0 = buf.copy()
     b0[mine[2] * 128 + 5] ^= 1
-    assert oracle.stream_block_checksum(b0, 128, A, k, len(mine)) != one_pass
+    assert oracle.stream_block_checksum(b0, 128, A, k, len(mine), F) != one_pass
     # ... a flipped word of quarter 1 does not, until pass 1 has read it
     b1 = buf.copy()
     b1[mine[2] * 128 + 32 + 5] ^= 1
-    assert oracle.stream_block_checksum(b1, 128, A, k, len(mine)) == one_pass
-    assert (oracle.stream_block_checksum(b1, 128, A, k, 2 * len(mine))
-            != oracle.stream_block_checksum(buf, 128, A, k, 2 * len(mine)))
+    assert oracle.stream_block_checksum(b1, 128, A, k, len(mine), F) == one_pass
+    assert oracle.stream_block_checksum(b1, 128, A, k, 2 * len(mine), F) != oracle.stream_block_checksum(
+        buf, 128, A, k, 2 * len(mine), F)
     # another block's chunk is never read by this block
     b2 = buf.copy()
     b2[(mine[0] + 1) * 128 + 5] ^= 1
-    assert oracle.stream_block_checksum(b2, 128, A, k, 8 * len(mine)) == oracle.stream_block_checksum(
-        buf, 128, A, k, 8 * len(mine))
+    assert oracle.stream_block_checksum(b2, 128, A, k, 8 * len(mine), F) == oracle.stream_block_checksum(
+        buf, 128, A, k, 8 * len(mine), F)
 
 
 # ---------------------------------------------------------------- FMA
