@@ -55,6 +55,7 @@ class ifr_stressor_cfg(C.Structure):
         ("working_set_bytes", C.c_int64), ("buf", C.c_void_p), ("seed", C.c_uint64), ("max_rounds", C.c_int64),
         ("sched_blocks", C.c_int32), ("sched_launches", C.c_int32), ("sched_cycles", C.c_int32),
         ("mask_mode", C.c_int32), ("deadline_ns", C.c_uint64), ("sm_mask", C.c_uint32 * (IFR_MAX_SMS // 32)),
+        ("staging", C.c_int32), ("reserved", C.c_int32),
     ]
 
 

@@ -50,6 +50,7 @@ extern "C" int ifr_init(int device, ifr_ctx **out) {
     ifr_ctx *c = (ifr_ctx *)calloc(1, sizeof(ifr_ctx));
     if (!c) return IFR_ERR_NOMEM;
     c->device = device;
+    c->gemm_cnt_key = -1;
     ifr_device_info &d = c->info;
     d.device = device;
     d.num_sms = p.multiProcessorCount;
@@ -140,6 +141,8 @@ extern "C" void ifr_shutdown(ifr_ctx *ctx) {
     for (int i = 0; i < IFR_SLOTS; ++i) slot_free(ctx->slots[i]);
     if (ctx->d_timing) cudaFree(ctx->d_timing);
     if (ctx->d_progress) cudaFree(ctx->d_progress);
+    if (ctx->gemm_ws) cudaFree(ctx->gemm_ws);
+    if (ctx->gemm_cnt) cudaFree(ctx->gemm_cnt);
     if (ctx->s_stress) cudaStreamDestroy(ctx->s_stress);
     if (ctx->s_victim) cudaStreamDestroy(ctx->s_victim);
     if (ctx->s_ctrl) cudaStreamDestroy(ctx->s_ctrl);

@@ -52,6 +52,39 @@ constexpr int RING = 4;  // tile indices in flight between the scheduler and the
 constexpr uint64_t kGemmTimeoutNs = 4000000000ull;
 int g_num_sms = 0;  // persistent grid size (set from the context before each launch)
 
+// Work split of one launch (variant 3).  Units 0 .. full-1 are whole tiles (unit =
+// tile).  When the tiles do not fill the last wave of CTAs, the tiles after `full`
+// are computed as `parts` K ranges each, units full + t*parts + part, so that the
+// last wave holds parts x as many, shorter units.  Each part stores its partial
+// tile in its slot of `ws`; per (tile, epilogue warp) a counter counts the parts
+// that have stored (modulo parts, so it needs no reset between launches), and the
+// last to arrive adds the slots in part order and stores C.  parts = 1: no split.
+struct GemmSplit {
+    int full;
+    int parts;
+    float *ws;      // [split tiles][parts][BM][BN] fp32 partial tiles
+    uint32_t *cnt;  // [split tiles][EPI_WARPS] arrival counters
+};
+
+template <bool SPLIT>
+__device__ __forceinline__ void unit_of(int u, const GemmSplit &sp, int KT, int &tile, int &k0, int &k1, int &part,
+                                        int &fix) {
+    if (!SPLIT || sp.parts <= 1 || u < sp.full) {
+        tile = u;
+        k0 = 0;
+        k1 = KT;
+        part = 0;
+        fix = -1;
+    } else {
+        const int v = u - sp.full;
+        fix = v / sp.parts;
+        part = v % sp.parts;
+        tile = sp.full + fix;
+        k0 = part * KT / sp.parts;
+        k1 = (part + 1) * KT / sp.parts;
+    }
+}
+
 template <int BN, int STAGES>
 struct GemmCfg {
     static constexpr int A_BYTES = BM * BK * 2;
@@ -103,21 +136,25 @@ __device__ __forceinline__ void store_row16(float *dst, const uint32_t (&r)[16])
                            __uint_as_float(r[4 * e + 3]));
 }
 
-template <int BN, int STAGES>
+// ACC accumulators of BN TMEM columns: with two, the MMAs of the next unit run into
+// one while the epilogue drains the other (variant 3, for solo use: 512 columns
+// leave no TMEM for other kernels on the SM).  SPLIT compiles the split last wave
+// in (variant 3 only: the other variants keep their registers).
+template <int BN, int STAGES, int ACC, bool SPLIT>
 __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_kernel(const __grid_constant__ CUtensorMap ta,
                                                                     const __grid_constant__ CUtensorMap tb,
                                                                     float *__restrict__ C, int M, int N, int K,
-                                                                    int group_m, DevTiming *tm) {
+                                                                    int group_m, GemmSplit sp, DevTiming *tm) {
     using Cf = GemmCfg<BN, STAGES>;
     constexpr int CHUNKS = BN / 16;
     extern __shared__ uint8_t g_smem_raw[];
     uint8_t *base = (uint8_t *)(((uintptr_t)g_smem_raw + 1023u) & ~(uintptr_t)1023u);
     uint64_t *full = (uint64_t *)(base + STAGES * Cf::STAGE);
     uint64_t *empty = full + STAGES;
-    uint64_t *tfull = empty + STAGES;
-    uint64_t *tempty = tfull + 1;
-    uint64_t *sfull = tempty + 1;   // [RING] tile index published
-    uint64_t *sempty = sfull + RING; // [RING] tile index read by the MMA lane and 4 epilogue warps
+    uint64_t *tfull = empty + STAGES;  // [ACC]
+    uint64_t *tempty = tfull + ACC;    // [ACC]
+    uint64_t *sfull = tempty + ACC;    // [RING] unit index published
+    uint64_t *sempty = sfull + RING;   // [RING] unit index read by the MMA lane and 4 epilogue warps
     int32_t *ring = (int32_t *)(sempty + RING);
     uint32_t *tmem_slot = (uint32_t *)(ring + RING);
     volatile int *fail = (volatile int *)(tmem_slot + 1);
@@ -126,6 +163,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_kernel(const __grid
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_m = M / BM, tiles_n = N / BN, n_tiles = tiles_m * tiles_n;
     const int KT = K / BK;
+    const int n_units = (SPLIT && sp.parts > 1) ? sp.full + (n_tiles - sp.full) * sp.parts : n_tiles;
     const uint64_t deadline = ifr_gtimer() + kGemmTimeoutNs;
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -136,15 +174,17 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_kernel(const __grid
             tc::mbar_init(&sfull[r], 1);
             tc::mbar_init(&sempty[r], 1 + EPI_WARPS);
         }
-        tc::mbar_init(tfull, 1);
-        tc::mbar_init(tempty, EPI_WARPS);
+        for (int a = 0; a < ACC; ++a) {
+            tc::mbar_init(&tfull[a], 1);
+            tc::mbar_init(&tempty[a], EPI_WARPS);
+        }
         *fail = 0;
         tc::fence_mbar_init();
         tc::prefetch_tmap(&ta);
         tc::prefetch_tmap(&tb);
     }
     if (warp == 1) {
-        tc::tmem_alloc(tmem_slot, BN);
+        tc::tmem_alloc(tmem_slot, ACC * BN);
         tc::tmem_relinquish();
     }
     tc::fence_before();
@@ -161,16 +201,18 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_kernel(const __grid
         for (int j = 0;; ++j) {
             const int r = j % RING;
             if (j >= RING && !tc::mbar_wait(&sempty[r], (uint32_t)((j / RING) - 1) & 1u, deadline)) *fail = 1;
-            const int tile = (*fail || next >= (uint32_t)n_tiles) ? -1 : (int)next;
-            ring[r] = tile;
+            const int unit = (*fail || next >= (uint32_t)n_units) ? -1 : (int)next;
+            ring[r] = unit;
             tc::mbar_arrive(&sfull[r]);  // release: the index is visible to the waiting roles
-            if (tile < 0) break;
+            if (unit < 0) break;
+            int tile, k0, k1, part, fix;
+            unit_of<SPLIT>(unit, sp, KT, tile, k0, k1, part, fix);
             int tmi, tni;
             tile_coords(tile, tiles_m, tiles_n, group_m, tmi, tni);
             const int m0 = tmi * BM, n0 = tni * BN;
-            for (int kt = 0; kt < KT; ++kt, ++g) {
+            for (int kt = k0; kt < k1; ++kt, ++g) {
                 const int s = (int)(g % STAGES);
-                if (kt == KT - 1) next = gridDim.x + atomicAdd(&tm->tile_next, 1u);
+                if (kt == k1 - 1) next = gridDim.x + atomicAdd(&tm->tile_next, 1u);
                 if (g >= STAGES && !tc::mbar_wait(&empty[s], (uint32_t)((g / STAGES) - 1) & 1u, deadline)) {
                     *fail = 1;
                     break;
@@ -190,17 +232,21 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_kernel(const __grid
         for (int j = 0;; ++j) {
             const int r = j % RING;
             const bool got = tc::mbar_wait(&sfull[r], (uint32_t)(j / RING) & 1u, deadline + 50000000ull);
-            const int tile = got ? ring[r] : -1;
+            const int unit = got ? ring[r] : -1;
             tc::mbar_arrive(&sempty[r]);
             if (!got) *fail = 1;
-            if (tile < 0) break;
-            if (j > 0 && !tc::mbar_wait(tempty, (uint32_t)((j - 1) & 1), deadline)) {
+            if (unit < 0) break;
+            int tile, k0, k1, part, fix;
+            unit_of<SPLIT>(unit, sp, KT, tile, k0, k1, part, fix);
+            const int a = j % ACC;  // accumulator of this unit
+            if (j >= ACC && !tc::mbar_wait(&tempty[a], (uint32_t)((j / ACC) - 1) & 1u, deadline)) {
                 *fail = 1;
-                tc::mma_commit(tfull);
+                tc::mma_commit(&tfull[a]);
                 continue;  // read the ring on to its end marker
             }
             tc::fence_after();
-            for (int kt = 0; kt < KT; ++kt, ++g) {
+            const uint32_t acc_cols = tmem + (uint32_t)(a * BN);
+            for (int kt = k0; kt < k1; ++kt, ++g) {
                 const int s = (int)(g % STAGES);
                 if (!tc::mbar_wait(&full[s], (uint32_t)(g / STAGES) & 1u, deadline)) {
                     *fail = 1;
@@ -212,35 +258,41 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_kernel(const __grid
                 const uint64_t bdesc = tc::desc_sw128(sa + Cf::A_BYTES);
 #pragma unroll
                 for (int kk = 0; kk < BK / 16; ++kk)
-                    tc::mma_bf16(tmem, adesc + 2ull * kk, bdesc + 2ull * kk, idesc, (uint32_t)((kt | kk) != 0));
+                    tc::mma_bf16(acc_cols, adesc + 2ull * kk, bdesc + 2ull * kk, idesc,
+                                 (uint32_t)((kt != k0) | (kk != 0)));
                 tc::mma_commit(&empty[s]);
             }
-            tc::mma_commit(tfull);  // also on failure, so the epilogue's wait completes
+            tc::mma_commit(&tfull[a]);  // also on failure, so the epilogue's wait completes
         }
     } else if (warp >= 2) {
         const int q = warp & 3;  // TMEM lane quadrant this warp may access
-        const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
         for (int j = 0;; ++j) {
             const int r = j % RING;
             const bool got = tc::mbar_wait(&sfull[r], (uint32_t)(j / RING) & 1u, deadline + 50000000ull);
-            const int tile = got ? ring[r] : -1;
+            const int unit = got ? ring[r] : -1;
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&sempty[r]);
             if (!__all_sync(0xffffffffu, got)) {
                 if (lane == 0) *fail = 1;
                 break;
             }
-            if (tile < 0) break;
-            const bool ok = tc::mbar_wait(tfull, (uint32_t)(j & 1), deadline + 100000000ull);
+            if (unit < 0) break;
+            const int a = j % ACC;
+            const bool ok = tc::mbar_wait(&tfull[a], (uint32_t)(j / ACC) & 1u, deadline + 100000000ull);
             tc::fence_after();
             if (!__all_sync(0xffffffffu, ok && !*fail)) {
                 if (lane == 0) *fail = 1;
                 break;
             }
+            int tile, k0, k1, part, fix;
+            unit_of<SPLIT>(unit, sp, KT, tile, k0, k1, part, fix);
+            const uint32_t trow = tmem + (uint32_t)(a * BN) + ((uint32_t)(q * 32) << 16);
             int tmi, tni;
             tile_coords(tile, tiles_m, tiles_n, group_m, tmi, tni);
             const int m0 = tmi * BM, n0 = tni * BN;
-            float *crow = C + (size_t)(m0 + q * 32 + lane) * (size_t)N + n0;
+            // a whole tile's rows go to C; a part's rows go to its slot of the workspace
+            float *crow = (!SPLIT || fix < 0) ? C + (size_t)(m0 + q * 32 + lane) * (size_t)N + n0
+                                  : sp.ws + ((size_t)(fix * sp.parts + part) * BM + (size_t)(q * 32 + lane)) * BN;
             uint32_t ra[16], rb[16];
             tc::tmem_ld16(trow, ra);
             tc::tmem_ld_wait();
@@ -256,18 +308,69 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_kernel(const __grid
                 } else {
                     tc::fence_before();
                     __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(tempty);  // accumulator drained: the next tile may start
+                    if (lane == 0) tc::mbar_arrive(&tempty[a]);  // accumulator drained: a later unit may use it
                     store_row16(crow + (c + 1) * 16, rb);
                 }
             }
-            if (warp == 2 && lane == 0) g_stamp(tm, false);  // victim progress, one stamp per tile
+            if (SPLIT && fix >= 0) {
+                // this part's rows are in its slot: count it; the last part of the
+                // (tile, warp) adds every slot in part order and stores C
+                __threadfence();
+                __syncwarp();
+                uint32_t prev = 0;
+                if (lane == 0) prev = atomicAdd(&sp.cnt[fix * EPI_WARPS + q], 1u);
+                prev = __shfl_sync(0xffffffffu, prev, 0);
+                if ((prev + 1u) % (uint32_t)sp.parts == 0u) {
+                    // coalesced: the warp walks its 32 rows four at a time, lanes across
+                    // the columns (BN / 128 float4 per lane per row), every load of the
+                    // four rows of all parts in flight together
+                    __threadfence();
+                    constexpr int H = BN / 128;
+                    const float *slot0 = sp.ws + ((size_t)fix * sp.parts * BM + (size_t)(q * 32)) * BN;
+                    float *cq = C + (size_t)(m0 + q * 32) * (size_t)N + n0;
+#pragma unroll 1
+                    for (int r0 = 0; r0 < 32; r0 += 4) {
+                        float4 t[4][H];
+#pragma unroll
+                        for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+                            for (int h = 0; h < H; ++h)
+                                t[rr][h] = __ldcg((const float4 *)(slot0 + (size_t)(r0 + rr) * BN) + lane + 32 * h);
+#pragma unroll 1
+                        for (int pp = 1; pp < sp.parts; ++pp) {
+                            const float *sl = slot0 + (size_t)pp * BM * BN;
+                            float4 u[4][H];
+#pragma unroll
+                            for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+                                for (int h = 0; h < H; ++h)
+                                    u[rr][h] = __ldcg((const float4 *)(sl + (size_t)(r0 + rr) * BN) + lane + 32 * h);
+#pragma unroll
+                            for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+                                for (int h = 0; h < H; ++h) {
+                                    t[rr][h].x += u[rr][h].x;
+                                    t[rr][h].y += u[rr][h].y;
+                                    t[rr][h].z += u[rr][h].z;
+                                    t[rr][h].w += u[rr][h].w;
+                                }
+                        }
+#pragma unroll
+                        for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+                            for (int h = 0; h < H; ++h)
+                                ((float4 *)(cq + (size_t)(r0 + rr) * N))[lane + 32 * h] = t[rr][h];
+                    }
+                }
+            }
+            if (warp == 2 && lane == 0) g_stamp(tm, false);  // victim progress, one stamp per unit
         }
     }
     tc::fence_before();
     __syncthreads();
     if (warp == 1) {
         tc::fence_after();
-        tc::tmem_dealloc(tmem, BN);
+        tc::tmem_dealloc(tmem, ACC * BN);
     }
     if (threadIdx.x == 0 && *fail) tm->status = IFR_ERR_TIMEOUT;
     g_exit(tm);
@@ -536,30 +639,94 @@ int make_map(CUtensorMap *m, const void *ptr, int64_t rows, int64_t K, int box_r
     return r == CUDA_SUCCESS ? IFR_OK : IFR_ERR_ARG;
 }
 
-template <int BN, int ST>
+// Variant 3 (two accumulators) is the one compiled with the split last wave.
+template <int BN, int ST, int ACC>
 const void *gemm_fn() {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(gemm_bf16_kernel<BN, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(gemm_bf16_kernel<BN, ST, ACC, ACC == 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              GemmCfg<BN, ST>::SMEM);
         attr = true;
     }
-    return (const void *)gemm_bf16_kernel<BN, ST>;
+    return (const void *)gemm_bf16_kernel<BN, ST, ACC, ACC == 2>;
 }
 
-template <int BN, int ST>
-int launch_gemm(const ifr_victim_cfg *c, cudaStream_t stream, int group_m, DevTiming *tm) {
-    gemm_fn<BN, ST>();
+// The split of a variant-3 launch over `ctas` persistent CTAs: the tiles left over
+// after the full waves (R = tiles mod ctas) become `parts` K ranges each when that
+// fills the last wave better: parts = min(4, ctas / R, K / 2048), at least 2.  Each
+// part then runs at least 32 K slices, enough to repay its partial tile's store and
+// the reduction (measured: 2- and 4-part splits of 8 or fewer slices each made K = 512
+// and K = 1024 launches slower than no split).
+constexpr int kMinSlicesPerPart = 32;
+GemmSplit split_for(int tiles, int ctas, int KT) {
+    GemmSplit sp;
+    memset(&sp, 0, sizeof sp);
+    sp.parts = 1;
+    const int R = tiles % ctas;
+    if (R == 0) return sp;
+    int parts = ctas / R;
+    if (parts > 4) parts = 4;
+    if (parts > KT / kMinSlicesPerPart) parts = KT / kMinSlicesPerPart;
+    if (parts < 2) return sp;
+    sp.full = tiles - R;
+    sp.parts = parts;
+    return sp;
+}
+
+// Workspace and counters of a split launch, owned by the context; the counters are
+// zeroed when allocated, when the split changes and after a failed launch.
+int ensure_split(ifr_ctx *ctx, GemmSplit &sp, int tiles, int BN, cudaStream_t stream) {
+    if (sp.parts <= 1) return IFR_OK;
+    const int R = tiles - sp.full;
+    const size_t ws = (size_t)R * sp.parts * BM * BN * sizeof(float);
+    const size_t nc = (size_t)R * EPI_WARPS;
+    if (ws > ctx->gemm_ws_bytes) {
+        if (ctx->gemm_ws) cudaFree(ctx->gemm_ws);
+        ctx->gemm_ws = nullptr;
+        ctx->gemm_ws_bytes = 0;
+        IFR_CUDA(cudaMalloc((void **)&ctx->gemm_ws, ws));
+        ctx->gemm_ws_bytes = ws;
+    }
+    if (nc > ctx->gemm_cnt_n) {
+        if (ctx->gemm_cnt) cudaFree(ctx->gemm_cnt);
+        ctx->gemm_cnt = nullptr;
+        ctx->gemm_cnt_n = 0;
+        IFR_CUDA(cudaMalloc((void **)&ctx->gemm_cnt, nc * sizeof(uint32_t)));
+        ctx->gemm_cnt_n = nc;
+        ctx->gemm_cnt_key = -1;
+    }
+    const int64_t key = (int64_t)R * 8 + sp.parts;
+    if (key != ctx->gemm_cnt_key) {
+        IFR_CUDA(cudaMemsetAsync(ctx->gemm_cnt, 0, ctx->gemm_cnt_n * sizeof(uint32_t), stream));
+        ctx->gemm_cnt_key = key;
+    }
+    sp.ws = ctx->gemm_ws;
+    sp.cnt = ctx->gemm_cnt;
+    return IFR_OK;
+}
+
+template <int BN, int ST, int ACC>
+int launch_gemm(ifr_ctx *ctx, const ifr_victim_cfg *c, cudaStream_t stream, int group_m, bool split, DevTiming *tm) {
+    gemm_fn<BN, ST, ACC>();
     CUtensorMap ta, tb;
     int rc = make_map(&ta, c->in0, c->m, c->k, BM);
     if (rc) return rc;
     rc = make_map(&tb, c->in1, c->n, c->k, BN);
     if (rc) return rc;
-    ifr_carveout((const void *)gemm_bf16_kernel<BN, ST>);
+    ifr_carveout(gemm_fn<BN, ST, ACC>());
     const int tiles = (int)((c->n / BN) * (c->m / BM));
-    const int grid = tiles < g_num_sms ? tiles : g_num_sms;
-    gemm_bf16_kernel<BN, ST><<<grid, GEMM_THREADS, GemmCfg<BN, ST>::SMEM, stream>>>(
-        ta, tb, (float *)c->out, (int)c->m, (int)c->n, (int)c->k, group_m, tm);
+    GemmSplit sp;
+    memset(&sp, 0, sizeof sp);
+    sp.parts = 1;
+    if (split) {
+        sp = split_for(tiles, g_num_sms, (int)(c->k / BK));
+        rc = ensure_split(ctx, sp, tiles, BN, stream);
+        if (rc) return rc;
+    }
+    const int units = sp.parts > 1 ? sp.full + (tiles - sp.full) * sp.parts : tiles;
+    const int grid = units < g_num_sms ? units : g_num_sms;
+    gemm_bf16_kernel<BN, ST, ACC, ACC == 2><<<grid, GEMM_THREADS, GemmCfg<BN, ST>::SMEM, stream>>>(
+        ta, tb, (float *)c->out, (int)c->m, (int)c->n, (int)c->k, group_m, sp, tm);
     return IFR_OK;
 }
 
@@ -637,28 +804,36 @@ int launch_gemm_pair(const ifr_victim_cfg *c, cudaStream_t stream, int group_m, 
 
 int ifr_gemm_shape(const ifr_victim_cfg *c, VictimShape *s) {
     if (g_num_sms == 0) cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, 0);
+    s->flops = 2.0 * (double)c->m * (double)c->n * (double)c->k;
+    s->bytes = 2.0 * ((double)c->m + (double)c->n) * (double)c->k + 4.0 * (double)c->m * (double)c->n;
+    s->uses_tensor = 1;
+    s->block = GEMM_THREADS;
     if (c->variant == 2) {
         s->fn = gemm_pair_fn<4>();
         s->grid = pair_grid<4>(c);
-        s->block = GEMM_THREADS;
         s->smem = PairCfg<4>::SMEM;
         s->tmem_cols = PAIR_N;
-        s->uses_tensor = 1;
-        s->flops = 2.0 * (double)c->m * (double)c->n * (double)c->k;
-        s->bytes = 2.0 * ((double)c->m + (double)c->n) * (double)c->k + 4.0 * (double)c->m * (double)c->n;
         return IFR_OK;
     }
-    const bool wide = c->n % 256 == 0, deep = c->variant == 1;
-    s->fn = wide ? (deep ? gemm_fn<256, 4>() : gemm_fn<256, 3>()) : (deep ? gemm_fn<128, 4>() : gemm_fn<128, 3>());
-    const int tiles = (int)((c->n / (wide ? 256 : 128)) * (c->m / BM));
+    const bool wide = c->n % 256 == 0;
+    const int BN = wide ? 256 : 128;
+    const int tiles = (int)((c->n / BN) * (c->m / BM));
+    if (c->variant == 3) {
+        s->fn = wide ? gemm_fn<256, 4, 2>() : gemm_fn<128, 4, 2>();
+        const GemmSplit sp = split_for(tiles, g_num_sms, (int)(c->k / BK));
+        const int units = sp.parts > 1 ? sp.full + (tiles - sp.full) * sp.parts : tiles;
+        s->grid = units < g_num_sms ? units : g_num_sms;
+        s->smem = wide ? GemmCfg<256, 4>::SMEM : GemmCfg<128, 4>::SMEM;
+        s->tmem_cols = 2 * BN;
+        return IFR_OK;
+    }
+    const bool deep = c->variant == 1;
+    s->fn = wide ? (deep ? gemm_fn<256, 4, 1>() : gemm_fn<256, 3, 1>())
+                 : (deep ? gemm_fn<128, 4, 1>() : gemm_fn<128, 3, 1>());
     s->grid = tiles < g_num_sms ? tiles : g_num_sms;
-    s->block = GEMM_THREADS;
     s->smem = wide ? (deep ? GemmCfg<256, 4>::SMEM : GemmCfg<256, 3>::SMEM)
                    : (deep ? GemmCfg<128, 4>::SMEM : GemmCfg<128, 3>::SMEM);
-    s->tmem_cols = wide ? 256 : 128;
-    s->uses_tensor = 1;
-    s->flops = 2.0 * (double)c->m * (double)c->n * (double)c->k;
-    s->bytes = 2.0 * ((double)c->m + (double)c->n) * (double)c->k + 4.0 * (double)c->m * (double)c->n;
+    s->tmem_cols = BN;
     return IFR_OK;
 }
 
@@ -668,14 +843,25 @@ int ifr_gemm_enqueue(ifr_ctx *ctx, const ifr_victim_cfg *c, cudaStream_t stream,
     const double operand_bytes = 2.0 * ((double)c->m + (double)c->n) * (double)c->k;
     const int gm = operand_bytes > (double)ctx->info.l2_bytes ? GROUP_M : 1;
     if (c->variant == 2) return launch_gemm_pair<4>(c, stream, gm, tm);
+    const bool wide = c->n % 256 == 0;
+    if (c->variant == 3)
+        return wide ? launch_gemm<256, 4, 2>(ctx, c, stream, gm, true, tm)
+                    : launch_gemm<128, 4, 2>(ctx, c, stream, gm, true, tm);
     const bool deep = c->variant == 1;
-    if (c->n % 256 == 0) return deep ? launch_gemm<256, 4>(c, stream, gm, tm) : launch_gemm<256, 3>(c, stream, gm, tm);
-    return deep ? launch_gemm<128, 4>(c, stream, gm, tm) : launch_gemm<128, 3>(c, stream, gm, tm);
+    if (wide)
+        return deep ? launch_gemm<256, 4, 1>(ctx, c, stream, gm, false, tm)
+                    : launch_gemm<256, 3, 1>(ctx, c, stream, gm, false, tm);
+    return deep ? launch_gemm<128, 4, 1>(ctx, c, stream, gm, false, tm)
+                : launch_gemm<128, 3, 1>(ctx, c, stream, gm, false, tm);
 }
 
+// After a launch that failed part-way the split counters may be off by a few
+// arrivals: the next split launch starts from zero.
+void ifr_gemm_forget_split(ifr_ctx *ctx) { ctx->gemm_cnt_key = -1; }
+
 int ifr_preload_gemm() {
-    const void *fns[] = {gemm_fn<128, 3>(), gemm_fn<256, 3>(), gemm_fn<128, 4>(), gemm_fn<256, 4>(),
-                         gemm_pair_fn<4>()};
+    const void *fns[] = {gemm_fn<128, 3, 1>(), gemm_fn<256, 3, 1>(), gemm_fn<128, 4, 1>(), gemm_fn<256, 4, 1>(),
+                         gemm_fn<128, 4, 2>(), gemm_fn<256, 4, 2>(), gemm_pair_fn<4>()};
     for (const void *f : fns) {
         int rc = ifr_preload(f);
         if (rc) return rc;

@@ -93,6 +93,7 @@ struct StressParams {
     float duty_inv_period; // 1 / period_ns
     const int4 *buf;      // L2/HBM
     int64_t n_chunks;     // L2/HBM chunks (chunk = blockDim * 4 int4)
+    int32_t ring;         // L2/HBM with TMA staging: shared-memory ring stages
     int32_t ilp;          // FMA
     float fma_a, fma_b;   // FMA multiplier and addend (launch-wide)
     double fp64_a;        // FP64 multiplier (launch-wide)
@@ -138,6 +139,12 @@ struct ifr_ctx {
     int part_sms_v, part_sms_s;
     void *green_v, *green_s;   // CUgreenCtx
     cudaStream_t own_victim, own_stress;
+    // GEMM variant 3: partial tiles of a split last wave and their arrival counters
+    float *gemm_ws;
+    size_t gemm_ws_bytes;
+    uint32_t *gemm_cnt;
+    size_t gemm_cnt_n;
+    int64_t gemm_cnt_key;  // split the counters were zeroed for (-1: zero before the next use)
 };
 
 // Prefer the maximum shared-memory carveout for every kernel of the library so
@@ -195,3 +202,4 @@ int ifr_victim_shape(ifr_ctx *ctx, const ifr_victim_cfg *cfg, VictimShape *s);
 // GEMM (ifr_gemm.cu)
 int ifr_gemm_enqueue(ifr_ctx *ctx, const ifr_victim_cfg *cfg, cudaStream_t stream, DevTiming *tm);
 int ifr_gemm_shape(const ifr_victim_cfg *cfg, VictimShape *s);
+void ifr_gemm_forget_split(ifr_ctx *ctx);

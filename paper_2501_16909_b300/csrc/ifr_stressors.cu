@@ -216,6 +216,9 @@ __device__ __forceinline__ int4 ld_stream(const int4 *p) {
     return v;
 }
 
+// Every chunk is read whole with 16-byte loads; the fold takes the first word of
+// each load, so every load enters the checksum (a load whose result nothing used
+// would be dropped by the compiler) at a quarter of the XORs of a full fold.
 __global__ void __launch_bounds__(1024) stream_stress_kernel(DevStress *st, StressParams p) {
     __shared__ int s_k;
     __shared__ uint64_t s_t0;
@@ -249,13 +252,120 @@ __global__ void __launch_bounds__(1024) stream_stress_kernel(DevStress *st, Stre
             }
         }
 #pragma unroll
-        for (int r = 0; r < kStreamChunksPerRound; ++r) {
-            uint32_t x = 0u;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) x ^= (uint32_t)(v[r][u].x ^ v[r][u].y ^ v[r][u].z ^ v[r][u].w);
-            acc ^= ifr_rotl(x, (uint32_t)ps[r]);
+        for (int r = 0; r < kStreamChunksPerRound; ++r)
+            acc ^= ifr_rotl((uint32_t)(v[r][0].x ^ v[r][1].x ^ v[r][2].x ^ v[r][3].x), (uint32_t)ps[r]);
+        done += kStreamChunksPerRound;
+    }
+    uint32_t cs = ifr_block_xor(acc, s_red);
+    if (threadIdx.x == 0) write_log(p, st, c, round, (uint64_t)done, cs, 0u);
+}
+
+// The same stressor with TMA staging: a ring of p.ring stages of one chunk each in
+// shared memory.  Thread 0 keeps the ring filled with whole-chunk bulk copies
+// (cp.async.bulk, global -> this CTA's shared memory, completion counted in bytes
+// on the stage's mbarrier) and waits for each chunk to land; one block barrier per
+// chunk then lets every thread fold its 16 bytes of the chunk's quarter (pass & 3)
+// from shared memory and tells thread 0 that the previous chunk's stage is free to
+// refill.  The load/store unit carries only those 16-byte shared-memory reads and
+// only thread 0 polls.  Every wait is bounded; a block drains the copies it issued
+// before it exits, so no copy lands in shared memory that another block may own.
+constexpr int kTmaMaxStages = 6;
+
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            tc::smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(tc::smem_u32(bar))
+        : "memory");
+}
+
+__global__ void __launch_bounds__(1024) stream_stress_tma_kernel(DevStress *st, StressParams p) {
+    extern __shared__ __align__(128) uint8_t s_ring[];
+    __shared__ __align__(8) uint64_t s_full[kTmaMaxStages];
+    __shared__ int s_k;
+    __shared__ uint64_t s_t0;
+    __shared__ int s_go[2];
+    __shared__ int s_fail;
+    __shared__ uint32_t s_red[32];
+    BlockCtl c;
+    if (!block_enter(st, p, c, &s_k, &s_t0)) return;
+    const int64_t A = p.planned, k = c.k;
+    const int S = p.ring;
+    const uint32_t chunk_bytes = blockDim.x * 64u;
+    const bool has_work = k < p.n_chunks;
+    const uint64_t wait_limit = c.deadline + 100000000ull;  // a copy gets 100 ms past the deadline
+    int64_t ipos = k, issued = 0, landed = 0;  // thread 0: next chunk to copy, copies issued, seen landed
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) tc::mbar_init(&s_full[s], 1);
+        s_fail = 0;
+        tc::fence_mbar_init();
+        if (has_work) {
+            for (int s = 0; s < S; ++s, ++issued) {
+                tc::mbar_arrive_expect_tx(&s_full[s], chunk_bytes);
+                bulk_copy_g2s(s_ring + (size_t)s * chunk_bytes, (const uint8_t *)p.buf + ipos * chunk_bytes,
+                              chunk_bytes, &s_full[s]);
+                ipos += A;
+                if (ipos >= p.n_chunks) ipos = k;
+            }
+        }
+    }
+    __syncthreads();
+    int64_t cpos = k, pass = 0, done = 0, j = 0;
+    int s = 0, sp = S - 1;  // stage of chunk j and of chunk j - 1
+    uint32_t par = 0u;      // phase parity of chunk j's stage
+    uint32_t acc = 0u;
+    int64_t round = 0;
+    for (;; ++round) {
+        if (threadIdx.x == 0) s_go[round & 1] = (has_work && !s_fail) ? round_decision(st, p, round, c) : 0;
+        __syncthreads();
+        if (!s_go[round & 1]) break;
+#pragma unroll 1
+        for (int r = 0; r < kStreamChunksPerRound; ++r, ++j) {
+            if (threadIdx.x == 0 && !s_fail) {
+                if (tc::mbar_wait(&s_full[s], par, wait_limit))
+                    landed = j + 1;
+                else
+                    s_fail = 1;
+            }
+            // chunk j has landed, and every thread has finished with chunk j - 1
+            __syncthreads();
+            if (threadIdx.x == 0 && j > 0 && !s_fail) {
+                // refill the stage of chunk j - 1 with the chunk S reads ahead of it
+                tc::mbar_arrive_expect_tx(&s_full[sp], chunk_bytes);
+                bulk_copy_g2s(s_ring + (size_t)sp * chunk_bytes, (const uint8_t *)p.buf + ipos * chunk_bytes,
+                              chunk_bytes, &s_full[sp]);
+                ipos += A;
+                if (ipos >= p.n_chunks) ipos = k;
+                ++issued;
+            }
+            if (!s_fail) {
+                const int4 *q = (const int4 *)(s_ring + (size_t)s * chunk_bytes) + (int)(pass & 3) * (int)blockDim.x +
+                                (int)threadIdx.x;
+                int4 v;
+                asm volatile("ld.shared.v4.s32 {%0,%1,%2,%3}, [%4];"
+                             : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                             : "r"(tc::smem_u32(q))
+                             : "memory");
+                acc ^= ifr_rotl((uint32_t)(v.x ^ v.y ^ v.z ^ v.w), (uint32_t)pass);
+            }
+            cpos += A;
+            if (cpos >= p.n_chunks) {
+                cpos = k;
+                ++pass;
+            }
+            sp = s;
+            if (++s == S) {
+                s = 0;
+                par ^= 1u;
+            }
         }
         done += kStreamChunksPerRound;
+    }
+    // drain: every copy this block issued has landed before it exits
+    if (threadIdx.x == 0) {
+        for (int64_t q = landed; q < issued; ++q)
+            if (!tc::mbar_wait(&s_full[q % S], (uint32_t)(q / S) & 1u, wait_limit)) s_fail = 1;
+        if (s_fail && c.status == 0) c.status = IFR_ERR_TIMEOUT;
     }
     uint32_t cs = ifr_block_xor(acc, s_red);
     if (threadIdx.x == 0) write_log(p, st, c, round, (uint64_t)done, cs, 0u);
@@ -702,6 +812,24 @@ const void *smem_kernel_for(int ways) {
     }
 }
 
+// Ring stages of the TMA-staged stream kernel: about 96 KiB of chunks per block
+// (2 to kTmaMaxStages stages of block x 64 bytes), so two blocks of 512 threads fit
+// on an SM with three stages each.
+int tma_ring_stages(int block) {
+    int n = (96 * 1024) / (block * 64);
+    return n < 2 ? 2 : (n > kTmaMaxStages ? kTmaMaxStages : n);
+}
+
+const void *stream_tma_fn() {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(stream_stress_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             2 * 1024 * 64);
+        attr = true;
+    }
+    return (const void *)stream_stress_tma_kernel;
+}
+
 // Kernel, block, dynamic shared memory and grid of a persistent stressor launch.
 struct StressShape {
     const void *fn;
@@ -717,7 +845,14 @@ StressShape stressor_shape(int num_sms, const ifr_stressor_cfg *cfg) {
     const int ilp = cfg->ilp ? cfg->ilp : 4;
     switch (kind) {
         case IFR_S_L2:
-        case IFR_S_HBM: s.fn = (const void *)stream_stress_kernel; break;
+        case IFR_S_HBM:
+            if (cfg->staging == 1) {
+                s.fn = stream_tma_fn();
+                s.smem = tma_ring_stages(s.block) * s.block * 64;
+            } else {
+                s.fn = (const void *)stream_stress_kernel;
+            }
+            break;
         case IFR_S_FMA:
             s.fn = ilp == 1 ? (const void *)fma_stress_kernel<1>
                  : ilp == 2 ? (const void *)fma_stress_kernel<2>
@@ -810,6 +945,7 @@ static int validate_cfg(ifr_ctx *ctx, const ifr_stressor_cfg *c) {
         int blk = c->block ? c->block : kind_default_block(c->kind);
         if (blk > 512) return IFR_ERR_ARG;  // 4 KiB per warp, at most 64 KiB per block
     }
+    if (c->staging != 0 && (c->staging != 1 || (c->kind != IFR_S_L2 && c->kind != IFR_S_HBM))) return IFR_ERR_ARG;
     if (c->kind == IFR_S_L2 || c->kind == IFR_S_HBM) {
         int blk = c->block ? c->block : kind_default_block(c->kind);
         int64_t chunk = (int64_t)blk * 64;
@@ -907,7 +1043,11 @@ int ifr_stressor_enqueue(ifr_ctx *ctx, const ifr_stressor_cfg *cfg, cudaStream_t
         case IFR_S_HBM:
             p.buf = (const int4 *)cfg->buf;
             p.n_chunks = cfg->working_set_bytes / ((int64_t)block * 64);
-            stream_stress_kernel<<<grid, blk, 0, stream>>>(s.d_state, p);
+            p.ring = tma_ring_stages(block);
+            if (cfg->staging == 1)
+                stream_stress_tma_kernel<<<grid, blk, sh, stream>>>(s.d_state, p);
+            else
+                stream_stress_kernel<<<grid, blk, 0, stream>>>(s.d_state, p);
             break;
         case IFR_S_FMA:
             switch (p.ilp) {
@@ -1208,7 +1348,7 @@ extern "C" int ifr_stream_stressor_noalloc(int kind, const void *buf, int64_t wo
 
 int ifr_preload_stressors() {
     const void *fns[] = {
-        (const void *)stress_reset_kernel, (const void *)stream_stress_kernel,
+        (const void *)stress_reset_kernel, (const void *)stream_stress_kernel, stream_tma_fn(),
         (const void *)fma_stress_kernel<1>, (const void *)fma_stress_kernel<2>, (const void *)fma_stress_kernel<4>,
         (const void *)fma_stress_kernel<8>, (const void *)fp64_stress_kernel<1>, (const void *)fp64_stress_kernel<2>,
         (const void *)fp64_stress_kernel<4>, (const void *)fp64_stress_kernel<8>, smem_kernel_for(1),

@@ -180,11 +180,12 @@ double per_launch_ratio(const ifr_timing &co, const ifr_timing &solo) {
     return (((double)co.t_end_ns - (double)co.t_start_ns) / kc) / (((double)solo.t_end_ns - (double)solo.t_start_ns) / ks);
 }
 
-// The CTA-pair GEMM (variant 2) allocates the same TMEM columns on two SMs at once;
-// beside other TMEM users (the tensor stressor, another pair) that allocation can
-// wait until they exit, so the measurements that colocate kernels refuse it.
+// The CTA-pair GEMM (variant 2) allocates the same TMEM columns on two SMs at once,
+// and the two-accumulator GEMM (variant 3) all 512 columns of an SM; beside other
+// TMEM users (the tensor stressor, another GEMM) those allocations can wait until
+// they exit, so the measurements that colocate kernels refuse both.
 int colocatable(const ifr_victim_cfg *c) {
-    return (c->kind == IFR_V_GEMM && c->variant == 2) ? IFR_ERR_ARG : IFR_OK;
+    return (c->kind == IFR_V_GEMM && (c->variant == 2 || c->variant == 3)) ? IFR_ERR_ARG : IFR_OK;
 }
 
 }  // namespace

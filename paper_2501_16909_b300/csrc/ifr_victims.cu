@@ -497,7 +497,7 @@ void ifr_timing_to_host(const DevTiming &d, int repeats, ifr_timing *out) {
 int ifr_victim_validate(ifr_ctx *ctx, const ifr_victim_cfg *c) {
     if (!c || c->kind < 0 || c->kind >= IFR_V_COUNT || c->repeats < 0 || c->grid < 0 || c->block < 0) return IFR_ERR_ARG;
     if (!c->in0 || !c->out) return IFR_ERR_ARG;
-    if (c->variant < 0 || c->variant > 2 || (c->kind != IFR_V_GEMM && c->variant != 0)) return IFR_ERR_ARG;
+    if (c->variant < 0 || c->variant > 3 || (c->kind != IFR_V_GEMM && c->variant != 0)) return IFR_ERR_ARG;
     switch (c->kind) {
         case IFR_V_TRIAD:
             if (!c->in1 || c->n <= 0 || !aligned16(c->in0) || !aligned16(c->in1) || !aligned16(c->out)) return IFR_ERR_ARG;
@@ -692,9 +692,10 @@ extern "C" int ifr_victim_launch(ifr_ctx *ctx, const ifr_victim_cfg *cfg, void *
     if (rc != IFR_OK) return rc;
     IFR_CUDA(cudaEventRecord(ctx->ev_b, st));
     IFR_CUDA(cudaEventSynchronize(ctx->ev_b));
+    DevTiming h;
+    IFR_CUDA(cudaMemcpy(&h, tm, sizeof h, cudaMemcpyDeviceToHost));
+    if (h.status != IFR_OK && cfg->kind == IFR_V_GEMM) ifr_gemm_forget_split(ctx);
     if (out) {
-        DevTiming h;
-        IFR_CUDA(cudaMemcpy(&h, tm, sizeof h, cudaMemcpyDeviceToHost));
         ifr_timing_to_host(h, cfg->repeats > 0 ? cfg->repeats : 1, out);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ctx->ev_a, ctx->ev_b);

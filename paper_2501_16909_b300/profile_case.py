@@ -6,14 +6,16 @@ one kernel kind in isolation on a small case so that a profiler can capture it:
 
     python -m paper_2501_16909_b300.profile_case <case> [--repeat N]
 
-cases: hbm, l2, fma, tensor, smem_cf, smem_32w, sched, fp64, sleep, gemm (--variant),
+cases: hbm, l2 (--staging), fma, tensor, smem_cf, smem_32w, sched, fp64, sleep, gemm (--variant),
 gemv, layernorm, softmax, hist, triad; gemm_variants, the solo throughput of every GEMM
 variant at four shapes; config5_kernels, one launch of each configuration-5
 decoder-layer kernel in order; and victim_bandwidth, which times every memory-bound
 configuration-2 victim alone over grids of 0 (default), 1, 2, 4, 8 and 16 blocks per
 SM (20 launches after a warm measurement) and prints one JSON line per run; and
 l2_set_sweep, which times the stream kernel on every SM (256 rounds per block) over
-sets of 8..96 MiB for 2 x 512, 4 x 512 and 2 x 256 threads per SM.  Inputs are the workloads' seeded inputs at the sizes
+sets of 8..96 MiB for 2 x 512, 4 x 512 and 2 x 256 threads per SM; and stream_staging,
+which times the HBM (4 GiB) and L2 (16 MiB) stressors with vector loads and with TMA
+bulk copies over four block shapes.  Inputs are the workloads' seeded inputs at the sizes
 given below (the stream stressors use a 1 GiB / 48 MiB set; the victims use their
 full configuration-2 shapes).
 """
@@ -44,6 +46,11 @@ def main(argv=None):
     ap.add_argument("--sm-fraction", type=float, default=1.0)
     ap.add_argument("--variant", type=int, default=None,
                     help="GEMM variant (0, 1, 2 = CTA-pair tiles; default: the workload's)")
+    ap.add_argument("--block", type=int, default=None, help="stressors: threads per block")
+    ap.add_argument("--bps", type=int, default=None, help="stressors: blocks per SM")
+    ap.add_argument("--ilp", type=int, default=None, help="FMA / FP64 stressors: chains per thread")
+    ap.add_argument("--staging", type=int, default=0,
+                    help="L2 / HBM stressors: 0 = vector loads into registers, 1 = TMA bulk copies into shared memory")
     a = ap.parse_args(argv)
     ctx = ifr.Context(0)
     S = ctx.info["num_sms"]
@@ -62,6 +69,25 @@ def main(argv=None):
                 print(json.dumps({"mib": mib, "block": block, "blocks_per_sm": bps, "gbs": round(rate / 1e9, 1)}))
         ctx.close()
         return
+    if a.case == "stream_staging":
+        # the stream stressor with vector loads (staging 0) and with TMA bulk copies
+        # (staging 1) on every SM: HBM over a 4 GiB set (64 rounds per block) and L2 over
+        # the 16 MiB set (256 rounds), 2 or 4 blocks of 512 threads or 2 of 1024 per SM
+        sets = {"hbm": (A.IFR_S_HBM, I.torch_u32_as_i32(1, (4 << 30) // 4, "cuda"), 64),
+                "l2": (A.IFR_S_L2, I.torch_u32_as_i32(3, W.L2_SET_BYTES // 4, "cuda"), 256)}
+        for name, (kind, buf, rounds) in sets.items():
+            for block, bps in ((512, 2), (512, 4), (1024, 2), (256, 4)):
+                for staging in (0, 1):
+                    if staging and bps * 3 * block * 64 > 200 * 1024:
+                        continue  # the ring would not fit beside the other blocks of the SM
+                    cfg = ifr.stressor_cfg(kind, sm_count=S, blocks_per_sm=bps, block=block, buf=buf,
+                                           working_set_bytes=buf.numel() * 4, staging=staging)
+                    P.solo_rate(ctx, cfg, rounds=rounds)
+                    rate, res = P.solo_rate(ctx, cfg, rounds=rounds)
+                    print(json.dumps({"set": name, "block": block, "blocks_per_sm": bps, "staging": staging,
+                                      "status": res["status"], "gbs": round(rate / 1e9, 1)}))
+        ctx.close()
+        return
     if a.case == "gemm_variants":
         # solo throughput of every GEMM variant at four shapes: 3 warm launches, then 20
         # launches timed with CUDA events on the victim stream
@@ -69,7 +95,7 @@ def main(argv=None):
             ga = I.torch_normal_bf16(1, M * K, "cuda").view(M, K)
             gb = I.torch_normal_bf16(2, N * K, "cuda").view(N, K)
             gc = torch.empty(M, N, device="cuda")
-            for var in (0, 1, 2):
+            for var in (0, 1, 2, 3):
                 cfg = ifr.victim_cfg(A.IFR_V_GEMM, ga, gb, gc, m=M, n=N, k=K, repeats=3, variant=var)
                 ctx.victim_launch(cfg)
                 cfg.repeats = 20
@@ -117,6 +143,11 @@ def main(argv=None):
         if kind == A.IFR_S_L2:
             bufs["l2"] = I.torch_u32_as_i32(3, W.L2_SET_BYTES // 4, "cuda")
         cfg = W.stressor_level_cfg(kind, n_sm, bufs, seed=1)
+        if kind in (A.IFR_S_L2, A.IFR_S_HBM):
+            cfg.staging = a.staging
+        for name, v in (("block", a.block), ("blocks_per_sm", a.bps), ("ilp", a.ilp)):
+            if v is not None:
+                setattr(cfg, name, v)
         for _ in range(a.repeat):
             rate, res = P.solo_rate(ctx, cfg)
         out.update(rate=rate, unit=P.UNIT[kind] + "/s", elapsed_ms=res["elapsed_ms"], work=res["work"],

@@ -22,11 +22,12 @@ def ctx():
     c.close()
 
 
-def _stream_check(ctx, kind, nbytes, block, bps, sm_count, rounds=0, stop_after_s=None, sample=None):
+def _stream_check(ctx, kind, nbytes, block, bps, sm_count, rounds=0, stop_after_s=None, sample=None, staging=0):
     n = nbytes // 4
     buf = I.torch_u32_as_i32(1, n, "cuda")
     cfg = ifr.stressor_cfg(kind, sm_count=sm_count, blocks_per_sm=bps, block=block, working_set_bytes=nbytes,
-                           buf=buf, max_rounds=rounds, seed=0)
+                           buf=buf, max_rounds=rounds, seed=0, staging=staging)
+    fold = oracle.FOLD_BULK if staging == 1 else oracle.FOLD_LOADS
     h = ctx.stressor_launch(cfg)
     if stop_after_s is not None:
         time.sleep(stop_after_s)
@@ -48,7 +49,7 @@ def _stream_check(ctx, kind, nbytes, block, bps, sm_count, rounds=0, stop_after_
     assert max(per_sm.values()) <= bps
     chk = logs if sample is None else logs[:sample]
     for L in chk:
-        want = oracle.stream_block_checksum(hbuf, chunk, planned, L["index"], L["work"])
+        want = oracle.stream_block_checksum(hbuf, chunk, planned, L["index"], L["work"], fold)
         assert L["checksum"] == want, L
         if rounds:
             n_chunks = n // chunk
@@ -61,30 +62,47 @@ def _stream_check(ctx, kind, nbytes, block, bps, sm_count, rounds=0, stop_after_
     return r, logs
 
 
-def test_hbm_stressor_fixed_rounds_all_sms(ctx):
+# staging 0: 16-byte loads into registers; 1: TMA bulk copies into a shared-memory ring
+@pytest.mark.parametrize("staging", [0, 1])
+def test_hbm_stressor_fixed_rounds_all_sms(ctx, staging):
     S = ctx.info["num_sms"]
-    _stream_check(ctx, A.IFR_S_HBM, 64 << 20, 512, 2, S, rounds=3)
+    _stream_check(ctx, A.IFR_S_HBM, 64 << 20, 512, 2, S, rounds=3, staging=staging)
 
 
-def test_l2_stressor_subset_ragged(ctx):
-    # 37 SMs, 1 block each, 256-thread blocks; the chunk count is not a multiple of the stride
-    _stream_check(ctx, A.IFR_S_L2, (16384 * 211), 256, 1, 37, rounds=5)
+@pytest.mark.parametrize("staging", [0, 1])
+def test_l2_stressor_subset_ragged(ctx, staging):
+    # 37 SMs, 1 block each, 256-thread blocks; the chunk count is not a multiple of the stride;
+    # 11 passes, so the bulk path folds every quarter
+    _stream_check(ctx, A.IFR_S_L2, (16384 * 211), 256, 1, 37, rounds=30, staging=staging)
 
 
-def test_stream_stressor_more_blocks_than_chunks(ctx):
+@pytest.mark.parametrize("staging", [0, 1])
+def test_stream_stressor_more_blocks_than_chunks(ctx, staging):
     S = ctx.info["num_sms"]
     # 40 chunks of 32 KiB for 2*S blocks: most blocks have no chunk and read nothing
-    r, logs = _stream_check(ctx, A.IFR_S_HBM, 40 * 32768, 512, 2, S, rounds=2)
+    r, logs = _stream_check(ctx, A.IFR_S_HBM, 40 * 32768, 512, 2, S, rounds=2, staging=staging)
     assert sum(1 for L in logs if L["work"] > 0) == 40
 
 
-def test_stream_stressor_stop_flag_arbitrary_counts(ctx):
+@pytest.mark.parametrize("staging", [0, 1])
+def test_stream_stressor_stop_flag_arbitrary_counts(ctx, staging):
     # stopped from the host after about 2 ms: every block's arbitrary chunk count is
     # checked against the oracle (a block that skipped work would show)
     S = ctx.info["num_sms"]
-    r, logs = _stream_check(ctx, A.IFR_S_HBM, 256 << 20, 512, 2, S, rounds=0, stop_after_s=0.002)
+    r, logs = _stream_check(ctx, A.IFR_S_HBM, 256 << 20, 512, 2, S, rounds=0, stop_after_s=0.002, staging=staging)
     assert r["work"] > 0 and all(L["status"] == 0 for L in logs)
     assert len(logs) == 2 * S and len({L["work"] for L in logs}) > 1
+
+
+def test_stream_stressor_staging_needs_a_stream_kind(ctx):
+    import ctypes as C
+
+    L = A.load()
+    h = C.c_int()
+    for cfg in (ifr.stressor_cfg(A.IFR_S_FMA, sm_count=1, staging=1),
+                ifr.stressor_cfg(A.IFR_S_HBM, sm_count=1, staging=2, block=512, working_set_bytes=1 << 20,
+                                 buf=torch.empty(1 << 18, dtype=torch.int32, device="cuda"))):
+        assert L.ifr_stressor_launch(ctx._h, C.byref(cfg), None, C.byref(h)) == A.IFR_ERR_ARG
 
 
 def test_stressor_deadline_returns_timeout_status(ctx):

@@ -31,11 +31,12 @@ def _gemm(ctx, M, N, K, seed=11, repeats=1, variant=0):
 
 # the last two shapes have more output tiles than SMs (160 tiles of 128 x 256, 192 of
 # 128 x 128), so most tiles are handed out by the device counter
-@pytest.mark.parametrize("variant", [0, 1])  # colocation-friendly (3 stages) / throughput (4)
+# variant 3 (two accumulators): K is too short for a split last wave at these shapes
+@pytest.mark.parametrize("variant", [0, 1, 3])  # colocation-friendly (3 stages) / throughput (4) / 2 accumulators
 @pytest.mark.parametrize("M,N,K", [(128, 128, 64), (128, 256, 128), (256, 384, 192), (384, 512, 1024),
                                    (2048, 2560, 128), (8192, 384, 64)])
-def test_gemm_small_all_entries(ctx, M, N, K, variant):
-    Ab, Bb, C, t = _gemm(ctx, M, N, K, variant=variant)
+def test_gemm_small_all_entries(ctx, M, N, K, variant, repeats=1):
+    Ab, Bb, C, t = _gemm(ctx, M, N, K, variant=variant, repeats=repeats)
     assert t["status"] == 0
     ref = Ab.double().cpu() @ Bb.double().cpu().T
     got = C.double().cpu()
@@ -54,7 +55,32 @@ def test_gemm_pair_tiles_all_entries(ctx, M, N, K):
     test_gemm_small_all_entries(ctx, M, N, K, 2)
 
 
-@pytest.mark.parametrize("variant", [0, 2])
+# variant 3 with split last waves (a part must run at least 32 K slices of 64): 72
+# tiles of 128 x 256 in 2 K parts (one wave of 144 units), 6 tiles in 4 parts, and
+# 320 tiles = 296 whole + 24 in 2 parts; three launches each, so the arrival counters
+# run over several launches, and the shapes alternate so the context re-zeroes them
+# when the split changes.  Small shapes: every entry against fp64; the large one:
+# entries of every 128 x 128 block against the oracle.
+@pytest.mark.parametrize("M,N,K", [(1152, 2048, 4096), (384, 512, 8192), (2560, 4096, 4096), (1152, 2048, 4096)])
+def test_gemm_two_accumulators_split_wave(ctx, M, N, K):
+    if M * N * K <= 1 << 34:
+        test_gemm_small_all_entries(ctx, M, N, K, 3, repeats=3)
+        return
+    Ab, Bb, C, t = _gemm(ctx, M, N, K, seed=31, repeats=3, variant=3)
+    assert t["status"] == 0 and torch.isfinite(C).all()
+    rng = np.random.default_rng(1)
+    ij = np.array([(bm * 128 + rng.integers(0, 128), bn * 128 + rng.integers(0, 128))
+                   for bm in range(M // 128) for bn in range(N // 128) for _ in range(2)], np.int64)
+    A_np = oracle.f32_bits_to_bf16_bits(I.np_normal_bf16(31, np.arange(M * K))).reshape(M, K)
+    B_np = oracle.f32_bits_to_bf16_bits(I.np_normal_bf16(32, np.arange(N * K))).reshape(N, K)
+    ref = oracle.gemm_entries(A_np, B_np, ij)
+    got = C.cpu().numpy()[ij[:, 0], ij[:, 1]].astype(np.float64)
+    rms = np.sqrt(np.mean(ref * ref))
+    assert np.all(np.abs(got - ref) <= BF16_TOL * np.maximum(np.abs(ref), rms))
+    assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("variant", [0, 2, 3])
 def test_gemm_full_size_sampled_vs_oracle(ctx, variant):
     M = N = K = 4096
     Ab, Bb, C, t = _gemm(ctx, M, N, K, seed=21, repeats=2, variant=variant)
@@ -78,12 +104,14 @@ def test_gemm_variant_profiles_and_bad_variant(ctx):
     p0 = ctx.victim_profile(ifr.victim_cfg(A.IFR_V_GEMM, Ab, Ab, C, m=256, n=256, k=256, variant=0))
     p1 = ctx.victim_profile(ifr.victim_cfg(A.IFR_V_GEMM, Ab, Ab, C, m=256, n=256, k=256, variant=1))
     p2 = ctx.victim_profile(ifr.victim_cfg(A.IFR_V_GEMM, Ab, Ab, C, m=256, n=256, k=256, variant=2))
+    p3 = ctx.victim_profile(ifr.victim_cfg(A.IFR_V_GEMM, Ab, Ab, C, m=256, n=256, k=256, variant=3))
+    assert p3["tmem_cols"] == 512 and p3["dynamic_smem"] == p1["dynamic_smem"]
     assert p1["dynamic_smem"] - p0["dynamic_smem"] == 128 * 64 * 2 + 256 * 64 * 2  # one more 48 KiB stage
     # pair tiles: four 32 KiB stages (each CTA's halves of A and B)
     assert p2["dynamic_smem"] == 4 * 2 * 128 * 64 * 2 + 1024 + 256 < p0["dynamic_smem"]
     assert p2["tmem_cols"] == 256 and p2["grid"] == 2
     assert max(p["regs_per_thread"] for p in (p0, p1, p2)) <= 96
-    for bad in (ifr.victim_cfg(A.IFR_V_GEMM, Ab, Ab, C, m=256, n=256, k=256, variant=3),
+    for bad in (ifr.victim_cfg(A.IFR_V_GEMM, Ab, Ab, C, m=256, n=256, k=256, variant=4),
                 ifr.victim_cfg(A.IFR_V_GEMM, Ab, Ab, C, m=128, n=256, k=256, variant=2),
                 ifr.victim_cfg(A.IFR_V_GEMM, Ab, Ab, C, m=256, n=384, k=256, variant=2),
                 ifr.victim_cfg(A.IFR_V_SOFTMAX, C, None, C, m=256, n=256, variant=1)):
@@ -91,11 +119,13 @@ def test_gemm_variant_profiles_and_bad_variant(ctx):
             ctx.victim_launch(bad)
 
 
-def test_pair_gemm_refused_where_kernels_are_colocated(ctx):
-    # the CTA pair's TMEM allocation can wait on other TMEM users: solo launches only
+@pytest.mark.parametrize("solo_variant", [2, 3])
+def test_pair_gemm_refused_where_kernels_are_colocated(ctx, solo_variant):
+    # the CTA pair's TMEM allocation, and the two-accumulator kernel's 512 columns, can
+    # wait on other TMEM users: solo launches only
     Ab = I.torch_normal_bf16(1, 256 * 256, "cuda").view(256, 256)
     C = torch.empty(256, 256, device="cuda")
-    pair = ifr.victim_cfg(A.IFR_V_GEMM, Ab, Ab, C, m=256, n=256, k=256, variant=2)
+    pair = ifr.victim_cfg(A.IFR_V_GEMM, Ab, Ab, C, m=256, n=256, k=256, variant=solo_variant)
     single = ifr.victim_cfg(A.IFR_V_GEMM, Ab, Ab, C, m=256, n=256, k=256, variant=0)
     fma = ifr.stressor_cfg(A.IFR_S_FMA, sm_count=1, block=128, max_rounds=1)
     for call in (lambda: ctx.sweep([pair], [], repeats=1), lambda: ctx.corun(pair, single),
