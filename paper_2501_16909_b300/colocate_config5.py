@@ -25,6 +25,9 @@ kernel pairs among the configuration-3 victims, then scores the configuration-5
 pairs it never saw; the baseline is the per-resource estimator
 1 + max_r S_v,r(x_c,r) over the victim's measured sensitivity curves (a stressor
 sweep of each configuration-5 kernel) and the co-runner's solo resource fractions.
+Both sides' features are measured (predictor module): a kernel's sensitivity is its
+slowdown beside each stressor kind at full intensity, a co-runner kernel's pressure
+the slowdown of six probe kernels beside it (ifr_corun).
 """
 from __future__ import annotations
 
@@ -164,87 +167,151 @@ def half_occupancy(cfg, num_sms):
     return c
 
 
-def features_of(ctx, cfgs, pk):
-    """Solo kernel features (per launch) of victim configurations."""
-    from paper_2501_16909_b300 import predictor as PR
-
-    S = ctx.info["num_sms"]
-    feats, solo = [], []
+def solo_facts(ctx, cfgs):
+    """Solo time per launch (ns) and SMs touched of every kernel configuration."""
+    ns, sms = [], []
     for c in cfgs:
         K = c.repeats
         c.repeats = 1
         tm = ctx.victim_launch(c)
         c.repeats = K
-        ns = float(tm["t_end_ns"] - tm["t_start_ns"])
-        solo.append(ns)
-        feats.append(PR.victim_features(ctx.victim_profile(c), ns, pk, S))
-    return np.array(feats), solo
+        ns.append(float(tm["t_end_ns"] - tm["t_start_ns"]))
+        sms.append(tm["sms_touched"])
+    return ns, sms
+
+
+def probe_pressure(ctx, kernels, probes):
+    """Slowdown of each probe kernel beside each kernel (ifr_corun, the kernel as the
+    co-runner chain); NaN where the probe could not run beside it."""
+    out = []
+    for c in kernels:
+        row = []
+        for p in probes:
+            r = ctx.corun(p, c)
+            row.append(r["victim_slowdown"] if r["valid"] else float("nan"))
+        out.append(row)
+    return out
+
+
+def full_sensitivity(ctx, cfgs, bufs):
+    """Slowdown of every kernel beside each stressor kind at full intensity."""
+    from paper_2501_16909_b300 import predictor as PR
+    from paper_2501_16909_b300 import train_predictor as TP
+    from paper_2501_16909_b300 import workloads
+
+    full = workloads.config3_base_stressors(ctx.info["num_sms"], bufs, PR.SENSITIVITY_KINDS)
+    sd, _ = TP._beside(ctx, cfgs, [[c] for c in full], repeats=2)
+    return [[sd.get((v, r, 1), float("nan")) for r in range(len(full))] for v in range(len(cfgs))]
+
+
+def features_of(ctx, cfgs, pk, sens, pressure):
+    """(victim features, co-runner features, solo ns) of kernel configurations."""
+    from paper_2501_16909_b300 import predictor as PR
+
+    S = ctx.info["num_sms"]
+    ns, sms = solo_facts(ctx, cfgs)
+    fv, fc = [], []
+    for i, c in enumerate(cfgs):
+        prof = ctx.victim_profile(c)
+        fv.append(PR.victim_features(prof, ns[i], sms[i], sens[i], pk, S))
+        fc.append(PR.kernel_corunner_features(prof, ns[i], sms[i], pressure[i], pk, S))
+    return np.array(fv), np.array(fc), ns
 
 
 def main(argv=None):
     import torch
 
     import paper_2501_16909_b300 as ifr
-    from paper_2501_16909_b300 import _abi as A
-    from paper_2501_16909_b300 import peaks, plan, predictor as PR, train_predictor as TP, workloads
-    from paper_2501_16909_b300.sweep_config3 import slowdown_table
+    from paper_2501_16909_b300 import train_predictor as TP
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--repeats", type=int, default=3)
     ap.add_argument("--pairs-npz", default=None, help="configuration-4 pairs saved by train_predictor --save")
     ap.add_argument("--save", default=None)
     ap.add_argument("--members", type=int, default=5, help="MLPs in the predictor ensemble")
+    ap.add_argument("--max-epochs", type=int, default=500)
+    ap.add_argument("--kernels", default=None,
+                    help="comma-separated kernel names: score only the pairs among these (a reduced run)")
+    ap.add_argument("--rows", default=None,
+                    help="comma-separated co-runner rows of the training collection (a reduced run)")
+    ap.add_argument("--co-idx", default=None, help="comma-separated configuration-3 co-runner indices")
     ap.add_argument("--occupancy-csv", default=None,
                     help="ncu achieved-occupancy capture of the kernels (profile_case config5_kernels): "
                          "adds the Usher / Orion pairing rules' scores")
     a = ap.parse_args(argv)
     log = lambda *x: print(*x, file=sys.stderr)  # noqa: E731
     ctx = ifr.Context(0)
-    S = ctx.info["num_sms"]
-
     # 1. training data: stressor pairs (configuration 4) + kernel pairs among configuration-3 victims
     t0 = time.perf_counter()
     if a.pairs_npz and os.path.exists(a.pairs_npz):
         d = dict(np.load(a.pairs_npz, allow_pickle=True))
     else:
-        d = TP.collect(ctx, repeats=2, log=log)
+        d = TP.collect(ctx, repeats=2, log=log, row_names=a.rows.split(",") if a.rows else None)
     log("stressor pairs: %d (%.1f s)" % (len(d["y"]), time.perf_counter() - t0))
+    out = score(ctx, d, repeats=a.repeats, members=a.members, max_epochs=a.max_epochs,
+                kernels=a.kernels.split(",") if a.kernels else None,
+                co_idx=[int(x) for x in a.co_idx.split(",")] if a.co_idx else None,
+                occupancy_csv=a.occupancy_csv, save=a.save, log=log)
+    ctx.close()
+    torch.cuda.synchronize()
+    print(json.dumps(out))
+    return out
+
+
+def score(ctx, d, repeats=3, members=5, max_epochs=500, kernels=None, co_idx=None, occupancy_csv=None, save=None,
+          log=lambda *x: None):
+    """Steps 2-3 on a context and the configuration-4 pairs `d` (train_predictor.collect):
+    kernel pairs among configuration-3 victims, the configuration-5 pairs and their
+    sensitivity curves, then the predictor ensemble against the measurements."""
+    import paper_2501_16909_b300 as ifr  # noqa: F401
+    from paper_2501_16909_b300 import _abi as A
+    from paper_2501_16909_b300 import peaks, plan, predictor as PR, train_predictor as TP, workloads
+    from paper_2501_16909_b300.sweep_config3 import slowdown_table
+
+    S = ctx.info["num_sms"]
     import ifr_inputs as I
 
     l2 = I.torch_u32_as_i32(3, workloads.L2_SET_BYTES // 4, "cuda")
+    bufs = {"l2": l2, "hbm": I.torch_u32_as_i32(1, (4 << 30) // 4, "cuda")}
     pk = peaks.peaks(ctx, l2)
+    probes, _pt = workloads.probe_victims(S, "cuda")
+    for c in probes:
+        TP.set_launches(ctx, c)
     v3, v3k, _t3 = workloads.config3_victims("cuda")
     v3 = [half_occupancy(c, S) for c in v3]
     for c in v3:
         set_launches(ctx, c, 50000.0)
-    co_idx = [0, 5, 10, 16, 21, 26, 32, 37, 42, 48, 53, 58]  # 3 GEMMs, 3 GEMVs, 3 softmax, 3 layernorm
+    if co_idx is None:
+        co_idx = [0, 5, 10, 16, 21, 26, 32, 37, 42, 48, 53, 58]  # 3 GEMMs, 3 GEMVs, 3 softmax, 3 layernorm
     t0 = time.perf_counter()
     kp = kernel_pairs(ctx, v3, [v3[j] for j in co_idx], repeats=1)
-    F3, _ = features_of(ctx, v3, pk)
+    pres3 = [[float("nan")] * len(probes)] * len(v3)
+    for j, pr in zip(co_idx, probe_pressure(ctx, [v3[j] for j in co_idx], probes)):
+        pres3[j] = pr
+    F3v, F3c, _ = features_of(ctx, v3, pk, full_sensitivity(ctx, v3, bufs), pres3)
     log("kernel pairs: %d (%.1f s)" % (len(kp), time.perf_counter() - t0))
-    Xk = np.array([np.concatenate([F3[i], F3[co_idx[j]]]) for (i, j) in kp])
+    Xk = np.array([np.concatenate([F3v[i], F3c[co_idx[j]]]) for (i, j) in kp])
     yk = np.array(list(kp.values()))
     X = np.concatenate([np.concatenate([d["Xv"], d["Xc"]], axis=1), Xk])
     y = np.concatenate([d["y"], yk])
 
     # 2. configuration-5 kernels, their pairs and sensitivity curves
     kern, _t5 = decoder_kernels(S, "cuda")
-    names = list(kern)
+    names = [n for n in kern if kernels is None or n in kernels]
     cfgs = [kern[n] for n in names]
     for c in cfgs:
         set_launches(ctx, c, 100000.0)
-    F5, solo5 = features_of(ctx, cfgs, pk)
+    F5v, F5c, solo5 = features_of(ctx, cfgs, pk, full_sensitivity(ctx, cfgs, bufs), probe_pressure(ctx, cfgs, probes))
     pre = [i for i, n in enumerate(names) if n.startswith("prefill")]
     dec = [i for i, n in enumerate(names) if n.startswith("decode")]
     t0 = time.perf_counter()
     blk_dp, blk_pd = [], []
-    m_dp = kernel_pairs(ctx, [cfgs[i] for i in dec], [cfgs[j] for j in pre], a.repeats, blk_dp)
-    m_pd = kernel_pairs(ctx, [cfgs[i] for i in pre], [cfgs[j] for j in dec], a.repeats, blk_pd)
+    m_dp = kernel_pairs(ctx, [cfgs[i] for i in dec], [cfgs[j] for j in pre], repeats, blk_dp)
+    m_pd = kernel_pairs(ctx, [cfgs[i] for i in pre], [cfgs[j] for j in dec], repeats, blk_pd)
     log("config-5 pairs: %d + %d (%.1f s)" % (len(m_dp), len(m_pd), time.perf_counter() - t0))
     pairs = [(dec[i], pre[j], s) for (i, j), s in m_dp.items()] + [(pre[i], dec[j], s) for (i, j), s in m_pd.items()]
 
     # victims' sensitivity curves: one batched stressor sweep (7 kinds x 8 autotuned levels)
-    bufs = {"l2": l2, "hbm": I.torch_u32_as_i32(1, (4 << 30) // 4, "cuda")}
     from paper_2501_16909_b300 import autotune
 
     base = workloads.config3_base_stressors(S, bufs)
@@ -269,7 +336,7 @@ def main(argv=None):
         for r, k in enumerate(kinds):
             if k == A.IFR_S_SMEM_32W:
                 continue  # a kernel's shared-memory use is scored with the conflict-free curve
-            x = F5[c][slot[k]]
+            x = F5c[c][slot[k]]
             xs, ss = curves[(v, r)]
             best = max(best, float(np.interp(x, xs, ss)))
         return 1.0 + best
@@ -281,8 +348,9 @@ def main(argv=None):
     nv = len(y) // 10
     # an ensemble of a.members MLPs: single models trained on these pairs scored the
     # configuration-5 pairs anywhere between 17 % and 27 % MAPE from run to run
-    models = PR.train_ensemble(ctx, z(X[idx[nv:]]), y[idx[nv:]], z(X[idx[:nv]]), y[idx[:nv]], members=a.members)
-    Xt = np.array([np.concatenate([F5[v], F5[c]]) for v, c, _ in pairs])
+    models = PR.train_ensemble(ctx, z(X[idx[nv:]]), y[idx[nv:]], z(X[idx[:nv]]), y[idx[:nv]], members=members,
+                               max_epochs=max_epochs)
+    Xt = np.array([np.concatenate([F5v[v], F5c[c]]) for v, c, _ in pairs])
     yt = np.array([s for _, _, s in pairs])
     pred = PR.predict_ensemble(models, z(Xt))
     single = PR.predict(models[0], z(Xt))
@@ -306,17 +374,14 @@ def main(argv=None):
                         for n, prof in ((n, ctx.victim_profile(c)) for n, c in zip(names, cfgs))},
         "peaks": {"tensor": pk[A.IFR_S_TENSOR][0], "fp32": pk[A.IFR_S_FMA][0], "hbm": pk[A.IFR_S_HBM][0]},
     }
-    if a.occupancy_csv:
+    if occupancy_csv:
         from paper_2501_16909_b300 import pairing
 
-        with open(a.occupancy_csv) as f:
+        with open(occupancy_csv) as f:
             occ = pairing.occupancy_by_kernel(names, pairing.parse_ncu_occupancy(f.read()))
         out["pairing"] = pairing.evaluate(out["pairs"], out["kernel_info"], occ, out["peaks"])
-    if a.save:
-        np.savez(a.save, X=X, y=y, Xt=Xt, yt=yt, pred=pred, base=base_pred)
-    ctx.close()
-    torch.cuda.synchronize()
-    print(json.dumps(out))
+    if save:
+        np.savez(save, X=X, y=y, Xt=Xt, yt=yt, pred=pred, base=base_pred)
     return out
 
 

@@ -6,9 +6,10 @@ turns that into the algorithmic quantity its resource's peak is stated in, and
 provides the peaks:
 
 * HBM        bytes/s — MEASURED_PEAKS.json `hbm_gbs` (STREAM-style copy)
-* L2         bytes/s — probe: best stream-kernel rate over 8 / 16 MiB sets, every SM
+* L2         bytes/s — L2_PEAK_BYTES_PER_S: the rate at which the L2 slices' ports to
+                        the crossbar are all busy, from ncu (see the constant)
 * FP32 FMA   flop/s  — SMs x 128 lanes x 2 flop x max SM clock
-* tensor     flop/s  — MEASURED_PEAKS.json `bf16_tflops` (cuBLAS bf16 burst)
+* tensor     flop/s  — SMs x 8192 flop per clock x max SM clock (the pipe's dense rate)
 * shared mem wavefronts/s — SMs x 1 wavefront per clock x max SM clock
 * scheduler  blocks/s — probe: zero-cycle 32-thread blocks on every SM
 * FP64       flop/s  — probe: best fp64 multiply-chain rate on every SM over
@@ -29,6 +30,19 @@ UNIT = {A.IFR_S_HBM: "B", A.IFR_S_L2: "B", A.IFR_S_FMA: "flop", A.IFR_S_TENSOR: 
 # fixed-work rounds of one calibration run per kind (about a millisecond at full SMs)
 CAL_ROUNDS = {A.IFR_S_HBM: 64, A.IFR_S_L2: 256, A.IFR_S_FMA: 32, A.IFR_S_TENSOR: 32, A.IFR_S_SMEM_CF: 16,
               A.IFR_S_SMEM_32W: 32, A.IFR_S_SCHED: 0, A.IFR_S_FP64: 16, A.IFR_S_SLEEP: 10}
+
+
+# Dense BF16 tcgen05 rate of one SM per clock: 4096 multiply-adds (NVIDIA's 2.25
+# PFLOP/s dense BF16 for 148 SMs corresponds to 8192 flop per clock at 1.86 GHz).
+TENSOR_FLOP_PER_CLK = 8192
+
+# The L2's peak, from ncu on B300 (--clock-control none): for a kernel streaming an
+# L2-resident set, lts__t_bytes.sum.per_second / lts__lts2xbar_cycles_active.avg
+# .pct_of_peak_sustained_elapsed is the byte rate with the L2-to-crossbar ports 100 %
+# busy, the sub-unit that bounds ncu's L2 throughput.  Three different stream kernels
+# (17.7 TB/s at 76.2 %, 16.2 TB/s at 69.5 %, 11.4 TB/s at 48.9 % busy) give 23.2
+# TB/s within 0.3 %.  A stressor cannot exceed it, unlike a probe of its own best rate.
+L2_PEAK_BYTES_PER_S = 23.2e12
 
 
 def measured_peaks():
@@ -98,24 +112,16 @@ def peaks(ctx, l2_buf=None):
     clk = ctx.info["sm_clock_khz"] * 1e3
     out = {
         A.IFR_S_HBM: (m["hbm_gbs"] * 1e9, "MEASURED_PEAKS hbm_gbs (%s)" % src),
-        A.IFR_S_TENSOR: (m["bf16_tflops"] * 1e12, "MEASURED_PEAKS bf16_tflops (%s)" % src),
+        # the pipe's own rate, not a GEMM's: the stressor's tiles sit in shared memory
+        # and it outruns a cuBLAS GEMM (the measured bf16_tflops) by 18 %
+        A.IFR_S_TENSOR: (S * TENSOR_FLOP_PER_CLK * clk, "nominal: SMs x 8192 bf16 flop per clock (dense "
+                                                        "tcgen05) x max SM clock"),
         A.IFR_S_FMA: (S * 128 * 2 * clk, "nominal: SMs x 128 FP32 lanes x 2 flop x max SM clock"),
         A.IFR_S_SMEM_CF: (S * clk, "nominal: SMs x 1 shared-memory wavefront per clock x max SM clock"),
         A.IFR_S_SMEM_32W: (S * clk, "nominal: SMs x 1 shared-memory wavefront per clock x max SM clock"),
     }
-    if l2_buf is not None:
-        best = (0.0, "")
-        for mib in (8, 16):
-            nb = min(l2_buf.numel() * 4, mib << 20)
-            nb -= nb % (512 * 64)
-            for bps in (2, 4):
-                cfg = stressor_cfg(A.IFR_S_L2, sm_count=S, blocks_per_sm=bps, block=512, buf=l2_buf,
-                                   working_set_bytes=nb)
-                rate, _ = solo_rate(ctx, cfg, rounds=256)
-                if rate > best[0]:
-                    best = (rate, "probe: best stream-kernel rate over 8 / 16 MiB L2-resident sets and 2 / 4 "
-                                  "blocks of 512 on every SM (%d MiB, %d blocks)" % (nb >> 20, bps))
-        out[A.IFR_S_L2] = best
+    out[A.IFR_S_L2] = (L2_PEAK_BYTES_PER_S, "ncu: L2-to-crossbar ports fully busy (lts__t_bytes rate over "
+                                            "lts__lts2xbar_cycles_active, B300)")
     best = (0.0, "")
     for bps, ilp in ((4, 4), (8, 4), (4, 8), (8, 8)):
         cfg = stressor_cfg(A.IFR_S_FP64, sm_count=S, blocks_per_sm=bps, block=256, ilp=ilp)

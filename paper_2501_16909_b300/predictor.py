@@ -1,22 +1,30 @@
 """Learned slowdown predictor — the kernel-level interference estimator of Sec. 5.1.
 
 The paper proposes an estimator that collects each kernel's metrics and resource
-sensitivity and predicts its slowdown under colocation; it gives no model.  Here:
+sensitivity and predicts its slowdown under colocation; it gives no model.  Here a
+pair (victim, co-runner) is described by 24 measured solo quantities of each side
+(a profiler that replays kernels serialises them and cannot observe colocation,
+Sec. 5.2, so every quantity comes from the library's own solo and probe runs):
 
-* every kernel (victim, or co-runner = a stressor configuration) gets a solo
-  profile of 24 features (FEATURES): its achieved fraction of each resource's peak
-  (HBM, L2, tensor pipe, FP32 pipe, shared-memory wavefronts, block dispatch) and
-  its launch shape (threads, registers, shared memory, occupancy, waves, TMEM,
-  SMs used, duty, ILP, bank-conflict degree, work and duration);
-* a pair is the concatenation victim || co-runner (48 features, z-scored with the
-  training statistics); the target is the log of the measured slowdown;
-* the network is an MLP 48-256-256-256-1 with exact GELU, bf16 weights and
-  activations into the tensor cores with fp32 accumulation, trained with Adam
-  (lr 1e-3, batch 512) by the library's own kernels (ifr_mlp_forward / backward,
-  ifr_mse_grad, ifr_adam_step) behind a torch.autograd.Function;
-* the baseline without the network ("the method without it") predicts
-  1 + S_v,r(x): the victim's measured slowdown-minus-one curve for the co-runner's
-  resource r, interpolated at the co-runner's solo fraction x of that resource.
+* victim (VICTIM_FEATURES): its achieved fraction of the HBM, L2, tensor and FP32
+  peaks (algorithmic bytes and flops over its measured solo time), that time, the
+  SMs its blocks ran on, its measured sensitivity — the log slowdown beside each of
+  the seven stressor kinds at full intensity (Sec. 5.1's "resource sensitivity") —
+  and its launch shape (threads, registers, shared memory, occupancy, waves, TMEM);
+* co-runner (CORUNNER_FEATURES): its measured solo fraction of each resource's peak
+  (a stressor's rate over the peak of its resource, the HBM stream's rate also over
+  the L2 peak since every byte crosses the L2; a kernel's algorithmic rates), its
+  measured pressure — the log slowdown of each of six probe kernels run beside it —
+  the SMs and blocks it held (from its block logs), and its launch shape.
+
+The pair's 48 features are z-scored with the training statistics; the target is
+the log of the measured slowdown.  The network is an MLP 48-256-256-256-1 with exact
+GELU, bf16 weights and activations into the tensor cores with fp32 accumulation,
+trained with Adam (lr 1e-3, batch 512) by the library's own kernels
+(ifr_mlp_forward / backward, ifr_mse_grad, ifr_adam_step) behind a
+torch.autograd.Function.  The baseline without the network ("the method without
+it") predicts 1 + S_v,r(x): the victim's measured slowdown-minus-one curve for the
+co-runner's resource r at the co-runner's solo fraction x of that resource.
 """
 from __future__ import annotations
 
@@ -29,12 +37,21 @@ import torch
 from . import _abi as A
 from . import check
 
-FEATURES = [
-    "frac_hbm", "frac_l2", "frac_tensor", "frac_fp32", "frac_smem", "frac_sched", "conflict_degree",
-    "sm_fraction", "threads_per_block", "regs_per_thread", "smem_per_block", "occupancy_blocks",
-    "warps_per_sm", "log_waves", "tmem_cols", "uses_tensor", "log_intensity", "log_duration_us", "duty", "ilp",
-    "log_bytes", "log_flops", "is_stressor", "thread_fill",
-]
+# kinds whose full-intensity slowdown makes up a victim's sensitivity vector, in order
+SENSITIVITY_KINDS = [A.IFR_S_SCHED, A.IFR_S_FMA, A.IFR_S_TENSOR, A.IFR_S_SMEM_CF, A.IFR_S_SMEM_32W, A.IFR_S_L2,
+                     A.IFR_S_HBM]
+PROBES = ["hbm_triad", "l2_triad", "tensor_gemm", "smem_hist", "exp_softmax", "short_gemv"]
+
+VICTIM_FEATURES = (["frac_hbm", "frac_l2", "frac_tensor", "frac_fp32", "log_duration_us", "sm_fraction"] +
+                   ["log_sens_" + A.STRESSOR_NAMES[k] for k in SENSITIVITY_KINDS] +
+                   ["threads_per_block", "regs_per_thread", "smem_per_block", "occupancy_blocks", "log_waves",
+                    "tmem_cols", "uses_tensor", "log_bytes", "log_flops", "log_intensity", "thread_fill"])
+CORUNNER_FEATURES = (["frac_hbm", "frac_l2", "frac_tensor", "frac_fp32", "frac_smem", "frac_sched"] +
+                     ["log_pressure_" + p for p in PROBES] +
+                     ["sm_fraction", "blocks_per_sm", "warps_per_sm", "threads_per_block", "regs_per_thread",
+                      "smem_per_block", "tmem_cols", "occupancy_blocks", "log_rate", "log_solo_ms",
+                      "pressure_max", "pressure_mean"])
+assert len(VICTIM_FEATURES) == 24 and len(CORUNNER_FEATURES) == 24
 RESOURCE_OF = {A.IFR_S_HBM: 0, A.IFR_S_L2: 1, A.IFR_S_TENSOR: 2, A.IFR_S_FMA: 3, A.IFR_S_SMEM_CF: 4,
                A.IFR_S_SMEM_32W: 4, A.IFR_S_SCHED: 5}
 
@@ -43,16 +60,18 @@ def _safe_log10(x):
     return math.log10(max(float(x), 1e-12))
 
 
-def _shape_features(prof, S, grid_blocks_active=None):
-    blocks = prof["grid"] if grid_blocks_active is None else grid_blocks_active
+def _log_slow(s):
+    return math.log(max(float(s), 1e-3)) if s == s else 0.0  # NaN (no valid cell): no evidence
+
+
+def _shape(prof, S, blocks=None):
+    blocks = prof["grid"] if blocks is None else blocks
     occ = max(1, prof["max_blocks_per_sm"])
-    resident = min(occ, max(1, math.ceil(blocks / S)))
     return {
         "threads_per_block": prof["block"] / 1024.0,
         "regs_per_thread": prof["regs_per_thread"] / 255.0,
         "smem_per_block": (prof["static_smem"] + prof["dynamic_smem"]) / (228.0 * 1024),
         "occupancy_blocks": occ / 32.0,
-        "warps_per_sm": resident * prof["block"] / 32.0 / 64.0,
         "log_waves": _safe_log10(blocks / (S * occ)),
         "tmem_cols": prof["tmem_cols"] / 512.0,
         "uses_tensor": float(prof["uses_tensor"]),
@@ -60,44 +79,75 @@ def _shape_features(prof, S, grid_blocks_active=None):
     }
 
 
-def victim_features(prof, solo_ns, pk, S):
-    """24 features of a victim from its profile and solo duration per launch (ns)."""
+def kernel_fracs(prof, solo_ns, pk):
+    """Achieved fractions of the HBM, L2, tensor and FP32 peaks of one kernel launch:
+    its algorithmic bytes and flops over its measured solo time."""
     T = max(solo_ns, 1.0) * 1e-9
     bps = prof["bytes_per_launch"] / T
     fps = prof["flops_per_launch"] / T
-    f = dict.fromkeys(FEATURES, 0.0)
-    f.update(_shape_features(prof, S))
-    f["frac_hbm"] = bps / pk[A.IFR_S_HBM][0]
-    f["frac_l2"] = bps / pk[A.IFR_S_L2][0]
-    if prof["uses_tensor"]:
-        f["frac_tensor"] = fps / pk[A.IFR_S_TENSOR][0]
-    else:
-        f["frac_fp32"] = fps / pk[A.IFR_S_FMA][0]
-    f["frac_sched"] = prof["grid"] / T / pk[A.IFR_S_SCHED][0]
-    f["sm_fraction"] = min(1.0, prof["grid"] / S)
-    f["log_intensity"] = _safe_log10(prof["flops_per_launch"] / max(prof["bytes_per_launch"], 1.0) + 1e-3)
-    f["log_duration_us"] = _safe_log10(T * 1e6)
+    return {"frac_hbm": bps / pk[A.IFR_S_HBM][0], "frac_l2": bps / pk[A.IFR_S_L2][0],
+            "frac_tensor": fps / pk[A.IFR_S_TENSOR][0] if prof["uses_tensor"] else 0.0,
+            "frac_fp32": 0.0 if prof["uses_tensor"] else fps / pk[A.IFR_S_FMA][0]}
+
+
+def victim_features(prof, solo_ns, sms_touched, sens, pk, S):
+    """24 measured features of a victim: profile, solo time per launch (ns), SMs its
+    blocks ran on, and its sensitivity (slowdown beside each SENSITIVITY_KINDS
+    stressor at full intensity)."""
+    f = dict.fromkeys(VICTIM_FEATURES, 0.0)
+    f.update({k: v for k, v in _shape(prof, S).items() if k in f})
+    f.update(kernel_fracs(prof, solo_ns, pk))
+    f["log_duration_us"] = _safe_log10(max(solo_ns, 1.0) * 1e-3)
+    f["sm_fraction"] = min(1.0, sms_touched / S)
+    for k, s in zip(SENSITIVITY_KINDS, sens):
+        f["log_sens_" + A.STRESSOR_NAMES[k]] = _log_slow(s)
     f["log_bytes"] = _safe_log10(prof["bytes_per_launch"] + 1.0)
     f["log_flops"] = _safe_log10(prof["flops_per_launch"] + 1.0)
-    return np.array([f[k] for k in FEATURES], np.float64)
+    f["log_intensity"] = _safe_log10(prof["flops_per_launch"] / max(prof["bytes_per_launch"], 1.0) + 1e-3)
+    return np.array([f[k] for k in VICTIM_FEATURES], np.float64)
 
 
-def stressor_features(prof, cfg, frac_of_peak, S):
-    """24 features of a stressor configuration from its profile and solo fraction of peak."""
-    f = dict.fromkeys(FEATURES, 0.0)
-    active = cfg.sm_count * max(1, prof["blocks_per_sm"])
-    f.update(_shape_features(prof, S, active if cfg.kind != A.IFR_S_SCHED else None))
+def _pressure(f, pressure):
+    logs = [_log_slow(s) for s in pressure]
+    for p, v in zip(PROBES, logs):
+        f["log_pressure_" + p] = v
+    f["pressure_max"] = max(logs)
+    f["pressure_mean"] = sum(logs) / len(logs)
+
+
+def stressor_corunner_features(prof, cfg, rate, frac_of_peak, pk, solo, pressure, S):
+    """24 measured features of a stressor configuration as a co-runner: its solo rate
+    and fraction of its resource's peak, `solo` (the fixed-work solo run's result:
+    SMs used, active blocks, elapsed ms) and its pressure on the PROBES."""
+    f = dict.fromkeys(CORUNNER_FEATURES, 0.0)
     slot = ["frac_hbm", "frac_l2", "frac_tensor", "frac_fp32", "frac_smem", "frac_sched"][RESOURCE_OF[cfg.kind]]
     f[slot] = frac_of_peak
     if cfg.kind == A.IFR_S_HBM:
-        f["frac_l2"] = frac_of_peak * 0.4  # every DRAM byte also crosses L2
-    if cfg.kind in (A.IFR_S_SMEM_CF, A.IFR_S_SMEM_32W):
-        f["conflict_degree"] = (cfg.smem_ways or (1 if cfg.kind == A.IFR_S_SMEM_CF else 32)) / 32.0
-    f["sm_fraction"] = cfg.sm_count / S
-    f["duty"] = cfg.duty if 0.0 < cfg.duty < 1.0 else 1.0
-    f["ilp"] = (cfg.ilp or 4) / 8.0 if cfg.kind == A.IFR_S_FMA else 0.0
-    f["is_stressor"] = 1.0
-    return np.array([f[k] for k in FEATURES], np.float64)
+        f["frac_l2"] = rate / pk[A.IFR_S_L2][0]  # every byte read from DRAM crosses the L2
+    _pressure(f, pressure)
+    f["sm_fraction"] = solo["sms_used"] / S
+    f["blocks_per_sm"] = solo["blocks_active"] / S / 8.0
+    f["warps_per_sm"] = solo["blocks_active"] * prof["block"] / 32.0 / S / 64.0
+    f.update({k: v for k, v in _shape(prof, S).items() if k in f})
+    f["log_rate"] = _safe_log10(rate)
+    f["log_solo_ms"] = _safe_log10(solo["elapsed_ms"])
+    return np.array([f[k] for k in CORUNNER_FEATURES], np.float64)
+
+
+def kernel_corunner_features(prof, solo_ns, sms_touched, pressure, pk, S):
+    """24 measured features of a kernel (a victim configuration) as a co-runner."""
+    f = dict.fromkeys(CORUNNER_FEATURES, 0.0)
+    f.update(kernel_fracs(prof, solo_ns, pk))
+    f["frac_sched"] = prof["grid"] / (max(solo_ns, 1.0) * 1e-9) / pk[A.IFR_S_SCHED][0]
+    _pressure(f, pressure)
+    f["sm_fraction"] = min(1.0, sms_touched / S)
+    blocks = min(prof["grid"], S * max(1, prof["max_blocks_per_sm"]))
+    f["blocks_per_sm"] = blocks / S / 8.0
+    f["warps_per_sm"] = blocks * prof["block"] / 32.0 / S / 64.0
+    f.update({k: v for k, v in _shape(prof, S).items() if k in f})
+    f["log_rate"] = _safe_log10((prof["bytes_per_launch"] + prof["flops_per_launch"]) / (max(solo_ns, 1.0) * 1e-9))
+    f["log_solo_ms"] = _safe_log10(solo_ns * 1e-6)
+    return np.array([f[k] for k in CORUNNER_FEATURES], np.float64)
 
 
 # ----------------------------------------------------------------------------- the network
@@ -248,13 +298,20 @@ def mape(pred, y):
 
 
 class Standardizer:
+    """z-scores with the training statistics, clipped to +-Z_CLIP: a held-out kernel
+    whose feature lies far outside the training range (a feature constant on the
+    training side, say) enters the network at the edge of that range instead of at a
+    z-score of thousands."""
+
+    Z_CLIP = 8.0
+
     def __init__(self, X):
         self.mu = X.mean(axis=0)
         self.sd = X.std(axis=0)
         self.sd[self.sd < 1e-9] = 1.0
 
     def __call__(self, X):
-        return (X - self.mu) / self.sd
+        return np.clip((X - self.mu) / self.sd, -self.Z_CLIP, self.Z_CLIP)
 
 
 def train(model, Xtr, ytr, Xva, yva, lr=1e-3, batch=512, max_epochs=500, patience=20, seed=5, log=None):
@@ -310,13 +367,18 @@ def predict_ensemble(models, X):
     return np.exp(logs.mean(axis=0))
 
 
+# predicted log slowdowns are clamped to slowdowns in [1/4, 1000]: the measured ones
+# lie within about 0.9 .. 60
+LOG_SLOWDOWN_RANGE = (math.log(0.25), math.log(1000.0))
+
+
 def predict(model, X, batch=512):
     X = torch.as_tensor(X, dtype=torch.float32, device=model.device)
     out = []
     for s in range(0, X.shape[0], batch):
         xb = X[s:s + batch]
         out.append(model.forward(xb).clone())
-    return np.exp(torch.cat(out).double().cpu().numpy())
+    return np.exp(np.clip(torch.cat(out).double().cpu().numpy(), *LOG_SLOWDOWN_RANGE))
 
 
 # ----------------------------------------------------------------------------- baseline

@@ -14,7 +14,11 @@ Evaluations (seed 5):
   random    80/20 split over all pairs (the configuration's split);
   unseen    the MLP is trained on every base pair and 80 % of the variant
             configurations and tested on the pairs of the other 20 %, which the
-            baseline's sensitivity curves (measured on base kinds only) never saw.
+            baseline's sensitivity curves (measured on base kinds only) never saw;
+  kind      leave one stressor kind out: trained without any co-runner of that
+            kind (base rows and variants), tested on them; pooled over the kinds.
+Features are measured solo quantities of both sides (see the predictor module):
+no configuration knob (ILP, conflict degree, duty) is an input.
 Baseline: 1 + S_v,r(x), the victim's measured slowdown-minus-one curve for the
 base kind matching the co-runner's resource, at the co-runner's solo fraction x.
 """
@@ -66,50 +70,110 @@ def corunner_rows(S, bufs):
     return rows
 
 
-def collect(ctx, repeats=2, log=print):
-    """Measure every (victim, co-runner) pair; returns a dict of numpy arrays."""
+def set_launches(ctx, cfg, target_ns=50000.0, cap=64):
+    """K back-to-back launches per measurement so that K launches span ~target_ns."""
+    cfg.repeats = 1
+    tm = ctx.victim_launch(cfg)
+    one = max(1.0, float(tm["t_end_ns"] - tm["t_start_ns"]))
+    cfg.repeats = int(max(1, min(cap, round(target_ns / one))))
+
+
+def _beside(ctx, victims, level_rows, repeats=1):
+    """Graph-batched sweep of `victims` beside every configuration of `level_rows`
+    ([rows][levels]); returns {(victim, row, level 1..L): median slowdown}."""
+    from paper_2501_16909_b300 import plan
+    from paper_2501_16909_b300.sweep_config3 import slowdown_table
+
+    windows = plan.solo_windows(ctx, victims)
+    t_launch = plan.sched_launch_ns(ctx, level_rows)
+    _, lv_b = plan.mode_levels(level_rows, windows, t_launch)
+    cells = ctx.sweep(victims, lv_b, repeats, batched=True)
+    sd, _ = slowdown_table(cells)
+    return sd, cells
+
+
+def collect(ctx, repeats=2, log=print, row_names=None):
+    """Measure every (victim, co-runner) pair and both sides' solo features; returns a
+    dict of numpy arrays.
+
+    1. every co-runner row is autotuned (8 or 16 intensities);
+    2. each tuned configuration runs alone once more (fixed work): its block logs
+       give the SMs and blocks it held, its CUDA-event time its rate;
+    3. its pressure: the six probe kernels run beside it (graph-batched);
+    4. each victim's sensitivity: its slowdown beside every stressor kind at full
+       intensity (a separate graph-batched sweep);
+    5. the pairs: every victim beside every tuned configuration (graph-batched)."""
     import torch
 
     import ifr_inputs as I
     from paper_2501_16909_b300 import _abi as A
-    from paper_2501_16909_b300 import autotune, peaks, plan, predictor, workloads
+    from paper_2501_16909_b300 import autotune, peaks, predictor, workloads
     from paper_2501_16909_b300.sweep_config3 import slowdown_table
 
     S = ctx.info["num_sms"]
-    bufs = {"l2": I.torch_u32_as_i32(3, (workloads.L2_SET_BYTES) // 4, "cuda"), "hbm": I.torch_u32_as_i32(1, (4 << 30) // 4, "cuda")}
+    bufs = {"l2": I.torch_u32_as_i32(3, (workloads.L2_SET_BYTES) // 4, "cuda"),
+            "hbm": I.torch_u32_as_i32(1, (4 << 30) // 4, "cuda")}
     victims, vkinds, _t = workloads.config3_victims("cuda")
+    probes, _pt = workloads.probe_victims(S, "cuda")
+    for c in probes:
+        set_launches(ctx, c)
     pk = peaks.peaks(ctx, bufs["l2"])
     rows = corunner_rows(S, bufs)
+    if row_names is not None:  # a reduced collection: only these co-runner rows
+        rows = [r for r in rows if r[0] in row_names]
     tuned = []
     t0 = time.perf_counter()
     for name, k, base, fr in rows:
         tuner = autotune.Tuner(ctx, base, pk[k][0])
         _, lv = tuner.tune(fr)
         cfgs = [peaks.copy_cfg(base, sm_count=l.sm_count, duty=(l.duty if l.duty < 1 else 0.0)) for l in lv]
-        tuned.append((name, k, cfgs, [l.frac_of_peak for l in lv]))
+        tuned.append((name, k, cfgs, [l.frac_of_peak for l in lv], [l.rate for l in lv]))
     log("autotuned %d rows in %.1f s" % (len(rows), time.perf_counter() - t0))
+    # 2. solo runs of every tuned configuration (block logs: SMs used, active blocks)
+    solo = {}
+    for r, (_n, _k, cfgs, _f, _rt) in enumerate(tuned):
+        for l, cfg in enumerate(cfgs):
+            _rate, res = peaks.solo_rate(ctx, cfg)
+            solo[(r, l)] = res
+    # 3. pressure of every tuned configuration on the probes
+    pres = {}
+    t0 = time.perf_counter()
+    for c0 in range(0, len(tuned), 16):
+        chunk = tuned[c0:c0 + 16]
+        sd, _ = _beside(ctx, probes, [cfgs for _, _, cfgs, _, _ in chunk])
+        for r in range(len(chunk)):
+            for l in range(len(chunk[r][2])):
+                pres[(c0 + r, l)] = [sd.get((p, r, l + 1), float("nan")) for p in range(len(probes))]
+    log("probe pressure of %d configurations in %.1f s" % (len(pres), time.perf_counter() - t0))
+    # 4. victims' sensitivity to every stressor kind at full intensity
+    full = workloads.config3_base_stressors(S, bufs, predictor.SENSITIVITY_KINDS)
+    sd_full, _ = _beside(ctx, victims, [[c] for c in full])
+    sens = [[sd_full.get((v, r, 1), float("nan")) for r in range(len(full))] for v in range(len(victims))]
+    # 5. the pairs
     vprof = [ctx.victim_profile(v) for v in victims]
-    windows = plan.solo_windows(ctx, victims)
     X_v, X_c, y, meta = [], [], [], []
     for c0 in range(0, len(tuned), 16):
         chunk = tuned[c0:c0 + 16]
-        levels = [cfgs for _, _, cfgs, _ in chunk]
-        t_launch = plan.sched_launch_ns(ctx, levels)
-        _, lv_b = plan.mode_levels(levels, windows, t_launch)
         t1 = time.perf_counter()
-        cells = ctx.sweep(victims, lv_b, repeats, batched=True)
+        sd, cells = _beside(ctx, victims, [cfgs for _, _, cfgs, _, _ in chunk], repeats)
         log("sweep rows %d..%d: %d cells, %d valid, %.1f s" % (c0, c0 + len(chunk) - 1, len(cells),
                                                                sum(c.valid for c in cells), time.perf_counter() - t1))
-        sd, t0v = slowdown_table(cells)
-        for r, (name, k, cfgs, fracs) in enumerate(chunk):
-            for l, (cfg, frac) in enumerate(zip(cfgs, fracs)):
+        _, t0v = slowdown_table(cells)
+        sms = {}
+        for c in cells:
+            if c.stressor < 0 and c.valid:
+                sms[c.victim] = max(sms.get(c.victim, 0), c.timing.sms_touched)
+        fv = {v: predictor.victim_features(vprof[v], t0v[v], sms.get(v, S), sens[v], pk, S) for v in t0v}
+        for r, (name, k, cfgs, fracs, rates) in enumerate(chunk):
+            for l, (cfg, frac, rate) in enumerate(zip(cfgs, fracs, rates)):
                 prof = ctx.stressor_profile(cfg)
-                fc = predictor.stressor_features(prof, cfg, frac, S)
+                fc = predictor.stressor_corunner_features(prof, cfg, rate, frac, pk, solo[(c0 + r, l)],
+                                                          pres[(c0 + r, l)], S)
                 for v in range(len(victims)):
                     key = (v, r, l + 1)
-                    if key not in sd or v not in t0v:
+                    if key not in sd or v not in fv:
                         continue
-                    X_v.append(predictor.victim_features(vprof[v], t0v[v], pk, S))
+                    X_v.append(fv[v])
                     X_c.append(fc)
                     y.append(sd[key])
                     meta.append((v, c0 + r, l, k, frac))
@@ -117,7 +181,8 @@ def collect(ctx, repeats=2, log=print):
     m = np.array(meta, np.float64)
     return {"Xv": np.array(X_v), "Xc": np.array(X_c), "y": np.array(y), "victim": m[:, 0].astype(int),
             "row": m[:, 1].astype(int), "level": m[:, 2].astype(int), "kind": m[:, 3].astype(int), "frac": m[:, 4],
-            "row_names": np.array([t[0] for t in tuned]), "n_base_rows": 14,
+            "row_names": np.array([t[0] for t in tuned]),
+            "n_base_rows": sum(1 for t in tuned if t[0].endswith("/a") or t[0].endswith("/b")),
             "victim_kinds": np.array([A.VICTIM_NAMES[k] for k in vkinds])}
 
 
@@ -136,20 +201,42 @@ def sensitivity_curves(d, mask):
     return curves
 
 
+SPLITS = ("random", "unseen", "kind")
+
+
 def evaluate(ctx, d, split="random", seed=5, max_epochs=500, log=None):
+    """MAPE of the MLP and of the baseline on held-out measured pairs.  Splits:
+    random (20 % of all pairs), unseen (the pairs of 20 % of the variant
+    configurations) and kind (leave one stressor kind out: for every kind, train on
+    the pairs of the other kinds' co-runners, base rows and variants, and test on
+    that kind's; the figures pool all seven folds)."""
+    if split == "kind":
+        res = [evaluate(ctx, d, ("kind", k), seed, max_epochs, log) for k in np.unique(d["kind"])]
+        n = sum(r["test_pairs"] for r in res)
+        pool = lambda key: round(sum(r[key] * r["test_pairs"] for r in res) / n, 4)  # noqa: E731
+        return {"split": "kind", "train_pairs": int(np.mean([r["train_pairs"] for r in res])),
+                "test_pairs": int(n), "epochs": int(sum(r["epochs"] for r in res)),
+                "train_s": round(sum(r["train_s"] for r in res), 2), "mlp_mape": pool("mlp_mape"),
+                "baseline_mape": pool("baseline_mape"),
+                "mlp_mape_by_held_out_kind": {r["held_out"]: r["mlp_mape"] for r in res}}
+    from paper_2501_16909_b300 import _abi as A
     from paper_2501_16909_b300 import predictor as PR
 
     n = len(d["y"])
     rng = np.random.default_rng(seed)
     base = d["row"] < d["n_base_rows"]
+    held_kind = None
     if split == "random":
         test = np.zeros(n, bool)
         test[rng.permutation(n)[: n // 5]] = True
-    else:
+    elif split == "unseen":
         cfg_id = d["row"] * 100 + d["level"]
         var_ids = np.unique(cfg_id[~base])
         held = rng.permutation(var_ids)[: max(1, len(var_ids) // 5)]
         test = np.isin(cfg_id, held)
+    else:
+        held_kind = int(split[1])
+        test = d["kind"] == held_kind
     train = ~test
     X = np.concatenate([d["Xv"], d["Xc"]], axis=1)
     # validation for early stopping: 10 % of the training pairs
@@ -172,7 +259,9 @@ def evaluate(ctx, d, split="random", seed=5, max_epochs=500, log=None):
     for i in te:
         key = (int(d["victim"][i]), int(d["kind"][i]))
         bl.append(PR.baseline_predict(curves, *key, d["frac"][i]) if key in curves else 1.0)
-    return {"split": split, "train_pairs": int(len(fit_idx)), "val_pairs": int(nv), "test_pairs": int(len(te)),
+    return {"split": split if held_kind is None else "kind", "train_pairs": int(len(fit_idx)), "val_pairs": int(nv),
+            "test_pairs": int(len(te)),
+            "held_out": A.STRESSOR_NAMES[held_kind] if held_kind is not None else None,
             "epochs": len(hist), "train_s": round(train_s, 2), "mlp_mape": round(mlp_mape, 4),
             "baseline_mape": round(PR.mape(bl, d["y"][te]), 4),
             "mlp_mape_by_victim_kind": {k: round(PR.mape(pred[d["victim_kinds"][d["victim"][te]] == k],
@@ -199,7 +288,7 @@ def main(argv=None):
             np.savez(a.save, **d)
     out = {"pairs": int(len(d["y"])), "slowdown_median": round(float(np.median(d["y"])), 4),
            "slowdown_p90": round(float(np.quantile(d["y"], 0.9)), 4)}
-    for split in ("random", "unseen"):
+    for split in SPLITS:
         out[split] = evaluate(ctx, d, split, max_epochs=a.max_epochs)
     ctx.close()
     print(json.dumps(out))

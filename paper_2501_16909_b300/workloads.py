@@ -74,7 +74,9 @@ STRESSOR_DEFAULTS = {
     A.IFR_S_TENSOR: dict(blocks_per_sm=1),
     A.IFR_S_SMEM_CF: dict(block=256, blocks_per_sm=2),
     A.IFR_S_SMEM_32W: dict(block=256, blocks_per_sm=2),
-    A.IFR_S_L2: dict(block=512, blocks_per_sm=2),
+    # four blocks of 256 hold the same threads and registers per SM as two of 512 and
+    # stream 17.2 TB/s from the L2 against 14.2 (B300, same box)
+    A.IFR_S_L2: dict(block=256, blocks_per_sm=4),
     A.IFR_S_HBM: dict(block=512, blocks_per_sm=2),
     # the paper's fp64 compute kernel shape (Sec. 4.4.3): one 128-thread block per SM
     A.IFR_S_FP64: dict(block=128, blocks_per_sm=1, ilp=4),
@@ -214,3 +216,39 @@ def config3_base_stressors(num_sms: int, bufs, kinds=None):
     kinds = kinds or [A.IFR_S_SCHED, A.IFR_S_FMA, A.IFR_S_TENSOR, A.IFR_S_SMEM_CF, A.IFR_S_SMEM_32W, A.IFR_S_L2,
                       A.IFR_S_HBM]
     return [stressor_level_cfg(k, num_sms, bufs, seed=r + 1) for r, k in enumerate(kinds)]
+
+
+# ----------------------------------------------------------------------------- probes
+def probe_victims(num_sms, device="cuda"):
+    """Six small kernels whose slowdown beside a co-runner measures the co-runner's
+    pressure on one resource each (the predictor's co-runner features), in the order
+    of predictor.PROBES: an HBM-bound triad (2^24 elements, 192 MiB), an L2-resident
+    triad (2^19 elements, 6 MiB), a tensor-pipe GEMM (2048 x 2048 x 1024), a
+    shared-memory-atomic histogram (2^22 keys), an exp-bound softmax (4096 x 1024) and
+    a GEMV of 65536 short rows (64 columns: many light blocks).  Seeds 300..315."""
+    t = {}
+    n = 1 << 24
+    t["hb"], t["hc"], t["ha"] = (I.torch_uniform_pm1(300, n, device), I.torch_uniform_pm1(301, n, device),
+                                 torch.empty(n, device=device))
+    m = 1 << 19
+    t["lb"], t["lc"], t["la"] = (I.torch_uniform_pm1(302, m, device), I.torch_uniform_pm1(303, m, device),
+                                 torch.empty(m, device=device))
+    t["gA"] = I.torch_normal_bf16(304, 2048 * 1024, device).view(2048, 1024)
+    t["gB"] = I.torch_normal_bf16(305, 2048 * 1024, device).view(2048, 1024)
+    t["gC"] = torch.empty(2048, 2048, device=device)
+    t["hk"] = I.torch_key256(306, 1 << 22, device)
+    t["hbins"] = torch.zeros(256, dtype=torch.int32, device=device)
+    t["sx"] = I.torch_uniform_pm1(307, 4096 * 1024, device).view(4096, 1024)
+    t["sy"] = torch.empty_like(t["sx"])
+    t["vA"] = I.torch_normal_bf16(308, 65536 * 64, device).view(65536, 64)
+    t["vx"] = I.torch_normal_bf16(309, 64, device)
+    t["vy"] = torch.empty(65536, device=device)
+    probes = [
+        victim_cfg(A.IFR_V_TRIAD, t["hb"], t["hc"], t["ha"], n=n, scalar=1.5),
+        victim_cfg(A.IFR_V_TRIAD, t["lb"], t["lc"], t["la"], n=m, scalar=1.5),
+        victim_cfg(A.IFR_V_GEMM, t["gA"], t["gB"], t["gC"], m=2048, n=2048, k=1024),
+        victim_cfg(A.IFR_V_HIST, t["hk"], None, t["hbins"], n=1 << 22),
+        victim_cfg(A.IFR_V_SOFTMAX, t["sx"], None, t["sy"], m=4096, n=1024),
+        victim_cfg(A.IFR_V_GEMV, t["vA"], t["vx"], t["vy"], m=65536, k=64),
+    ]
+    return probes, t
