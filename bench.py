@@ -247,7 +247,7 @@ def run_ours(args):
     hb = full.get("hbm")
     roofline_hbm = {"bound": "hbm", "achieved": round(hb["rate"] / 1e9, 1), "peak": round(pk[A.IFR_S_HBM][0] / 1e9, 1),
                     "unit": "GB/s", "frac": round(hb["frac"], 4), "traffic": ncu_traffic("hbm"),
-                    "kernel": "stream_stress_kernel (HBM 4 GiB set, %d SMs x 2 blocks of 512, %d rounds x 4 chunks "
+                    "kernel": "stream_stress_kernel (HBM 4 GiB set, %d SMs x 2 blocks of 512, %d rounds x 8 chunks "
                               "x 32 KiB per block)" % (S, P.CAL_ROUNDS[A.IFR_S_HBM]),
                     "peak_source": pk[A.IFR_S_HBM][1]}
 
@@ -859,7 +859,8 @@ def run_config3(args):
     roofline_hbm = {"bound": "hbm", "achieved": round(hb["rate"] / 1e9, 1), "peak": round(hb["peak"] / 1e9, 1),
                     "unit": "GB/s", "frac": round(hb["frac"], 4), "traffic": ncu_traffic("hbm"),
                     "kernel": "stream_stress_kernel (16-byte loads; HBM 4 GiB set, %d SMs x 2 blocks of 512, "
-                              "%d rounds x 4 chunks x 32 KiB per block)" % (S, P.CAL_ROUNDS[A.IFR_S_HBM]),
+                              "%d rounds x %d chunks x 32 KiB per block)" % (S, P.CAL_ROUNDS[A.IFR_S_HBM],
+                                                                          P.STREAM_CHUNKS_PER_ROUND),
                     "peak_source": hb["peak_source"] + " (of measured)",
                     "tma_staging": {"achieved": round(solo["stressors"]["hbm_tma"]["rate"] / 1e9, 1),
                                     "frac": round(solo["stressors"]["hbm_tma"]["frac"], 4),

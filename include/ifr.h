@@ -261,6 +261,18 @@ typedef struct {
                               wait until they exit, so it is for solo use
                               (ifr_victim_launch); ifr_sweep, ifr_corun and ifr_colocate
                               refuse it with IFR_ERR_ARG.
+                              3 = throughput, two accumulators: variant 1 (4 stages) with
+                              two 256-column TMEM accumulators, so the next tile's MMAs
+                              overlap the epilogue, and, when the tiles leave the last wave
+                              of CTAs part-empty, the left-over tiles split into 2-4 K
+                              ranges of at least 2048 (partial tiles in a context-owned
+                              workspace, reduced in a fixed order by the last range);
+                              4 = multicast pairs: a 2-CTA cluster takes two vertically
+                              adjacent 128 x 256 tiles and loads each half of their shared
+                              256 rows of B once, multicast into both CTAs (m and n
+                              multiples of 256, else IFR_ERR_ARG), two accumulators.
+                              Variants 3 and 4 hold all 512 TMEM columns of an SM: solo
+                              use only, refused like variant 2.
                               Other kinds: 0. */
     int32_t reserved;
 } ifr_victim_cfg;

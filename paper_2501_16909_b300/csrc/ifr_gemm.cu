@@ -612,6 +612,233 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_pair_kernel(const _
     }
 }
 
+// ------------------------------------------------------------------ multicast pairs
+// Variant 4: a cluster of two CTAs on two SMs takes two vertically adjacent 128 x 256
+// tiles, (2p, n) and (2p + 1, n), which need the same 256 rows of B.  Each CTA
+// loads its own 128 rows of A and one half (128 rows) of B, the half multicast into
+// both CTAs' shared memory: 32 KiB of operands per SM per 64-wide K slice where a
+// lone CTA needs 48 KiB.  Each CTA then issues its own cta_group::1 MMAs (M = 128,
+// N = 256) into one of two 256-column accumulators and drains it with its own
+// epilogue, as variant 3 does.
+//   stage barriers  full[s]: one arrival (the CTA's own expect_tx of 48 KiB: its A,
+//                   its B half and the other CTA's); a B half may land before the
+//                   expect_tx of its phase (the pending arrival keeps the phase open);
+//                   empty[s]: two arrivals, both CTAs' MMA commits (multicast), since
+//                   a CTA's next copy into stage s also writes the other CTA's stage s
+//   scheduling      the leader claims units (tile pairs) and writes each into both
+//                   CTAs' rings, as the CTA-pair kernel does; the ring's release needs
+//                   both MMA threads, both CTAs' epilogue warps and the other producer
+// Bounded waits throughout; a final cluster barrier keeps each CTA resident until the
+// other has finished writing into its shared memory.
+template <int STAGES>
+struct McCfg {
+    static constexpr int A_BYTES = BM * BK * 2;        // 16 KiB
+    static constexpr int B_BYTES = 256 * BK * 2;       // 32 KiB (both halves)
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
+};
+
+template <int STAGES>
+__global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_mc_kernel(const __grid_constant__ CUtensorMap ta,
+                                                                       const __grid_constant__ CUtensorMap tb,
+                                                                       float *__restrict__ C, int M, int N, int K,
+                                                                       int group_m, DevTiming *tm) {
+    using Cf = McCfg<STAGES>;
+    constexpr int BN = 256, ACC = 2, CHUNKS = BN / 16;
+    constexpr uint16_t kBoth = 3;
+    extern __shared__ uint8_t g_smem_raw[];
+    uint8_t *base = (uint8_t *)(((uintptr_t)g_smem_raw + 1023u) & ~(uintptr_t)1023u);
+    uint64_t *full = (uint64_t *)(base + STAGES * Cf::STAGE);
+    uint64_t *empty = full + STAGES;
+    uint64_t *tfull = empty + STAGES;   // [ACC]
+    uint64_t *tempty = tfull + ACC;     // [ACC]
+    uint64_t *sfull = tempty + ACC;     // [RING], both CTAs
+    uint64_t *sempty = sfull + RING;    // [RING], leader
+    int32_t *ring = (int32_t *)(sempty + RING);
+    uint32_t *tmem_slot = (uint32_t *)(ring + RING);
+    volatile int *fail = (volatile int *)(tmem_slot + 1);
+
+    if (tc::cluster_nctarank() != 2) {
+        if (threadIdx.x == 0) tm->status = IFR_ERR_LAUNCH;
+        return;
+    }
+    const uint32_t rank = tc::cluster_ctarank();
+    const bool leader = rank == 0;
+    if (threadIdx.x == 0) g_stamp(tm, true);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles_m = M / BM, tiles_n = N / BN, n_units = (tiles_m / 2) * tiles_n;
+    const int KT = K / BK;
+    const uint64_t deadline = ifr_gtimer() + kGemmTimeoutNs;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 2);
+        }
+        for (int a = 0; a < ACC; ++a) {
+            tc::mbar_init(&tfull[a], 1);
+            tc::mbar_init(&tempty[a], EPI_WARPS);
+        }
+        for (int r = 0; r < RING; ++r) {
+            tc::mbar_init(&sfull[r], 1);
+            tc::mbar_init(&sempty[r], 2 + 1 + 2 * EPI_WARPS);  // two MMA threads, the other producer, 8 epilogue warps
+        }
+        *fail = 0;
+        tc::fence_mbar_init();
+        tc::prefetch_tmap(&ta);
+        tc::prefetch_tmap(&tb);
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tmem_slot, ACC * BN);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before();
+    tc::cluster_sync();  // both CTAs' barriers are initialised before any remote arrival or multicast
+    tc::fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        int64_t g = 0;
+        uint32_t next = blockIdx.x >> 1;  // leader: first unit = cluster index, later ones from the counter
+        for (int j = 0;; ++j) {
+            const int r = j % RING;
+            int unit;
+            if (leader) {
+                if (j >= RING && !tc::mbar_wait_cluster(&sempty[r], (uint32_t)((j / RING) - 1) & 1u, deadline))
+                    *fail = 1;
+                unit = (*fail || next >= (uint32_t)n_units) ? -1 : (int)next;
+                ring[r] = unit;
+                tc::st_remote_s32(tc::mapa(&ring[r], 1), unit);
+                tc::mbar_arrive(&sfull[r]);
+                tc::mbar_arrive_remote(tc::mapa(&sfull[r], 1));
+            } else {
+                const bool got = tc::mbar_wait_cluster(&sfull[r], (uint32_t)(j / RING) & 1u, deadline + 50000000ull);
+                unit = got ? ring[r] : -1;
+                if (!got) *fail = 1;
+                tc::mbar_arrive_remote(tc::mapa(&sempty[r], 0));
+            }
+            if (unit < 0) break;
+            int pm, tni;
+            tile_coords(unit, tiles_m / 2, tiles_n, group_m, pm, tni);
+            const int m0 = (2 * pm + (int)rank) * BM, n0 = tni * BN;
+            for (int kt = 0; kt < KT; ++kt, ++g) {
+                const int s = (int)(g % STAGES);
+                if (leader && kt == KT - 1) next = (gridDim.x >> 1) + atomicAdd(&tm->tile_next, 1u);
+                // both CTAs' MMAs must have finished with stage s: this copy writes both
+                if (g >= STAGES && !tc::mbar_wait_cluster(&empty[s], (uint32_t)((g / STAGES) - 1) & 1u, deadline)) {
+                    *fail = 1;
+                    break;
+                }
+                uint8_t *sa = base + s * Cf::STAGE;
+                tc::mbar_arrive_expect_tx(&full[s], (uint32_t)Cf::STAGE);
+                tc::tma_load_2d(sa, &ta, &full[s], kt * BK, m0);
+                tc::tma_load_2d_mc(sa + Cf::A_BYTES + rank * (Cf::B_BYTES / 2), &tb, &full[s], kt * BK,
+                                   n0 + (int)rank * (BN / 2), kBoth);
+            }
+        }
+        // this CTA's own stages have landed (the other CTA's copies into it are covered
+        // by the final cluster barrier, after its MMAs waited for them)
+        for (int64_t q = g - STAGES < 0 ? 0 : g - STAGES; q < g; ++q)
+            tc::mbar_wait(&full[q % STAGES], (uint32_t)(q / STAGES) & 1u, deadline + 100000000ull);
+    } else if (warp == 1 && lane == 0) {
+        constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+        int64_t g = 0;
+        for (int j = 0;; ++j) {
+            const int r = j % RING;
+            const bool got = tc::mbar_wait_cluster(&sfull[r], (uint32_t)(j / RING) & 1u, deadline + 50000000ull);
+            const int unit = got ? ring[r] : -1;
+            tc::mbar_arrive_remote(tc::mapa(&sempty[r], 0));
+            if (!got) *fail = 1;
+            if (unit < 0) break;
+            const int a = j % ACC;
+            if (j >= ACC && !tc::mbar_wait(&tempty[a], (uint32_t)((j / ACC) - 1) & 1u, deadline)) {
+                *fail = 1;
+                tc::mma_commit(&tfull[a]);
+                continue;
+            }
+            tc::fence_after();
+            const uint32_t acc_cols = tmem + (uint32_t)(a * BN);
+            for (int kt = 0; kt < KT; ++kt, ++g) {
+                const int s = (int)(g % STAGES);
+                if (!tc::mbar_wait(&full[s], (uint32_t)(g / STAGES) & 1u, deadline)) {
+                    *fail = 1;
+                    break;
+                }
+                tc::fence_after();
+                const uint32_t sa = tc::smem_u32(base + s * Cf::STAGE);
+                const uint64_t adesc = tc::desc_sw128(sa);
+                const uint64_t bdesc = tc::desc_sw128(sa + Cf::A_BYTES);
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk)
+                    tc::mma_bf16(acc_cols, adesc + 2ull * kk, bdesc + 2ull * kk, idesc, (uint32_t)((kt | kk) != 0));
+                tc::mma_commit_mc(&empty[s], kBoth);
+            }
+            tc::mma_commit(&tfull[a]);
+        }
+    } else if (warp >= 2) {
+        const int q = warp & 3;
+        for (int j = 0;; ++j) {
+            const int r = j % RING;
+            const bool got = tc::mbar_wait_cluster(&sfull[r], (uint32_t)(j / RING) & 1u, deadline + 50000000ull);
+            const int unit = got ? ring[r] : -1;
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive_remote(tc::mapa(&sempty[r], 0));
+            if (!__all_sync(0xffffffffu, got)) {
+                if (lane == 0) *fail = 1;
+                break;
+            }
+            if (unit < 0) break;
+            const int a = j % ACC;
+            const bool ok = tc::mbar_wait(&tfull[a], (uint32_t)(j / ACC) & 1u, deadline + 100000000ull);
+            tc::fence_after();
+            if (!__all_sync(0xffffffffu, ok && !*fail)) {
+                if (lane == 0) *fail = 1;
+                break;
+            }
+            int pm, tni;
+            tile_coords(unit, tiles_m / 2, tiles_n, group_m, pm, tni);
+            const int m0 = (2 * pm + (int)rank) * BM, n0 = tni * BN;
+            const uint32_t trow = tmem + (uint32_t)(a * BN) + ((uint32_t)(q * 32) << 16);
+            float *crow = C + (size_t)(m0 + q * 32 + lane) * (size_t)N + n0;
+            uint32_t ra[16], rb[16];
+            tc::tmem_ld16(trow, ra);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int c = 0; c < CHUNKS; c += 2) {
+                tc::tmem_ld16(trow + (uint32_t)((c + 1) * 16), rb);
+                store_row16(crow + c * 16, ra);
+                tc::tmem_ld_wait();
+                if (c + 2 < CHUNKS) {
+                    tc::tmem_ld16(trow + (uint32_t)((c + 2) * 16), ra);
+                    store_row16(crow + (c + 1) * 16, rb);
+                    tc::tmem_ld_wait();
+                } else {
+                    tc::fence_before();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&tempty[a]);
+                    store_row16(crow + (c + 1) * 16, rb);
+                }
+            }
+            if (warp == 2 && lane == 0) g_stamp(tm, false);
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::cluster_sync();  // every multicast and remote arrival into this CTA has landed
+    if (warp == 1) {
+        tc::fence_after();
+        tc::tmem_dealloc(tmem, ACC * BN);
+    }
+    if (threadIdx.x == 0 && *fail) tm->status = IFR_ERR_TIMEOUT;
+    g_exit(tm);
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&tm->tile_done, 1u) == gridDim.x - 1u) {
+            atomicExch(&tm->tile_next, 0u);
+            atomicExch(&tm->tile_done, 0u);
+        }
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -800,6 +1027,75 @@ int launch_gemm_pair(const ifr_victim_cfg *c, cudaStream_t stream, int group_m, 
     return e == cudaSuccess ? IFR_OK : IFR_ERR_LAUNCH;
 }
 
+template <int ST>
+const void *gemm_mc_fn() {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(gemm_bf16_mc_kernel<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, McCfg<ST>::SMEM);
+        attr = true;
+    }
+    return (const void *)gemm_bf16_mc_kernel<ST>;
+}
+
+template <int ST>
+void mc_launch_cfg(cudaLaunchConfig_t *cfg, cudaLaunchAttribute *at, int grid, cudaStream_t stream) {
+    memset(cfg, 0, sizeof(*cfg));
+    memset(at, 0, sizeof(*at));
+    cfg->gridDim = dim3((unsigned)grid);
+    cfg->blockDim = dim3(GEMM_THREADS);
+    cfg->dynamicSmemBytes = McCfg<ST>::SMEM;
+    cfg->stream = stream;
+    at->id = cudaLaunchAttributeClusterDimension;
+    at->val.clusterDim.x = 2;
+    at->val.clusterDim.y = 1;
+    at->val.clusterDim.z = 1;
+    cfg->attrs = at;
+    cfg->numAttrs = 1;
+}
+
+// Clusters of the multicast kernel the device holds at once, asked once.
+template <int ST>
+int mc_clusters() {
+    static int n = 0;
+    if (n == 0) {
+        ifr_carveout(gemm_mc_fn<ST>());
+        cudaLaunchConfig_t cfg;
+        cudaLaunchAttribute at;
+        mc_launch_cfg<ST>(&cfg, &at, 2 * (g_num_sms / 2), nullptr);
+        int c = 0;
+        if (cudaOccupancyMaxActiveClusters(&c, gemm_bf16_mc_kernel<ST>, &cfg) != cudaSuccess || c <= 0) {
+            cudaGetLastError();
+            c = g_num_sms / 2;
+        }
+        n = c < g_num_sms / 2 ? c : g_num_sms / 2;
+    }
+    return n;
+}
+
+template <int ST>
+int mc_grid(const ifr_victim_cfg *c) {
+    const int units = (int)((c->m / 256) * (c->n / 256));
+    const int cl = mc_clusters<ST>();
+    return 2 * (units < cl ? units : cl);
+}
+
+template <int ST>
+int launch_gemm_mc(const ifr_victim_cfg *c, cudaStream_t stream, int group_m, DevTiming *tm) {
+    gemm_mc_fn<ST>();
+    CUtensorMap ta, tb;
+    int rc = make_map(&ta, c->in0, c->m, c->k, BM);
+    if (rc) return rc;
+    rc = make_map(&tb, c->in1, c->n, c->k, 128);  // one half of a 256-row B panel per copy
+    if (rc) return rc;
+    ifr_carveout(gemm_mc_fn<ST>());
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute at;
+    mc_launch_cfg<ST>(&cfg, &at, mc_grid<ST>(c), stream);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, gemm_bf16_mc_kernel<ST>, ta, tb, (float *)c->out, (int)c->m,
+                                             (int)c->n, (int)c->k, group_m, tm);
+    return e == cudaSuccess ? IFR_OK : IFR_ERR_LAUNCH;
+}
+
 }  // namespace
 
 int ifr_gemm_shape(const ifr_victim_cfg *c, VictimShape *s) {
@@ -813,6 +1109,13 @@ int ifr_gemm_shape(const ifr_victim_cfg *c, VictimShape *s) {
         s->grid = pair_grid<4>(c);
         s->smem = PairCfg<4>::SMEM;
         s->tmem_cols = PAIR_N;
+        return IFR_OK;
+    }
+    if (c->variant == 4) {
+        s->fn = gemm_mc_fn<4>();
+        s->grid = mc_grid<4>(c);
+        s->smem = McCfg<4>::SMEM;
+        s->tmem_cols = 512;
         return IFR_OK;
     }
     const bool wide = c->n % 256 == 0;
@@ -843,6 +1146,7 @@ int ifr_gemm_enqueue(ifr_ctx *ctx, const ifr_victim_cfg *c, cudaStream_t stream,
     const double operand_bytes = 2.0 * ((double)c->m + (double)c->n) * (double)c->k;
     const int gm = operand_bytes > (double)ctx->info.l2_bytes ? GROUP_M : 1;
     if (c->variant == 2) return launch_gemm_pair<4>(c, stream, gm, tm);
+    if (c->variant == 4) return launch_gemm_mc<4>(c, stream, gm, tm);
     const bool wide = c->n % 256 == 0;
     if (c->variant == 3)
         return wide ? launch_gemm<256, 4, 2>(ctx, c, stream, gm, true, tm)
@@ -861,7 +1165,7 @@ void ifr_gemm_forget_split(ifr_ctx *ctx) { ctx->gemm_cnt_key = -1; }
 
 int ifr_preload_gemm() {
     const void *fns[] = {gemm_fn<128, 3, 1>(), gemm_fn<256, 3, 1>(), gemm_fn<128, 4, 1>(), gemm_fn<256, 4, 1>(),
-                         gemm_fn<128, 4, 2>(), gemm_fn<256, 4, 2>(), gemm_pair_fn<4>()};
+                         gemm_fn<128, 4, 2>(), gemm_fn<256, 4, 2>(), gemm_pair_fn<4>(), gemm_mc_fn<4>()};
     for (const void *f : fns) {
         int rc = ifr_preload(f);
         if (rc) return rc;

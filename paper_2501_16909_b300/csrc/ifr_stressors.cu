@@ -23,7 +23,7 @@
 
 namespace {
 
-constexpr int kStreamChunksPerRound = 4;  // L2/HBM: chunks per round
+constexpr int kStreamChunksPerRound = 8;  // L2/HBM: chunks per round (8 x 4 loads in flight per thread)
 // FMA: steps per chain per round = kFmaWork / ILP (16384 FMAs per thread per round)
 constexpr int kFmaWork = 16384;
 // FP64: steps per chain per round = kFp64Work / ILP (1024 multiplies per thread per round)
@@ -229,8 +229,13 @@ __global__ void __launch_bounds__(1024) stream_stress_kernel(DevStress *st, Stre
     const int64_t A = p.planned;
     const int64_t k = c.k;
     const int vpc = (int)blockDim.x * 4;  // int4 per chunk
-    int64_t cpos = k, pass = 0, done = 0;
-    uint32_t acc = 0u;
+    // the thread's first int4 of the current chunk, advanced by the stride of A chunks
+    // (no multiply per chunk), and where the block's cycle of chunks starts again
+    const int4 *const first = p.buf + k * vpc + threadIdx.x;
+    const int64_t stride = A * vpc, last = p.n_chunks - A;  // cpos >= last: the next chunk wraps
+    const int4 *src = first;
+    int64_t cpos = k, done = 0;
+    uint32_t pass = 0u, acc = 0u;
     int64_t round = 0;
     const bool has_work = k < p.n_chunks;
     for (;; ++round) {
@@ -238,22 +243,24 @@ __global__ void __launch_bounds__(1024) stream_stress_kernel(DevStress *st, Stre
         __syncthreads();
         if (!s_go[round & 1]) break;
         int4 v[kStreamChunksPerRound][4];
-        int64_t ps[kStreamChunksPerRound];
+        uint32_t ps[kStreamChunksPerRound];
 #pragma unroll
         for (int r = 0; r < kStreamChunksPerRound; ++r) {
-            const int4 *src = p.buf + cpos * vpc + threadIdx.x;
 #pragma unroll
             for (int u = 0; u < 4; ++u) v[r][u] = ld_stream(src + u * blockDim.x);
             ps[r] = pass;
-            cpos += A;
-            if (cpos >= p.n_chunks) {
+            if (cpos >= last) {
                 cpos = k;
+                src = first;
                 ++pass;
+            } else {
+                cpos += A;
+                src += stride;
             }
         }
 #pragma unroll
         for (int r = 0; r < kStreamChunksPerRound; ++r)
-            acc ^= ifr_rotl((uint32_t)(v[r][0].x ^ v[r][1].x ^ v[r][2].x ^ v[r][3].x), (uint32_t)ps[r]);
+            acc ^= ifr_rotl((uint32_t)(v[r][0].x ^ v[r][1].x ^ v[r][2].x ^ v[r][3].x), ps[r]);
         done += kStreamChunksPerRound;
     }
     uint32_t cs = ifr_block_xor(acc, s_red);

@@ -181,11 +181,11 @@ double per_launch_ratio(const ifr_timing &co, const ifr_timing &solo) {
 }
 
 // The CTA-pair GEMM (variant 2) allocates the same TMEM columns on two SMs at once,
-// and the two-accumulator GEMM (variant 3) all 512 columns of an SM; beside other
+// and the two-accumulator GEMMs (variants 3, 4) all 512 columns of an SM; beside other
 // TMEM users (the tensor stressor, another GEMM) those allocations can wait until
 // they exit, so the measurements that colocate kernels refuse both.
 int colocatable(const ifr_victim_cfg *c) {
-    return (c->kind == IFR_V_GEMM && (c->variant == 2 || c->variant == 3)) ? IFR_ERR_ARG : IFR_OK;
+    return (c->kind == IFR_V_GEMM && c->variant >= 2) ? IFR_ERR_ARG : IFR_OK;
 }
 
 }  // namespace

@@ -232,6 +232,27 @@ __device__ __forceinline__ void mma_commit_pair(uint64_t *bar, uint16_t cta_mask
         : "memory");
 }
 
+// ---------------------------------------------------------------- multicast (cta_group::1)
+// TMA tile load whose bytes land at `dst`'s offset in every CTA of `cta_mask` and
+// complete on the mbarrier at `bar`'s offset in each of them.
+__device__ __forceinline__ void tma_load_2d_mc(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y,
+                                               uint16_t cta_mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster "
+        "[%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y), "h"(cta_mask)
+        : "memory");
+}
+// Arrive once on the mbarrier at `bar`'s offset in every CTA of `cta_mask` when all
+// previously issued (cta_group::1) MMAs of this thread complete.
+__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t cta_mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"(cta_mask)
+        : "memory");
+}
+
 // Byte offset of bf16 element (row, col) in a K-major 128-byte-swizzled tile
 // (64 columns per row, tile 1024-B aligned): the 16-byte chunk index is XORed
 // with the row index modulo 8.

@@ -497,7 +497,7 @@ void ifr_timing_to_host(const DevTiming &d, int repeats, ifr_timing *out) {
 int ifr_victim_validate(ifr_ctx *ctx, const ifr_victim_cfg *c) {
     if (!c || c->kind < 0 || c->kind >= IFR_V_COUNT || c->repeats < 0 || c->grid < 0 || c->block < 0) return IFR_ERR_ARG;
     if (!c->in0 || !c->out) return IFR_ERR_ARG;
-    if (c->variant < 0 || c->variant > 3 || (c->kind != IFR_V_GEMM && c->variant != 0)) return IFR_ERR_ARG;
+    if (c->variant < 0 || c->variant > 4 || (c->kind != IFR_V_GEMM && c->variant != 0)) return IFR_ERR_ARG;
     switch (c->kind) {
         case IFR_V_TRIAD:
             if (!c->in1 || c->n <= 0 || !aligned16(c->in0) || !aligned16(c->in1) || !aligned16(c->out)) return IFR_ERR_ARG;
@@ -517,7 +517,8 @@ int ifr_victim_validate(ifr_ctx *ctx, const ifr_victim_cfg *c) {
         case IFR_V_GEMM:
             if (!c->in1 || c->m <= 0 || c->n <= 0 || c->k <= 0) return IFR_ERR_ARG;
             if (c->m % 128 || c->n % 128 || c->k % 64) return IFR_ERR_ARG;
-            if (c->variant == 2 && (c->m % 256 || c->n % 256)) return IFR_ERR_ARG;  // 256 x 256 pair tiles
+            if ((c->variant == 2 || c->variant == 4) && (c->m % 256 || c->n % 256))
+                return IFR_ERR_ARG;  // 256 x 256 pair tiles / pairs of 128 x 256 tiles
             if (!aligned16(c->in0) || !aligned16(c->in1) || !aligned16(c->out)) return IFR_ERR_ARG;
             return IFR_OK;
         default: return IFR_ERR_ARG;

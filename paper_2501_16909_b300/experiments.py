@@ -282,7 +282,7 @@ def _l2_sizes(ctx, repeats, S, half, ids_a, ids_b, green):
     out = []
     for mib in sizes_mib:
         nb = mib * MiB
-        per_round = half * 4 * 16 * 1024  # 4 chunks of 16 B x 1024 threads per block per round
+        per_round = half * P.STREAM_CHUNKS_PER_ROUND * 64 * 1024  # bytes of `half` 1024-thread blocks per round
         rounds = max(256, math.ceil(8 * nb / per_round))
         if green:
             a = stressor_cfg(A.IFR_S_L2, sm_count=green[0], blocks_per_sm=1, block=1024, buf=buf_a,
@@ -295,7 +295,7 @@ def _l2_sizes(ctx, repeats, S, half, ids_a, ids_b, green):
             b = with_mask(stressor_cfg(A.IFR_S_L2, blocks_per_sm=1, block=1024, buf=buf_b, working_set_bytes=nb,
                                        seed=2, max_rounds=rounds), ids_b)
         pr = run_pair(ctx, a, b, repeats)
-        bytes_a = half * rounds * 4 * 16 * 1024
+        bytes_a = half * rounds * P.STREAM_CHUNKS_PER_ROUND * 64 * 1024
         out.append({"mib_per_instance": mib, "rounds": rounds, "slowdown_a": round(pr["slowdown_a"], 3),
                     "slowdown_b": round(pr["slowdown_b"], 3),
                     "solo_a_gbs": round(bytes_a / (pr["solo_a_us"] * 1e3), 1),

@@ -27,8 +27,10 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 TILE_MMA_FLOP = 2 * 128 * 128 * 64
 UNIT = {A.IFR_S_HBM: "B", A.IFR_S_L2: "B", A.IFR_S_FMA: "flop", A.IFR_S_TENSOR: "flop", A.IFR_S_SMEM_CF: "wavefront",
         A.IFR_S_SMEM_32W: "wavefront", A.IFR_S_SCHED: "block", A.IFR_S_FP64: "flop", A.IFR_S_SLEEP: "round"}
+# chunks (block x 64 bytes each) an L2 / HBM stream block reads per round
+STREAM_CHUNKS_PER_ROUND = 8
 # fixed-work rounds of one calibration run per kind (about a millisecond at full SMs)
-CAL_ROUNDS = {A.IFR_S_HBM: 64, A.IFR_S_L2: 256, A.IFR_S_FMA: 32, A.IFR_S_TENSOR: 32, A.IFR_S_SMEM_CF: 16,
+CAL_ROUNDS = {A.IFR_S_HBM: 32, A.IFR_S_L2: 128, A.IFR_S_FMA: 32, A.IFR_S_TENSOR: 32, A.IFR_S_SMEM_CF: 16,
               A.IFR_S_SMEM_32W: 32, A.IFR_S_SCHED: 0, A.IFR_S_FP64: 16, A.IFR_S_SLEEP: 10}
 
 

@@ -48,9 +48,9 @@ def hbm_buf():
 def _cases(ctx, hbm_buf):
     S = ctx.info["num_sms"]
     return {
-        # full SMs, 2 blocks of 512 per SM, 1 GiB set: a round is 4 chunks of 32 KiB per block
+        # full SMs, 2 blocks of 512 per SM, 1 GiB set: a round is 8 chunks of 32 KiB per block
         "hbm": ifr.stressor_cfg(A.IFR_S_HBM, sm_count=S, blocks_per_sm=2, block=512, buf=hbm_buf,
-                                working_set_bytes=1 << 30, max_rounds=128, seed=0),
+                                working_set_bytes=1 << 30, max_rounds=64, seed=0),
         # 16 SMs, one warp of 4 chains each (the oracle recomputes every chain of every block)
         "fma": ifr.stressor_cfg(A.IFR_S_FMA, sm_count=16, blocks_per_sm=1, block=32, ilp=4, max_rounds=64, seed=7),
         # full SMs, 2 blocks of 256 per SM, conflict-free
@@ -67,7 +67,7 @@ def _check_blocks(ctx, name, cfg, logs, hbuf):
         assert L["status"] == 0 and L["rounds"] == cfg.max_rounds, L
         if name == "hbm":
             assert L["checksum"] == oracle.stream_block_checksum(hbuf, cfg.block * 16, planned, L["index"], L["work"])
-            assert L["work"] == 4 * cfg.max_rounds
+            assert L["work"] == P.STREAM_CHUNKS_PER_ROUND * cfg.max_rounds
         elif name == "fma":
             steps = 16384 // cfg.ilp
             r0, fin = oracle.fma_block(cfg.seed, L["index"], cfg.block, cfg.ilp, steps, cfg.max_rounds)

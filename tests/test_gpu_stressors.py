@@ -9,6 +9,7 @@ import ifr_inputs as I
 import oracle
 import paper_2501_16909_b300 as ifr
 from paper_2501_16909_b300 import _abi as A
+from paper_2501_16909_b300 import peaks as P
 from tests.gpu_common import need_gpu, spread_mask
 
 pytestmark = pytest.mark.gpu
@@ -53,7 +54,7 @@ def _stream_check(ctx, kind, nbytes, block, bps, sm_count, rounds=0, stop_after_
         assert L["checksum"] == want, L
         if rounds:
             n_chunks = n // chunk
-            exp = 4 * rounds if L["index"] < n_chunks else 0
+            exp = P.STREAM_CHUNKS_PER_ROUND * rounds if L["index"] < n_chunks else 0
             assert L["work"] == exp
     xor = 0
     for L in logs:

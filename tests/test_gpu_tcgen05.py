@@ -55,6 +55,15 @@ def test_gemm_pair_tiles_all_entries(ctx, M, N, K):
     test_gemm_small_all_entries(ctx, M, N, K, 2)
 
 
+# variant 4: pairs of vertically adjacent 128 x 256 tiles sharing B through TMA
+# multicast; (2048, 2560) is 80 tile pairs for at most 74 clusters, so pairs also come
+# from the device counter; three launches reuse the counter
+@pytest.mark.parametrize("M,N,K", [(256, 256, 64), (256, 512, 128), (512, 768, 192), (768, 256, 1024),
+                                   (2048, 2560, 128), (8192, 512, 64)])
+def test_gemm_multicast_pairs_all_entries(ctx, M, N, K):
+    test_gemm_small_all_entries(ctx, M, N, K, 4, repeats=3)
+
+
 # variant 3 with split last waves (a part must run at least 32 K slices of 64): 72
 # tiles of 128 x 256 in 2 K parts (one wave of 144 units), 6 tiles in 4 parts, and
 # 320 tiles = 296 whole + 24 in 2 parts; three launches each, so the arrival counters
@@ -80,7 +89,7 @@ def test_gemm_two_accumulators_split_wave(ctx, M, N, K):
     assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref)
 
 
-@pytest.mark.parametrize("variant", [0, 2, 3])
+@pytest.mark.parametrize("variant", [0, 2, 3, 4])
 def test_gemm_full_size_sampled_vs_oracle(ctx, variant):
     M = N = K = 4096
     Ab, Bb, C, t = _gemm(ctx, M, N, K, seed=21, repeats=2, variant=variant)
@@ -111,7 +120,10 @@ def test_gemm_variant_profiles_and_bad_variant(ctx):
     assert p2["dynamic_smem"] == 4 * 2 * 128 * 64 * 2 + 1024 + 256 < p0["dynamic_smem"]
     assert p2["tmem_cols"] == 256 and p2["grid"] == 2
     assert max(p["regs_per_thread"] for p in (p0, p1, p2)) <= 96
-    for bad in (ifr.victim_cfg(A.IFR_V_GEMM, Ab, Ab, C, m=256, n=256, k=256, variant=4),
+    p4 = ctx.victim_profile(ifr.victim_cfg(A.IFR_V_GEMM, Ab, Ab, C, m=256, n=256, k=256, variant=4))
+    assert p4["tmem_cols"] == 512 and p4["grid"] == 2 and p4["dynamic_smem"] == p1["dynamic_smem"]
+    for bad in (ifr.victim_cfg(A.IFR_V_GEMM, Ab, Ab, C, m=256, n=256, k=256, variant=5),
+                ifr.victim_cfg(A.IFR_V_GEMM, Ab, Ab, C, m=128, n=256, k=256, variant=4),
                 ifr.victim_cfg(A.IFR_V_GEMM, Ab, Ab, C, m=128, n=256, k=256, variant=2),
                 ifr.victim_cfg(A.IFR_V_GEMM, Ab, Ab, C, m=256, n=384, k=256, variant=2),
                 ifr.victim_cfg(A.IFR_V_SOFTMAX, C, None, C, m=256, n=256, variant=1)):
@@ -119,7 +131,7 @@ def test_gemm_variant_profiles_and_bad_variant(ctx):
             ctx.victim_launch(bad)
 
 
-@pytest.mark.parametrize("solo_variant", [2, 3])
+@pytest.mark.parametrize("solo_variant", [2, 3, 4])
 def test_pair_gemm_refused_where_kernels_are_colocated(ctx, solo_variant):
     # the CTA pair's TMEM allocation, and the two-accumulator kernel's 512 columns, can
     # wait on other TMEM users: solo launches only
