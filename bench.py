@@ -86,8 +86,29 @@ class ClockSampler:
 
 # DRAM bytes (read + write) per launch of the roofline kernels from ncu captures of
 # the same launch shape, each with the SHA-256 of the kernel's source file at capture
-# time; when that file has changed since, the line reports null instead.
-NCU_DRAM_BYTES = {}
+# time; when that file has changed since, the line reports null instead.  Captured
+# with `ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
+# --clock-control none -k regex:<kernel> -c 1 python -m paper_2501_16909_b300.profile_case
+# <case>` (cases sched, fma, tensor, smem_cf, smem_32w, l2, hbm, `hbm --staging 1`,
+# `gemm --variant {0,2,3}`), after the same command ran clean; the stressors' shapes
+# and rounds are those of the solo runs below, the GEMM is the same 4096^3 launch.
+_GEMM_SRC = ("paper_2501_16909_b300/csrc/ifr_gemm.cu",
+             "e8b0c478e88782980fd46b3cd6ed4a1c2b0fd706db922701469cbc383f46822a")
+_STRESS_SRC = ("paper_2501_16909_b300/csrc/ifr_stressors.cu",
+               "dce4f69d115e9b98123961bd203ed8d2d2e6c22f193b96840584b799198284e7")
+NCU_DRAM_BYTES = {
+    "sched": (4864 + 0,) + _STRESS_SRC,
+    "fma": (20992 + 0,) + _STRESS_SRC,
+    "tensor": (47360 + 0,) + _STRESS_SRC,
+    "smem_cf": (29184 + 0,) + _STRESS_SRC,
+    "smem_32w": (18432 + 0,) + _STRESS_SRC,
+    "l2": (16794880 + 0,) + _STRESS_SRC,
+    "hbm": (2483068416 + 2992640,) + _STRESS_SRC,
+    "hbm_tma": (2502674688 + 3000576,) + _STRESS_SRC,
+    "gemm": (77078016 + 35707648,) + _GEMM_SRC,
+    "gemm_v2": (75990528 + 40968448,) + _GEMM_SRC,
+    "gemm_v3": (77721344 + 41471488,) + _GEMM_SRC,
+}
 
 
 def _src_sha(rel):
@@ -706,9 +727,9 @@ def _full_stressor_levels(S, bufs):
 def solo_kernel_rooflines(ctx, bufs, pk):
     """Untimed solo measurements behind the roofline objects: every stressor kind at
     all SMs (fixed work, CUDA events on the stressor stream), the HBM stressor with
-    both load paths, and the BF16 GEMM at 4096^3 in its sweep variant (0) and its
-    throughput variant (3), 20 launches each after 3 warm ones (CUDA events on the
-    victim stream)."""
+    both load paths, and the BF16 GEMM at 4096^3 in its sweep variant (0), its CTA-pair
+    throughput variant (2) and its single-CTA two-accumulator variant (3), 20 launches
+    each after 3 warm ones (CUDA events on the victim stream)."""
     import torch
 
     import ifr_inputs as I
@@ -734,7 +755,7 @@ def solo_kernel_rooflines(ctx, bufs, pk):
     ga = I.torch_normal_bf16(11, G * G, "cuda").view(G, G)
     gb = I.torch_normal_bf16(12, G * G, "cuda").view(G, G)
     gc = torch.empty(G, G, device="cuda")
-    for var in (0, 3):
+    for var in (0, 2, 3):
         cfg = ifr.victim_cfg(A.IFR_V_GEMM, ga, gb, gc, m=G, n=G, k=G, repeats=3, variant=var)
         ctx.victim_launch(cfg)
         cfg.repeats = 20
@@ -865,14 +886,20 @@ def run_config3(args):
                     "tma_staging": {"achieved": round(solo["stressors"]["hbm_tma"]["rate"] / 1e9, 1),
                                     "frac": round(solo["stressors"]["hbm_tma"]["frac"], 4),
                                     "traffic": ncu_traffic("hbm_tma")}}
-    g0, g3 = solo["gemm"][0], solo["gemm"][3]
+    g0, g2, g3 = solo["gemm"][0], solo["gemm"][2], solo["gemm"][3]
     roofline_gemm = {"bound": "tensor", "achieved": round(g0["tflops"], 1), "peak": mp["bf16_tflops"],
                      "unit": "TFLOP/s", "frac": round(g0["tflops"] / mp["bf16_tflops"], 4),
                      "traffic": ncu_traffic("gemm"),
                      "kernel": "gemm_bf16_kernel<256, 3, 1> (variant 0, the sweeps' GEMM: BF16 4096^3, persistent, "
                                "%d CTAs; 20 solo launches)" % g0["grid"],
                      "peak_source": "MEASURED_PEAKS bf16_tflops (%s, burst)" % msrc,
-                     "throughput_variant": {"variant": 3, "achieved": round(g3["tflops"], 1),
+                     "throughput_variant": {"variant": 2, "achieved": round(g2["tflops"], 1),
+                                            "frac": round(g2["tflops"] / mp["bf16_tflops"], 4),
+                                            "traffic": ncu_traffic("gemm_v2"),
+                                            "kernel": "gemm_bf16_pair_kernel<6, 2, split> (256 x 256 tiles on CTA "
+                                                      "pairs, two TMEM accumulators, split last wave; %d CTAs)"
+                                                      % g2["grid"]},
+                     "single_cta_variant": {"variant": 3, "achieved": round(g3["tflops"], 1),
                                             "frac": round(g3["tflops"] / mp["bf16_tflops"], 4),
                                             "traffic": ncu_traffic("gemm_v3"),
                                             "kernel": "gemm_bf16_kernel<256, 4, 2> (two TMEM accumulators, split "

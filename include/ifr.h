@@ -253,14 +253,16 @@ typedef struct {
                               memory: leaves room for a stressor block, Sec. 5.3),
                               1 = throughput (4 stages, 193 KiB: more operand bytes in
                               flight, but no shared-memory stressor block fits beside it),
-                              2 = CTA pairs (a 2-CTA cluster per 256 x 256 tile with
-                              tcgen05 cta_group::2, 4 stages of 32 KiB per SM, 129 KiB;
-                              m and n multiples of 256, else IFR_ERR_ARG).  The pair's
-                              TMEM allocation needs the same 256 columns free on both
-                              SMs: beside other TMEM users (the tensor stressor) it can
-                              wait until they exit, so it is for solo use
-                              (ifr_victim_launch); ifr_sweep, ifr_corun and ifr_colocate
-                              refuse it with IFR_ERR_ARG.
+                              2 = CTA pairs, the fastest variant (a 2-CTA cluster per
+                              256 x 256 tile with tcgen05 cta_group::2, 6 stages of 32
+                              KiB per SM, 193 KiB; two 256-column accumulators per SM;
+                              the split last wave of variant 3 over pair tiles, with K
+                              ranges of at least 2048; m and n multiples of 256, else
+                              IFR_ERR_ARG).  The pair's TMEM allocation needs the same
+                              512 columns free on both SMs: beside other TMEM users (the
+                              tensor stressor) it can wait until they exit, so it is for
+                              solo use (ifr_victim_launch); ifr_sweep, ifr_corun and
+                              ifr_colocate refuse it with IFR_ERR_ARG.
                               3 = throughput, two accumulators: variant 1 (4 stages) with
                               two 256-column TMEM accumulators, so the next tile's MMAs
                               overlap the epilogue, and, when the tiles leave the last wave

@@ -136,6 +136,55 @@ __device__ __forceinline__ void store_row16(float *dst, const uint32_t (&r)[16])
                            __uint_as_float(r[4 * e + 3]));
 }
 
+// One epilogue warp's 32 rows of a split tile are in this part's slot: count the
+// part on the (tile, warp) counter; the last part to arrive adds the 32 rows of every
+// slot in part order and stores them to C.  Coalesced: the warp walks its rows four
+// at a time with the lanes across the columns (BN / 128 float4 per lane per row), the
+// loads of the four rows of all parts in flight together.  slot0: row 0 of part 0;
+// part_stride: floats from one part's slot to the next.
+template <int BN>
+__device__ __forceinline__ void split_arrive_reduce(const GemmSplit &sp, uint32_t *cnt, const float *slot0,
+                                                    size_t part_stride, float *cq, int N, int lane) {
+    __threadfence();
+    __syncwarp();
+    uint32_t prev = 0;
+    if (lane == 0) prev = atomicAdd(cnt, 1u);
+    prev = __shfl_sync(0xffffffffu, prev, 0);
+    if ((prev + 1u) % (uint32_t)sp.parts != 0u) return;
+    __threadfence();
+    constexpr int H = BN / 128;
+#pragma unroll 1
+    for (int r0 = 0; r0 < 32; r0 += 4) {
+        float4 t[4][H];
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+            for (int h = 0; h < H; ++h) t[rr][h] = __ldcg((const float4 *)(slot0 + (size_t)(r0 + rr) * BN) + lane + 32 * h);
+#pragma unroll 1
+        for (int pp = 1; pp < sp.parts; ++pp) {
+            const float *sl = slot0 + (size_t)pp * part_stride;
+            float4 u[4][H];
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+                for (int h = 0; h < H; ++h) u[rr][h] = __ldcg((const float4 *)(sl + (size_t)(r0 + rr) * BN) + lane + 32 * h);
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
+                    t[rr][h].x += u[rr][h].x;
+                    t[rr][h].y += u[rr][h].y;
+                    t[rr][h].z += u[rr][h].z;
+                    t[rr][h].w += u[rr][h].w;
+                }
+        }
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+            for (int h = 0; h < H; ++h) ((float4 *)(cq + (size_t)(r0 + rr) * N))[lane + 32 * h] = t[rr][h];
+    }
+}
+
 // ACC accumulators of BN TMEM columns: with two, the MMAs of the next unit run into
 // one while the epilogue drains the other (variant 3, for solo use: 512 columns
 // leave no TMEM for other kernels on the SM).  SPLIT compiles the split last wave
@@ -312,57 +361,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_kernel(const __grid
                     store_row16(crow + (c + 1) * 16, rb);
                 }
             }
-            if (SPLIT && fix >= 0) {
-                // this part's rows are in its slot: count it; the last part of the
-                // (tile, warp) adds every slot in part order and stores C
-                __threadfence();
-                __syncwarp();
-                uint32_t prev = 0;
-                if (lane == 0) prev = atomicAdd(&sp.cnt[fix * EPI_WARPS + q], 1u);
-                prev = __shfl_sync(0xffffffffu, prev, 0);
-                if ((prev + 1u) % (uint32_t)sp.parts == 0u) {
-                    // coalesced: the warp walks its 32 rows four at a time, lanes across
-                    // the columns (BN / 128 float4 per lane per row), every load of the
-                    // four rows of all parts in flight together
-                    __threadfence();
-                    constexpr int H = BN / 128;
-                    const float *slot0 = sp.ws + ((size_t)fix * sp.parts * BM + (size_t)(q * 32)) * BN;
-                    float *cq = C + (size_t)(m0 + q * 32) * (size_t)N + n0;
-#pragma unroll 1
-                    for (int r0 = 0; r0 < 32; r0 += 4) {
-                        float4 t[4][H];
-#pragma unroll
-                        for (int rr = 0; rr < 4; ++rr)
-#pragma unroll
-                            for (int h = 0; h < H; ++h)
-                                t[rr][h] = __ldcg((const float4 *)(slot0 + (size_t)(r0 + rr) * BN) + lane + 32 * h);
-#pragma unroll 1
-                        for (int pp = 1; pp < sp.parts; ++pp) {
-                            const float *sl = slot0 + (size_t)pp * BM * BN;
-                            float4 u[4][H];
-#pragma unroll
-                            for (int rr = 0; rr < 4; ++rr)
-#pragma unroll
-                                for (int h = 0; h < H; ++h)
-                                    u[rr][h] = __ldcg((const float4 *)(sl + (size_t)(r0 + rr) * BN) + lane + 32 * h);
-#pragma unroll
-                            for (int rr = 0; rr < 4; ++rr)
-#pragma unroll
-                                for (int h = 0; h < H; ++h) {
-                                    t[rr][h].x += u[rr][h].x;
-                                    t[rr][h].y += u[rr][h].y;
-                                    t[rr][h].z += u[rr][h].z;
-                                    t[rr][h].w += u[rr][h].w;
-                                }
-                        }
-#pragma unroll
-                        for (int rr = 0; rr < 4; ++rr)
-#pragma unroll
-                            for (int h = 0; h < H; ++h)
-                                ((float4 *)(cq + (size_t)(r0 + rr) * N))[lane + 32 * h] = t[rr][h];
-                    }
-                }
-            }
+            if (SPLIT && fix >= 0)
+                split_arrive_reduce<BN>(sp, &sp.cnt[fix * EPI_WARPS + q],
+                                        sp.ws + ((size_t)fix * sp.parts * BM + (size_t)(q * 32)) * BN,
+                                        (size_t)BM * BN, C + (size_t)(m0 + q * 32) * (size_t)N + n0, N, lane);
             if (warp == 2 && lane == 0) g_stamp(tm, false);  // victim progress, one stamp per unit
         }
     }
@@ -389,22 +391,28 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_kernel(const __grid
 // tcgen05.mma.cta_group::2 (M = 256, N = 256, K = 16), issued by the even CTA (the
 // leader).  Each CTA loads its own 128 rows of A and its own 128 rows of B per 64-wide
 // K slice: 32 KiB per stage per SM where the single-CTA tile needs 48 KiB for the same
-// MMA work, and four stages take 129 KiB (six stages measured no faster).  Each CTA
-// holds its 128 rows of the accumulator in 256 of its own TMEM columns and stores
-// them.  The paired allocation needs the same 256 columns free on both SMs, which
-// other TMEM users of those SMs (a tensor stressor) can withhold until they exit, so
-// this variant is not a victim beside them.
-//   warp 0, lane 0   TMA producer in both CTAs; in the leader also the tile
-//                    scheduler, which writes each tile index into both CTAs' rings.
+// MMA work, so six stages (193 KiB) hold 1.5 times the MMA time in operands that four
+// 48 KiB stages hold for the single-CTA tile.  Each CTA keeps its 128 rows of the
+// accumulator in its own TMEM columns and stores them.  The paired allocation needs
+// the same columns free on both SMs, which other TMEM users of those SMs (a tensor
+// stressor) can withhold until they exit, so this variant is not a victim beside them.
+// The library runs it with STAGES = 6, ACC = 2 and SPLIT:
+//   * two 256-column accumulators per CTA (all 512 columns): the next unit's MMAs run
+//     into one while both epilogues drain the other;
+//   * the split last wave: units as in the single-CTA kernel, over pair tiles.  Each
+//     CTA's epilogue warps store their 32 rows of a part into the part's 256-row slot
+//     and count it per (tile, CTA, warp); the last part reduces those rows.
+//   warp 0, lane 0   TMA producer in both CTAs; in the leader also the unit
+//                    scheduler, which writes each unit index into both CTAs' rings.
 //                    Both producers complete their bytes on the leader's stage
 //                    barrier, whose one arrival (the leader's) expects both CTAs'
 //                    bytes: the other CTA's copies may land first, the pending
 //                    arrival keeps the phase open until the leader has posted
 //   warp 1           allocates the pair's TMEM (both CTAs); leader lane 0 issues the
-//                    MMAs and commits each stage and each finished tile to both CTAs
-//   warps 2..5       epilogue of the CTA's own 128 accumulator rows; the leader's
-//                    MMAs wait for both CTAs' epilogues before the next tile
-// Tiles are handed out as in the single-CTA kernel (first tile = cluster index, later
+//                    MMAs and commits each stage and each finished unit to both CTAs
+//   warps 2..5       epilogue of the CTA's own 128 accumulator rows; an accumulator
+//                    is reused once both CTAs' epilogues have drained it
+// Units are handed out as in the single-CTA kernel (first unit = cluster index, later
 // ones from the device counter).  Waits are bounded; a teardown cluster barrier
 // keeps each CTA resident until the other has finished touching its shared memory.
 constexpr int PAIR_M = 256, PAIR_N = 256, HALF = 128;
@@ -417,11 +425,12 @@ struct PairCfg {
     static constexpr int SMEM = STAGES * STAGE + 1024 + 256;  // + alignment slack + barriers / ring
 };
 
-template <int STAGES>
+template <int STAGES, int ACC, bool SPLIT>
 __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_pair_kernel(const __grid_constant__ CUtensorMap ta,
                                                                          const __grid_constant__ CUtensorMap tb,
                                                                          float *__restrict__ C, int M, int N,
-                                                                         int K, int group_m, DevTiming *tm) {
+                                                                         int K, int group_m, GemmSplit sp,
+                                                                         DevTiming *tm) {
     using Cf = PairCfg<STAGES>;
     constexpr int CHUNKS = PAIR_N / 16;
     constexpr uint16_t kBoth = 3;
@@ -429,9 +438,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_pair_kernel(const _
     uint8_t *base = (uint8_t *)(((uintptr_t)g_smem_raw + 1023u) & ~(uintptr_t)1023u);
     uint64_t *full = (uint64_t *)(base + STAGES * Cf::STAGE);  // [STAGES], used in the leader
     uint64_t *empty = full + STAGES;                            // [STAGES], both CTAs
-    uint64_t *tfull = empty + STAGES;                           // both CTAs
-    uint64_t *tempty = tfull + 1;                               // leader
-    uint64_t *sfull = tempty + 1;                               // [RING], both CTAs
+    uint64_t *tfull = empty + STAGES;                           // [ACC], both CTAs
+    uint64_t *tempty = tfull + ACC;                             // [ACC], leader
+    uint64_t *sfull = tempty + ACC;                             // [RING], both CTAs
     uint64_t *sempty = sfull + RING;                            // [RING], leader
     int32_t *ring = (int32_t *)(sempty + RING);
     uint32_t *tmem_slot = (uint32_t *)(ring + RING);
@@ -447,6 +456,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_pair_kernel(const _
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_m = M / PAIR_M, tiles_n = N / PAIR_N, n_tiles = tiles_m * tiles_n;
     const int KT = K / BK;
+    const int n_units = (SPLIT && sp.parts > 1) ? sp.full + (n_tiles - sp.full) * sp.parts : n_tiles;
     const uint64_t deadline = ifr_gtimer() + kGemmTimeoutNs;
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -457,15 +467,17 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_pair_kernel(const _
             tc::mbar_init(&sfull[r], 1);
             tc::mbar_init(&sempty[r], 2 * (1 + EPI_WARPS));  // leader MMA + peer producer + 2 x 4 epilogue warps
         }
-        tc::mbar_init(tfull, 1);
-        tc::mbar_init(tempty, 2 * EPI_WARPS);
+        for (int a = 0; a < ACC; ++a) {
+            tc::mbar_init(&tfull[a], 1);
+            tc::mbar_init(&tempty[a], 2 * EPI_WARPS);
+        }
         *fail = 0;
         tc::fence_mbar_init();
         tc::prefetch_tmap(&ta);
         tc::prefetch_tmap(&tb);
     }
     if (warp == 1) {
-        tc::tmem_alloc_pair(tmem_slot, PAIR_N);
+        tc::tmem_alloc_pair(tmem_slot, ACC * PAIR_N);
         tc::tmem_relinquish_pair();
     }
     tc::fence_before();
@@ -475,31 +487,33 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_pair_kernel(const _
 
     if (warp == 0 && lane == 0) {
         int64_t g = 0;
-        uint32_t next = blockIdx.x >> 1;  // leader: first tile = cluster index, later ones from the counter
+        uint32_t next = blockIdx.x >> 1;  // leader: first unit = cluster index, later ones from the counter
         for (int j = 0;; ++j) {
             const int r = j % RING;
-            int tile;
+            int unit;
             if (leader) {
                 if (j >= RING && !tc::mbar_wait_cluster(&sempty[r], (uint32_t)((j / RING) - 1) & 1u, deadline))
                     *fail = 1;
-                tile = (*fail || next >= (uint32_t)n_tiles) ? -1 : (int)next;
-                ring[r] = tile;
-                tc::st_remote_s32(tc::mapa(&ring[r], 1), tile);
+                unit = (*fail || next >= (uint32_t)n_units) ? -1 : (int)next;
+                ring[r] = unit;
+                tc::st_remote_s32(tc::mapa(&ring[r], 1), unit);
                 tc::mbar_arrive(&sfull[r]);
                 tc::mbar_arrive_remote(tc::mapa(&sfull[r], 1));  // release: orders the remote ring store
             } else {
                 const bool got = tc::mbar_wait_cluster(&sfull[r], (uint32_t)(j / RING) & 1u, deadline + 50000000ull);
-                tile = got ? ring[r] : -1;
+                unit = got ? ring[r] : -1;
                 if (!got) *fail = 1;
                 tc::mbar_arrive_remote(tc::mapa(&sempty[r], 0));
             }
-            if (tile < 0) break;
+            if (unit < 0) break;
+            int tile, k0, k1, part, fix;
+            unit_of<SPLIT>(unit, sp, KT, tile, k0, k1, part, fix);
             int tmi, tni;
             tile_coords(tile, tiles_m, tiles_n, group_m, tmi, tni);
             const int m0 = tmi * PAIR_M + (int)rank * HALF, n0 = tni * PAIR_N + (int)rank * HALF;
-            for (int kt = 0; kt < KT; ++kt, ++g) {
+            for (int kt = k0; kt < k1; ++kt, ++g) {
                 const int s = (int)(g % STAGES);
-                if (leader && kt == KT - 1) next = (gridDim.x >> 1) + atomicAdd(&tm->tile_next, 1u);
+                if (leader && kt == k1 - 1) next = (gridDim.x >> 1) + atomicAdd(&tm->tile_next, 1u);
                 if (g >= STAGES && !tc::mbar_wait(&empty[s], (uint32_t)((g / STAGES) - 1) & 1u, deadline)) {
                     *fail = 1;
                     break;
@@ -521,17 +535,21 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_pair_kernel(const _
         for (int j = 0;; ++j) {
             const int r = j % RING;
             const bool got = tc::mbar_wait(&sfull[r], (uint32_t)(j / RING) & 1u, deadline + 50000000ull);
-            const int tile = got ? ring[r] : -1;
+            const int unit = got ? ring[r] : -1;
             tc::mbar_arrive(&sempty[r]);
             if (!got) *fail = 1;
-            if (tile < 0) break;
-            if (j > 0 && !tc::mbar_wait_cluster(tempty, (uint32_t)((j - 1) & 1), deadline)) {
+            if (unit < 0) break;
+            int tile, k0, k1, part, fix;
+            unit_of<SPLIT>(unit, sp, KT, tile, k0, k1, part, fix);
+            const int a = j % ACC;  // accumulator of this unit
+            if (j >= ACC && !tc::mbar_wait_cluster(&tempty[a], (uint32_t)((j / ACC) - 1) & 1u, deadline)) {
                 *fail = 1;
-                tc::mma_commit_pair(tfull, kBoth);
+                tc::mma_commit_pair(&tfull[a], kBoth);
                 continue;  // read the ring on to its end marker
             }
             tc::fence_after();
-            for (int kt = 0; kt < KT; ++kt, ++g) {
+            const uint32_t acc_cols = tmem + (uint32_t)(a * PAIR_N);
+            for (int kt = k0; kt < k1; ++kt, ++g) {
                 const int s = (int)(g % STAGES);
                 if (!tc::mbar_wait(&full[s], (uint32_t)(g / STAGES) & 1u, deadline)) {
                     *fail = 1;
@@ -543,35 +561,43 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_pair_kernel(const _
                 const uint64_t bdesc = tc::desc_sw128(sa + Cf::A_BYTES);
 #pragma unroll
                 for (int kk = 0; kk < BK / 16; ++kk)
-                    tc::mma_bf16_pair(tmem, adesc + 2ull * kk, bdesc + 2ull * kk, idesc, (uint32_t)((kt | kk) != 0));
+                    tc::mma_bf16_pair(acc_cols, adesc + 2ull * kk, bdesc + 2ull * kk, idesc,
+                                      (uint32_t)((kt != k0) | (kk != 0)));
                 tc::mma_commit_pair(&empty[s], kBoth);
             }
-            tc::mma_commit_pair(tfull, kBoth);  // also on failure, so both epilogues' waits complete
+            tc::mma_commit_pair(&tfull[a], kBoth);  // also on failure, so both epilogues' waits complete
         }
     } else if (warp >= 2) {
         const int q = warp & 3;  // TMEM lane quadrant this warp may access
-        const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
         for (int j = 0;; ++j) {
             const int r = j % RING;
             const bool got = tc::mbar_wait_cluster(&sfull[r], (uint32_t)(j / RING) & 1u, deadline + 50000000ull);
-            const int tile = got ? ring[r] : -1;
+            const int unit = got ? ring[r] : -1;
             __syncwarp();
             if (lane == 0) tc::mbar_arrive_remote(tc::mapa(&sempty[r], 0));
             if (!__all_sync(0xffffffffu, got)) {
                 if (lane == 0) *fail = 1;
                 break;
             }
-            if (tile < 0) break;
-            const bool ok = tc::mbar_wait(tfull, (uint32_t)(j & 1), deadline + 100000000ull);
+            if (unit < 0) break;
+            const int a = j % ACC;
+            const bool ok = tc::mbar_wait(&tfull[a], (uint32_t)(j / ACC) & 1u, deadline + 100000000ull);
             tc::fence_after();
             if (!__all_sync(0xffffffffu, ok && !*fail)) {
                 if (lane == 0) *fail = 1;
                 break;
             }
+            int tile, k0, k1, part, fix;
+            unit_of<SPLIT>(unit, sp, KT, tile, k0, k1, part, fix);
+            const uint32_t trow = tmem + (uint32_t)(a * PAIR_N) + ((uint32_t)(q * 32) << 16);
             int tmi, tni;
             tile_coords(tile, tiles_m, tiles_n, group_m, tmi, tni);
             const int m0 = tmi * PAIR_M + (int)rank * HALF, n0 = tni * PAIR_N;
-            float *crow = C + (size_t)(m0 + q * 32 + lane) * (size_t)N + n0;
+            // slot rows of a part: the CTA's 128 rows at rank x 128 of the 256-row slot
+            const size_t slot_row = (size_t)rank * HALF + (size_t)(q * 32);
+            float *crow = (!SPLIT || fix < 0)
+                              ? C + (size_t)(m0 + q * 32 + lane) * (size_t)N + n0
+                              : sp.ws + ((size_t)(fix * sp.parts + part) * PAIR_M + slot_row + lane) * PAIR_N;
             uint32_t ra[16], rb[16];
             tc::tmem_ld16(trow, ra);
             tc::tmem_ld_wait();
@@ -587,10 +613,15 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_pair_kernel(const _
                 } else {
                     tc::fence_before();
                     __syncwarp();
-                    if (lane == 0) tc::mbar_arrive_remote(tc::mapa(tempty, 0));  // this half of the accumulator is drained
+                    if (lane == 0) tc::mbar_arrive_remote(tc::mapa(&tempty[a], 0));  // this half is drained
                     store_row16(crow + (c + 1) * 16, rb);
                 }
             }
+            if (SPLIT && fix >= 0)
+                split_arrive_reduce<PAIR_N>(sp, &sp.cnt[(fix * 2 + (int)rank) * EPI_WARPS + q],
+                                            sp.ws + ((size_t)fix * sp.parts * PAIR_M + slot_row) * PAIR_N,
+                                            (size_t)PAIR_M * PAIR_N, C + (size_t)(m0 + q * 32) * (size_t)N + n0, N,
+                                            lane);
             if (warp == 2 && lane == 0) g_stamp(tm, false);
         }
     }
@@ -599,7 +630,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_pair_kernel(const _
     tc::cluster_sync();  // every remote arrival and every MMA into this CTA's TMEM is done
     if (warp == 1) {
         tc::fence_after();
-        tc::tmem_dealloc_pair(tmem, PAIR_N);
+        tc::tmem_dealloc_pair(tmem, ACC * PAIR_N);
     }
     if (threadIdx.x == 0 && *fail) tm->status = IFR_ERR_TIMEOUT;
     g_exit(tm);
@@ -902,11 +933,12 @@ GemmSplit split_for(int tiles, int ctas, int KT) {
 
 // Workspace and counters of a split launch, owned by the context; the counters are
 // zeroed when allocated, when the split changes and after a failed launch.
-int ensure_split(ifr_ctx *ctx, GemmSplit &sp, int tiles, int BN, cudaStream_t stream) {
+// slot_floats: floats of one part's partial tile; counters: counters per split tile.
+int ensure_split(ifr_ctx *ctx, GemmSplit &sp, int tiles, size_t slot_floats, int counters, cudaStream_t stream) {
     if (sp.parts <= 1) return IFR_OK;
     const int R = tiles - sp.full;
-    const size_t ws = (size_t)R * sp.parts * BM * BN * sizeof(float);
-    const size_t nc = (size_t)R * EPI_WARPS;
+    const size_t ws = (size_t)R * sp.parts * slot_floats * sizeof(float);
+    const size_t nc = (size_t)R * counters;
     if (ws > ctx->gemm_ws_bytes) {
         if (ctx->gemm_ws) cudaFree(ctx->gemm_ws);
         ctx->gemm_ws = nullptr;
@@ -947,7 +979,7 @@ int launch_gemm(ifr_ctx *ctx, const ifr_victim_cfg *c, cudaStream_t stream, int 
     sp.parts = 1;
     if (split) {
         sp = split_for(tiles, g_num_sms, (int)(c->k / BK));
-        rc = ensure_split(ctx, sp, tiles, BN, stream);
+        rc = ensure_split(ctx, sp, tiles, (size_t)BM * BN, EPI_WARPS, stream);
         if (rc) return rc;
     }
     const int units = sp.parts > 1 ? sp.full + (tiles - sp.full) * sp.parts : tiles;
@@ -957,15 +989,15 @@ int launch_gemm(ifr_ctx *ctx, const ifr_victim_cfg *c, cudaStream_t stream, int 
     return IFR_OK;
 }
 
-template <int ST>
+template <int ST, int ACC, bool SPLIT>
 const void *gemm_pair_fn() {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(gemm_bf16_pair_kernel<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(gemm_bf16_pair_kernel<ST, ACC, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              PairCfg<ST>::SMEM);
         attr = true;
     }
-    return (const void *)gemm_bf16_pair_kernel<ST>;
+    return (const void *)gemm_bf16_pair_kernel<ST, ACC, SPLIT>;
 }
 
 template <int ST>
@@ -985,16 +1017,16 @@ void pair_launch_cfg(cudaLaunchConfig_t *cfg, cudaLaunchAttribute *at, int grid,
 }
 
 // CTA pairs the device can hold at once (pairs must sit in one GPC), asked once.
-template <int ST>
+template <int ST, int ACC, bool SPLIT>
 int pair_clusters() {
     static int n = 0;
     if (n == 0) {
-        ifr_carveout(gemm_pair_fn<ST>());
+        ifr_carveout(gemm_pair_fn<ST, ACC, SPLIT>());
         cudaLaunchConfig_t cfg;
         cudaLaunchAttribute at;
         pair_launch_cfg<ST>(&cfg, &at, 2 * (g_num_sms / 2), nullptr);
         int c = 0;
-        if (cudaOccupancyMaxActiveClusters(&c, gemm_bf16_pair_kernel<ST>, &cfg) != cudaSuccess || c <= 0) {
+        if (cudaOccupancyMaxActiveClusters(&c, gemm_bf16_pair_kernel<ST, ACC, SPLIT>, &cfg) != cudaSuccess || c <= 0) {
             cudaGetLastError();
             c = g_num_sms / 2;
         }
@@ -1003,27 +1035,45 @@ int pair_clusters() {
     return n;
 }
 
-template <int ST>
-int pair_grid(const ifr_victim_cfg *c) {
+// Split of a pair launch (SPLIT only) and its grid: one pair per unit, at most as
+// many pairs as the device holds.
+template <int ST, int ACC, bool SPLIT>
+GemmSplit pair_split(const ifr_victim_cfg *c) {
     const int tiles = (int)((c->n / PAIR_N) * (c->m / PAIR_M));
-    const int cl = pair_clusters<ST>();
-    return 2 * (tiles < cl ? tiles : cl);
+    GemmSplit sp;
+    memset(&sp, 0, sizeof sp);
+    sp.parts = 1;
+    if (SPLIT) sp = split_for(tiles, pair_clusters<ST, ACC, SPLIT>(), (int)(c->k / BK));
+    return sp;
 }
 
-template <int ST>
-int launch_gemm_pair(const ifr_victim_cfg *c, cudaStream_t stream, int group_m, DevTiming *tm) {
-    gemm_pair_fn<ST>();
+template <int ST, int ACC, bool SPLIT>
+int pair_grid(const ifr_victim_cfg *c) {
+    const int tiles = (int)((c->n / PAIR_N) * (c->m / PAIR_M));
+    const GemmSplit sp = pair_split<ST, ACC, SPLIT>(c);
+    const int units = sp.parts > 1 ? sp.full + (tiles - sp.full) * sp.parts : tiles;
+    const int cl = pair_clusters<ST, ACC, SPLIT>();
+    return 2 * (units < cl ? units : cl);
+}
+
+template <int ST, int ACC, bool SPLIT>
+int launch_gemm_pair(ifr_ctx *ctx, const ifr_victim_cfg *c, cudaStream_t stream, int group_m, DevTiming *tm) {
+    gemm_pair_fn<ST, ACC, SPLIT>();
     CUtensorMap ta, tb;
     int rc = make_map(&ta, c->in0, c->m, c->k, HALF);
     if (rc) return rc;
     rc = make_map(&tb, c->in1, c->n, c->k, HALF);
     if (rc) return rc;
-    ifr_carveout(gemm_pair_fn<ST>());
+    ifr_carveout(gemm_pair_fn<ST, ACC, SPLIT>());
+    const int tiles = (int)((c->n / PAIR_N) * (c->m / PAIR_M));
+    GemmSplit sp = pair_split<ST, ACC, SPLIT>(c);
+    rc = ensure_split(ctx, sp, tiles, (size_t)PAIR_M * PAIR_N, 2 * EPI_WARPS, stream);
+    if (rc) return rc;
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute at;
-    pair_launch_cfg<ST>(&cfg, &at, pair_grid<ST>(c), stream);
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, gemm_bf16_pair_kernel<ST>, ta, tb, (float *)c->out,
-                                             (int)c->m, (int)c->n, (int)c->k, group_m, tm);
+    pair_launch_cfg<ST>(&cfg, &at, pair_grid<ST, ACC, SPLIT>(c), stream);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, gemm_bf16_pair_kernel<ST, ACC, SPLIT>, ta, tb, (float *)c->out,
+                                             (int)c->m, (int)c->n, (int)c->k, group_m, sp, tm);
     return e == cudaSuccess ? IFR_OK : IFR_ERR_LAUNCH;
 }
 
@@ -1105,10 +1155,10 @@ int ifr_gemm_shape(const ifr_victim_cfg *c, VictimShape *s) {
     s->uses_tensor = 1;
     s->block = GEMM_THREADS;
     if (c->variant == 2) {
-        s->fn = gemm_pair_fn<4>();
-        s->grid = pair_grid<4>(c);
-        s->smem = PairCfg<4>::SMEM;
-        s->tmem_cols = PAIR_N;
+        s->fn = gemm_pair_fn<6, 2, true>();
+        s->grid = pair_grid<6, 2, true>(c);
+        s->smem = PairCfg<6>::SMEM;
+        s->tmem_cols = 2 * PAIR_N;
         return IFR_OK;
     }
     if (c->variant == 4) {
@@ -1145,7 +1195,7 @@ int ifr_gemm_enqueue(ifr_ctx *ctx, const ifr_victim_cfg *c, cudaStream_t stream,
     if (c->m > 65535 * BM || c->n > (1ll << 30) || c->k > (1ll << 30)) return IFR_ERR_ARG;
     const double operand_bytes = 2.0 * ((double)c->m + (double)c->n) * (double)c->k;
     const int gm = operand_bytes > (double)ctx->info.l2_bytes ? GROUP_M : 1;
-    if (c->variant == 2) return launch_gemm_pair<4>(c, stream, gm, tm);
+    if (c->variant == 2) return launch_gemm_pair<6, 2, true>(ctx, c, stream, gm, tm);
     if (c->variant == 4) return launch_gemm_mc<4>(c, stream, gm, tm);
     const bool wide = c->n % 256 == 0;
     if (c->variant == 3)
@@ -1165,7 +1215,7 @@ void ifr_gemm_forget_split(ifr_ctx *ctx) { ctx->gemm_cnt_key = -1; }
 
 int ifr_preload_gemm() {
     const void *fns[] = {gemm_fn<128, 3, 1>(), gemm_fn<256, 3, 1>(), gemm_fn<128, 4, 1>(), gemm_fn<256, 4, 1>(),
-                         gemm_fn<128, 4, 2>(), gemm_fn<256, 4, 2>(), gemm_pair_fn<4>(), gemm_mc_fn<4>()};
+                         gemm_fn<128, 4, 2>(), gemm_fn<256, 4, 2>(), gemm_pair_fn<6, 2, true>(), gemm_mc_fn<4>()};
     for (const void *f : fns) {
         int rc = ifr_preload(f);
         if (rc) return rc;

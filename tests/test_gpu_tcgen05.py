@@ -47,8 +47,9 @@ def test_gemm_small_all_entries(ctx, M, N, K, variant, repeats=1):
     assert float(torch.linalg.norm(got - ref) / torch.linalg.norm(ref)) <= 1e-5
 
 
-# variant 2: 256 x 256 tiles on CTA pairs (cta_group::2); (2048, 2560) is 80 pair tiles
-# for at most 74 pairs, so tiles also come from the device counter
+# variant 2: 256 x 256 tiles on CTA pairs (cta_group::2, two accumulators); (2048,
+# 2560) is 80 pair tiles for at most 74 pairs, so tiles also come from the device
+# counter; K is too short for a split last wave at these shapes
 @pytest.mark.parametrize("M,N,K", [(256, 256, 64), (256, 512, 128), (512, 768, 192), (768, 256, 1024),
                                    (2048, 2560, 128), (8192, 512, 64)])
 def test_gemm_pair_tiles_all_entries(ctx, M, N, K):
@@ -64,18 +65,22 @@ def test_gemm_multicast_pairs_all_entries(ctx, M, N, K):
     test_gemm_small_all_entries(ctx, M, N, K, 4, repeats=3)
 
 
-# variant 3 with split last waves (a part must run at least 32 K slices of 64): 72
-# tiles of 128 x 256 in 2 K parts (one wave of 144 units), 6 tiles in 4 parts, and
-# 320 tiles = 296 whole + 24 in 2 parts; three launches each, so the arrival counters
-# run over several launches, and the shapes alternate so the context re-zeroes them
-# when the split changes.  Small shapes: every entry against fp64; the large one:
-# entries of every 128 x 128 block against the oracle.
-@pytest.mark.parametrize("M,N,K", [(1152, 2048, 4096), (384, 512, 8192), (2560, 4096, 4096), (1152, 2048, 4096)])
-def test_gemm_two_accumulators_split_wave(ctx, M, N, K):
+# split last waves (a part must run at least 32 K slices of 64).  Variant 3 (128 x 256
+# tiles on 148 CTAs): 72 tiles in 2 K parts (one wave of 144 units), 6 tiles in 4
+# parts, and 320 tiles = 296 whole + 24 in 2 parts.  Variant 2 (256 x 256 tiles on 74
+# CTA pairs): 32 tiles in 2 parts, 4 tiles in 4 parts, and 160 tiles = 148 whole + 12
+# in 2 parts.  Three launches each, so the arrival counters run over several
+# launches, and the shapes alternate so the context re-zeroes them when the split
+# changes.  Small shapes: every entry against fp64; the large ones: entries of every
+# 128 x 128 block against the oracle.
+@pytest.mark.parametrize("variant,M,N,K", [(3, 1152, 2048, 4096), (3, 384, 512, 8192), (3, 2560, 4096, 4096),
+                                           (3, 1152, 2048, 4096), (2, 1024, 2048, 4096), (2, 512, 512, 8192),
+                                           (2, 2560, 4096, 4096), (2, 1024, 2048, 4096)])
+def test_gemm_split_wave(ctx, variant, M, N, K):
     if M * N * K <= 1 << 34:
-        test_gemm_small_all_entries(ctx, M, N, K, 3, repeats=3)
+        test_gemm_small_all_entries(ctx, M, N, K, variant, repeats=3)
         return
-    Ab, Bb, C, t = _gemm(ctx, M, N, K, seed=31, repeats=3, variant=3)
+    Ab, Bb, C, t = _gemm(ctx, M, N, K, seed=31, repeats=3, variant=variant)
     assert t["status"] == 0 and torch.isfinite(C).all()
     rng = np.random.default_rng(1)
     ij = np.array([(bm * 128 + rng.integers(0, 128), bn * 128 + rng.integers(0, 128))
@@ -116,10 +121,10 @@ def test_gemm_variant_profiles_and_bad_variant(ctx):
     p3 = ctx.victim_profile(ifr.victim_cfg(A.IFR_V_GEMM, Ab, Ab, C, m=256, n=256, k=256, variant=3))
     assert p3["tmem_cols"] == 512 and p3["dynamic_smem"] == p1["dynamic_smem"]
     assert p1["dynamic_smem"] - p0["dynamic_smem"] == 128 * 64 * 2 + 256 * 64 * 2  # one more 48 KiB stage
-    # pair tiles: four 32 KiB stages (each CTA's halves of A and B)
-    assert p2["dynamic_smem"] == 4 * 2 * 128 * 64 * 2 + 1024 + 256 < p0["dynamic_smem"]
-    assert p2["tmem_cols"] == 256 and p2["grid"] == 2
-    assert max(p["regs_per_thread"] for p in (p0, p1, p2)) <= 96
+    # pair tiles: six 32 KiB stages (each CTA's halves of A and B), two accumulators
+    assert p2["dynamic_smem"] == 6 * 2 * 128 * 64 * 2 + 1024 + 256
+    assert p2["tmem_cols"] == 512 and p2["grid"] == 2
+    assert max(p["regs_per_thread"] for p in (p0, p1)) <= 96  # the variants that share SMs
     p4 = ctx.victim_profile(ifr.victim_cfg(A.IFR_V_GEMM, Ab, Ab, C, m=256, n=256, k=256, variant=4))
     assert p4["tmem_cols"] == 512 and p4["grid"] == 2 and p4["dynamic_smem"] == p1["dynamic_smem"]
     for bad in (ifr.victim_cfg(A.IFR_V_GEMM, Ab, Ab, C, m=256, n=256, k=256, variant=5),
