@@ -95,16 +95,16 @@ class ClockSampler:
 _GEMM_SRC = ("paper_2501_16909_b300/csrc/ifr_gemm.cu",
              "e8b0c478e88782980fd46b3cd6ed4a1c2b0fd706db922701469cbc383f46822a")
 _STRESS_SRC = ("paper_2501_16909_b300/csrc/ifr_stressors.cu",
-               "dce4f69d115e9b98123961bd203ed8d2d2e6c22f193b96840584b799198284e7")
+               "858b425a2daa113157846bb21b0e573c6a56c91de8263c8e5e803f46cbf69386")
 NCU_DRAM_BYTES = {
-    "sched": (4864 + 0,) + _STRESS_SRC,
+    "sched": (4608 + 0,) + _STRESS_SRC,
     "fma": (20992 + 0,) + _STRESS_SRC,
-    "tensor": (47360 + 0,) + _STRESS_SRC,
-    "smem_cf": (29184 + 0,) + _STRESS_SRC,
-    "smem_32w": (18432 + 0,) + _STRESS_SRC,
-    "l2": (16794880 + 0,) + _STRESS_SRC,
-    "hbm": (2483068416 + 2992640,) + _STRESS_SRC,
-    "hbm_tma": (2502674688 + 3000576,) + _STRESS_SRC,
+    "tensor": (47616 + 0,) + _STRESS_SRC,
+    "smem_cf": (17408 + 0,) + _STRESS_SRC,
+    "smem_32w": (18688 + 0,) + _STRESS_SRC,
+    "l2": (16794112 + 0,) + _STRESS_SRC,
+    "hbm": (2483067904 + 2713856,) + _STRESS_SRC,
+    "hbm_tma": (2502516480 + 2992384,) + _STRESS_SRC,
     "gemm": (77078016 + 35707648,) + _GEMM_SRC,
     "gemm_v2": (75990528 + 40968448,) + _GEMM_SRC,
     "gemm_v3": (77721344 + 41471488,) + _GEMM_SRC,
@@ -879,7 +879,7 @@ def run_config3(args):
     mp, msrc = P.measured_peaks()
     roofline_hbm = {"bound": "hbm", "achieved": round(hb["rate"] / 1e9, 1), "peak": round(hb["peak"] / 1e9, 1),
                     "unit": "GB/s", "frac": round(hb["frac"], 4), "traffic": ncu_traffic("hbm"),
-                    "kernel": "stream_stress_kernel (16-byte loads; HBM 4 GiB set, %d SMs x 2 blocks of 512, "
+                    "kernel": "stream_stress_kernel (word loads 16 B apart, whole sectors; HBM 4 GiB set, %d SMs x 2 blocks of 512, "
                               "%d rounds x %d chunks x 32 KiB per block)" % (S, P.CAL_ROUNDS[A.IFR_S_HBM],
                                                                           P.STREAM_CHUNKS_PER_ROUND),
                     "peak_source": hb["peak_source"] + " (of measured)",

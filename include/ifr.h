@@ -137,9 +137,10 @@ typedef struct {
                                    sm_count must equal the number of bits set */
     uint64_t deadline_ns;    /* device-side limit on the run (0 = 2 s) */
     uint32_t sm_mask[IFR_MAX_SMS / 32]; /* mask_mode 2: bit s of word s/32 allows SM id s */
-    int32_t staging;         /* L2/HBM: 0 = 16-byte vector loads into registers, no shared
-                                memory (default; the checksum folds the first word of every
-                                16-byte load);
+    int32_t staging;         /* L2/HBM: 0 = loads into registers, no shared memory
+                                (default): a thread loads the first word of each of its
+                                16-byte groups, which brings every 32-byte sector of the
+                                chunk into the SM; the checksum folds those words;
                                 1 = TMA bulk copies (cp.async.bulk) of whole chunks into a ring
                                 in shared memory of about 96 KiB per block (2 to 6 stages of
                                 block x 64 bytes), folded from there (the checksum folds

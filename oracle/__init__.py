@@ -77,9 +77,9 @@ def splitmix64(s0: int, i: int) -> int:
 
 
 # ------------------------------------------------------------------ stressors
-# fold of the L2 / HBM stream stressor's checksum: by vector loads into registers
-# (first word of every 16-byte group) or by bulk copies into shared memory (quarter
-# pass mod 4 of each chunk); see ifr_oracle.c
+# fold of the L2 / HBM stream stressor's checksum: by loads into registers (first
+# word of every 16-byte group) or by bulk copies into shared memory (quarter pass
+# mod 4 of each chunk); see ifr_oracle.c
 FOLD_LOADS, FOLD_BULK = 0, 1
 
 

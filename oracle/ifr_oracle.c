@@ -53,7 +53,7 @@ static uint32_t f32_bits(float f) {
 /* p_j = floor(j / m_k).  The kernel reads every word of every chunk and folds */
 /* a part of it, by `fold`:                                                   */
 /*   fold 0 (loads into registers): the first word of every 16-byte group,    */
-/*          words 4i of the chunk, so every 16-byte load enters the fold;     */
+/*          words 4i of the chunk, the words the register-load kernel loads;  */
 /*   fold 1 (bulk copies into shared memory): quarter p_j mod 4 of the chunk  */
 /*          (the chunk's four contiguous quarters), so four consecutive       */
 /*          passes fold every word once.                                      */

@@ -11,10 +11,11 @@ gemv, layernorm, softmax, hist, triad; gemm_variants, the solo throughput of eve
 variant at four shapes; config5_kernels, one launch of each configuration-5
 decoder-layer kernel in order; and victim_bandwidth, which times every memory-bound
 configuration-2 victim alone over grids of 0 (default), 1, 2, 4, 8 and 16 blocks per
-SM (20 launches after a warm measurement) and prints one JSON line per run; and
+SM (20 launches after a warm measurement), then a triad moving the same bytes per
+launch, and prints one JSON line per run; and
 l2_set_sweep, which times the stream kernel on every SM (256 rounds per block) over
 sets of 8..96 MiB for 2 x 512, 4 x 512 and 2 x 256 threads per SM; and stream_staging,
-which times the HBM (4 GiB) and L2 (16 MiB) stressors with vector loads and with TMA
+which times the HBM (4 GiB) and L2 (16 MiB) stressors with register loads and with TMA
 bulk copies over four block shapes.  Inputs are the workloads' seeded inputs at the sizes
 given below (the stream stressors use a 1 GiB / 48 MiB set; the victims use their
 full configuration-2 shapes).
@@ -50,7 +51,7 @@ def main(argv=None):
     ap.add_argument("--bps", type=int, default=None, help="stressors: blocks per SM")
     ap.add_argument("--ilp", type=int, default=None, help="FMA / FP64 stressors: chains per thread")
     ap.add_argument("--staging", type=int, default=0,
-                    help="L2 / HBM stressors: 0 = vector loads into registers, 1 = TMA bulk copies into shared memory")
+                    help="L2 / HBM stressors: 0 = loads into registers, 1 = TMA bulk copies into shared memory")
     a = ap.parse_args(argv)
     ctx = ifr.Context(0)
     S = ctx.info["num_sms"]
@@ -70,7 +71,7 @@ def main(argv=None):
         ctx.close()
         return
     if a.case == "stream_staging":
-        # the stream stressor with vector loads (staging 0) and with TMA bulk copies
+        # the stream stressor with register loads (staging 0) and with TMA bulk copies
         # (staging 1) on every SM: HBM over a 4 GiB set (64 rounds per block) and L2 over
         # the 16 MiB set (256 rounds), 2 or 4 blocks of 512 threads or 2 of 1024 per SM
         sets = {"hbm": (A.IFR_S_HBM, I.torch_u32_as_i32(1, (4 << 30) // 4, "cuda"), 64),
@@ -143,6 +144,18 @@ def main(argv=None):
                 us = t["event_ms"] * 1e3 / 20
                 print(json.dumps({"victim": names[k], "grid": g or prof["grid"], "us_per_launch": round(us, 2),
                                   "gbs": round(prof["bytes_per_launch"] / (us * 1e-6) / 1e9, 1)}))
+            # a triad moving the same bytes per launch, timed the same way: the rate a
+            # plain stream of this length reaches (launch ramp and tail included)
+            n = int(prof["bytes_per_launch"] // 12) // 4 * 4
+            tb, tc_ = I.torch_uniform_pm1(90, n, "cuda"), I.torch_uniform_pm1(91, n, "cuda")
+            ta = torch.empty(n, device="cuda")
+            tv = ifr.victim_cfg(A.IFR_V_TRIAD, tb, tc_, ta, n=n, scalar=0.5, repeats=20)
+            ctx.victim_launch(tv)
+            t = ctx.victim_launch(tv)
+            us = t["event_ms"] * 1e3 / 20
+            print(json.dumps({"victim": "triad, same bytes as " + names[k], "n": n, "us_per_launch": round(us, 2),
+                              "gbs": round(12.0 * n / (us * 1e-6) / 1e9, 1)}))
+            del tb, tc_, ta
         ctx.close()
         return
     if a.case in stressors:

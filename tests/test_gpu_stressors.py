@@ -63,7 +63,8 @@ def _stream_check(ctx, kind, nbytes, block, bps, sm_count, rounds=0, stop_after_
     return r, logs
 
 
-# staging 0: 16-byte loads into registers; 1: TMA bulk copies into a shared-memory ring
+# staging 0: loads into registers (the first word of every 16-byte group); 1: TMA bulk
+# copies into a shared-memory ring
 @pytest.mark.parametrize("staging", [0, 1])
 def test_hbm_stressor_fixed_rounds_all_sms(ctx, staging):
     S = ctx.info["num_sms"]
@@ -93,6 +94,16 @@ def test_stream_stressor_stop_flag_arbitrary_counts(ctx, staging):
     r, logs = _stream_check(ctx, A.IFR_S_HBM, 256 << 20, 512, 2, S, rounds=0, stop_after_s=0.002, staging=staging)
     assert r["work"] > 0 and all(L["status"] == 0 for L in logs)
     assert len(logs) == 2 * S and len({L["work"] for L in logs}) > 1
+
+
+# every instantiation of the register-load kernel (block sizes fixed at compile time,
+# and 384 read at run time): 13 SMs x 2 blocks over 291 chunks, so each block cycles
+# through 11 or 12 chunks; 5 rounds of 8 chunks run whole rounds from one pointer and
+# rounds that wrap to the block's first chunk part-way, over 3 or 4 passes
+@pytest.mark.parametrize("block", [128, 256, 384, 512, 1024])
+def test_stream_stressor_block_sizes_wrap_inside_rounds(ctx, block):
+    n_chunks = 13 * 2 * 11 + 5
+    _stream_check(ctx, A.IFR_S_HBM, n_chunks * block * 64, block, 2, 13, rounds=5)
 
 
 def test_stream_stressor_staging_needs_a_stream_kind(ctx):
