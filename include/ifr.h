@@ -276,6 +276,11 @@ typedef struct {
                               multiples of 256, else IFR_ERR_ARG), two accumulators.
                               Variants 3 and 4 hold all 512 TMEM columns of an SM: solo
                               use only, refused like variant 2.
+                              GEMV: 0 = one warp per row, 16-byte loads into registers;
+                              1 = rows streamed into shared memory by bulk copies (each
+                              warp a ring of two 4 KiB segments; x in shared memory too,
+                              80 KiB per block at k = 8192), for solo use: ifr_sweep,
+                              ifr_corun and ifr_colocate refuse it with IFR_ERR_ARG.
                               Other kinds: 0. */
     int32_t reserved;
 } ifr_victim_cfg;

@@ -183,9 +183,13 @@ double per_launch_ratio(const ifr_timing &co, const ifr_timing &solo) {
 // The CTA-pair GEMM (variant 2) allocates the same TMEM columns on two SMs at once,
 // and the two-accumulator GEMMs (variants 3, 4) all 512 columns of an SM; beside other
 // TMEM users (the tensor stressor, another GEMM) those allocations can wait until
-// they exit, so the measurements that colocate kernels refuse both.
+// they exit, so the measurements that colocate kernels refuse both.  The bulk-copy
+// GEMV (variant 1) is a solo variant too: its 80 KiB of shared memory per block is
+// not in the co-residence budget the stressors leave room for.
 int colocatable(const ifr_victim_cfg *c) {
-    return (c->kind == IFR_V_GEMM && c->variant >= 2) ? IFR_ERR_ARG : IFR_OK;
+    if (c->kind == IFR_V_GEMM && c->variant >= 2) return IFR_ERR_ARG;
+    if (c->kind == IFR_V_GEMV && c->variant == 1) return IFR_ERR_ARG;
+    return IFR_OK;
 }
 
 }  // namespace

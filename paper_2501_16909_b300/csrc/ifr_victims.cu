@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include "ifr_internal.cuh"
+#include "ifr_tcgen05.cuh"
 
 namespace {
 
@@ -328,6 +329,117 @@ __global__ void __launch_bounds__(256) gemv_kernel(const __nv_bfloat16 *__restri
     v_exit(tm);
 }
 
+// Variant 1: the same y = A x with the rows of A streamed into shared memory by bulk
+// copies.  Register loads of A are staged in the L1, which the library's max-shared
+// carveout leaves at about 28 KiB per SM, and that caps the bytes in flight; bulk
+// copies land in shared memory instead.  Each warp takes rows w, w + W, ... (W warps
+// in the grid) and owns a ring of kGemvStages segments of kGemvSeg bytes: lane 0 keeps
+// the ring full (one bulk copy per segment, completion counted in bytes on the
+// segment's mbarrier), every lane waits for a segment, multiplies its 16-byte groups
+// (lane + 32 i) with x, and lane 0 refills the segment once the warp has read it.  x
+// sits in shared memory as bf16 (16 bytes per group, as A), and each lane keeps eight
+// partial sums, one per position in a 16-byte group, so the FMAs of a group do not
+// wait on each other; bf16 widens to fp32 exactly by a shift.  A row's last segment
+// may be short (cols x 2 bytes is a multiple of 16).  Waits are bounded: a warp that
+// times out records IFR_ERR_TIMEOUT, stops, and lane 0 waits (bounded) for the copies
+// it issued before the block exits.
+constexpr int kGemvSeg = 4096, kGemvStages = 2, kGemvWarps = 8;
+constexpr uint64_t kGemvTimeoutNs = 2000000000ull;
+
+__device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+__global__ void __launch_bounds__(256) gemv_bulk_kernel(const __nv_bfloat16 *__restrict__ A,
+                                                        const __nv_bfloat16 *__restrict__ x, float *__restrict__ y,
+                                                        int64_t rows, int cols, DevTiming *tm) {
+    extern __shared__ __align__(128) uint8_t g_gemv_smem[];
+    __shared__ __align__(8) uint64_t bars[kGemvWarps][kGemvStages];
+    v_enter(tm);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int xbytes = ((cols * 2 + 127) / 128) * 128;
+    uint4 *xs = (uint4 *)g_gemv_smem;
+    uint8_t *ring = g_gemv_smem + xbytes + (size_t)warp * kGemvStages * kGemvSeg;
+    for (int i = threadIdx.x; i < (cols >> 3); i += blockDim.x) xs[i] = ((const uint4 *)x)[i];
+    if (lane == 0) {
+        for (int s = 0; s < kGemvStages; ++s) tc::mbar_init(&bars[warp][s], 1);
+        tc::fence_mbar_init();
+    }
+    __syncthreads();
+    const uint64_t deadline = ifr_gtimer() + kGemvTimeoutNs;
+    const int64_t W = (int64_t)gridDim.x * kGemvWarps, w0 = (int64_t)blockIdx.x * kGemvWarps + warp;
+    const int row_bytes = cols * 2;
+    const int nseg = (row_bytes + kGemvSeg - 1) / kGemvSeg;
+    const int64_t my_rows = w0 < rows ? (rows - 1 - w0) / W + 1 : 0;
+    const int64_t total = my_rows * nseg;  // segments this warp reads, in order
+    int64_t issued = 0;
+    auto issue = [&](int64_t q) {
+        const int64_t r = w0 + (q / nseg) * W;
+        const int sg = (int)(q % nseg);
+        const int rem = row_bytes - sg * kGemvSeg;
+        const uint32_t bytes = (uint32_t)(rem < kGemvSeg ? rem : kGemvSeg);
+        const int s = (int)(q % kGemvStages);
+        tc::mbar_arrive_expect_tx(&bars[warp][s], bytes);
+        tc::bulk_g2s(ring + (size_t)s * kGemvSeg, (const uint8_t *)(A + r * cols) + (size_t)sg * kGemvSeg, bytes,
+                     &bars[warp][s]);
+    };
+    if (lane == 0)
+        for (; issued < total && issued < kGemvStages; ++issued) issue(issued);
+    float p[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int64_t q = 0;
+    bool ok = true;
+    for (; q < total; ++q) {
+        const int s = (int)(q % kGemvStages);
+        const bool got = tc::mbar_wait(&bars[warp][s], (uint32_t)((q / kGemvStages) & 1), deadline);
+        if (!__all_sync(0xffffffffu, got)) {
+            ok = false;
+            break;
+        }
+        const int sg = (int)(q % nseg);
+        const int rem = row_bytes - sg * kGemvSeg;
+        const int n16 = (rem < kGemvSeg ? rem : kGemvSeg) >> 4;
+        const uint4 *seg = (const uint4 *)(ring + (size_t)s * kGemvSeg);
+        const uint4 *xseg = xs + (size_t)sg * (kGemvSeg / 16);
+#pragma unroll 4
+        for (int i = lane; i < n16; i += 32) {
+            const uint4 av = seg[i];
+            const uint4 xv = xseg[i];
+            p[0] = fmaf(bf16_lo(av.x), bf16_lo(xv.x), p[0]);
+            p[1] = fmaf(bf16_hi(av.x), bf16_hi(xv.x), p[1]);
+            p[2] = fmaf(bf16_lo(av.y), bf16_lo(xv.y), p[2]);
+            p[3] = fmaf(bf16_hi(av.y), bf16_hi(xv.y), p[3]);
+            p[4] = fmaf(bf16_lo(av.z), bf16_lo(xv.z), p[4]);
+            p[5] = fmaf(bf16_hi(av.z), bf16_hi(xv.z), p[5]);
+            p[6] = fmaf(bf16_lo(av.w), bf16_lo(xv.w), p[6]);
+            p[7] = fmaf(bf16_hi(av.w), bf16_hi(xv.w), p[7]);
+        }
+        if (sg == nseg - 1) {
+            float acc = ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) y[w0 + (q / nseg) * W] = acc;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) p[e] = 0.f;
+        }
+        __syncwarp();  // every lane has read segment q: its stage may be refilled
+        if (lane == 0 && issued < total) {
+            tc::fence_proxy_async_smem();  // the reads above come before the copy's writes
+            issue(issued++);
+        }
+    }
+    if (lane == 0) {
+        // copies issued but not read (only after a timeout) land before the block exits
+        for (int64_t d = q; d < issued; ++d)
+            tc::mbar_wait(&bars[warp][d % kGemvStages], (uint32_t)((d / kGemvStages) & 1), deadline + 100000000ull);
+        if (!ok) tm->status = IFR_ERR_TIMEOUT;
+    }
+    v_exit(tm);
+}
+
+// Dynamic shared memory of the variant-1 GEMV: x, then every warp's ring.
+inline int gemv_bulk_smem(int64_t cols) {
+    return (int)(((cols * 2 + 127) / 128) * 128) + kGemvWarps * kGemvStages * kGemvSeg;
+}
+
 // Short rows (cols <= 256): L = the power of two >= cols/8 lanes share one row (one
 // 16-byte load each), so a warp reduces 32/L rows at once and no lane idles; x is
 // read straight from global memory (each lane keeps its fixed 8-element slice).
@@ -497,7 +609,8 @@ void ifr_timing_to_host(const DevTiming &d, int repeats, ifr_timing *out) {
 int ifr_victim_validate(ifr_ctx *ctx, const ifr_victim_cfg *c) {
     if (!c || c->kind < 0 || c->kind >= IFR_V_COUNT || c->repeats < 0 || c->grid < 0 || c->block < 0) return IFR_ERR_ARG;
     if (!c->in0 || !c->out) return IFR_ERR_ARG;
-    if (c->variant < 0 || c->variant > 4 || (c->kind != IFR_V_GEMM && c->variant != 0)) return IFR_ERR_ARG;
+    if (c->variant < 0 || c->variant > 4) return IFR_ERR_ARG;
+    if (c->kind != IFR_V_GEMM && c->variant != 0 && !(c->kind == IFR_V_GEMV && c->variant == 1)) return IFR_ERR_ARG;
     switch (c->kind) {
         case IFR_V_TRIAD:
             if (!c->in1 || c->n <= 0 || !aligned16(c->in0) || !aligned16(c->in1) || !aligned16(c->out)) return IFR_ERR_ARG;
@@ -557,7 +670,13 @@ int ifr_victim_shape(ifr_ctx *ctx, const ifr_victim_cfg *c, VictimShape *s) {
         }
         case IFR_V_GEMV: {
             const int lanes = gemv_short_lanes(c->k);
-            if (lanes) {
+            if (c->variant == 1) {
+                // one block of 8 warps per 8 rows, at most two blocks per SM
+                s->fn = (const void *)gemv_bulk_kernel;
+                const int64_t need = (c->m + kGemvWarps - 1) / kGemvWarps;
+                s->grid = c->grid ? c->grid : (int)(need < (int64_t)sms * 2 ? need : (int64_t)sms * 2);
+                s->smem = gemv_bulk_smem(c->k);
+            } else if (lanes) {
                 s->fn = gemv_short_fn(lanes);
                 const int64_t rows_per_block = 8 * (32 / lanes);
                 const int64_t need = (c->m + rows_per_block - 1) / rows_per_block;
@@ -617,6 +736,11 @@ int ifr_victim_enqueue(ifr_ctx *ctx, const ifr_victim_cfg *c, cudaStream_t strea
                 const auto *xb = (const __nv_bfloat16 *)c->in1;
                 float *yo = (float *)c->out;
                 ifr_carveout(sh.fn);
+                if (c->variant == 1) {
+                    cudaFuncSetAttribute(gemv_bulk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sh.smem);
+                    gemv_bulk_kernel<<<sh.grid, 256, sh.smem, stream>>>(Ab, xb, yo, c->m, (int)c->k, tm);
+                    break;
+                }
                 switch (gemv_short_lanes(c->k)) {
                     case 1: gemv_short_kernel<1><<<sh.grid, 256, 0, stream>>>(Ab, xb, yo, c->m, (int)c->k, tm); break;
                     case 2: gemv_short_kernel<2><<<sh.grid, 256, 0, stream>>>(Ab, xb, yo, c->m, (int)c->k, tm); break;
@@ -714,6 +838,7 @@ extern "C" int ifr_launch_count(ifr_ctx *ctx, uint64_t *out) {
 int ifr_preload_victims() {
     const void *fns[] = {
         (const void *)timing_reset_kernel, (const void *)triad_kernel, (const void *)gemv_kernel,
+        (const void *)gemv_bulk_kernel,
         gemv_short_fn(1), gemv_short_fn(2), gemv_short_fn(4), gemv_short_fn(8), gemv_short_fn(16), gemv_short_fn(32),
         (const void *)hist_kernel, row_fn<true>(true, 1), row_fn<true>(true, 2048), row_fn<true>(true, 4096),
         row_fn<true>(false, 1), row_fn<true>(false, 2048), row_fn<true>(false, 4096), row_fn<false>(true, 1),

@@ -299,19 +299,23 @@ def mape(pred, y):
 
 class Standardizer:
     """z-scores with the training statistics, clipped to +-Z_CLIP: a held-out kernel
-    whose feature lies far outside the training range (a feature constant on the
-    training side, say) enters the network at the edge of that range instead of at a
-    z-score of thousands."""
+    whose feature lies far outside the training range enters the network at the edge
+    of that range instead of at a z-score of thousands.  A feature that is constant
+    over the training rows (the fraction of a resource only the held-out stressor kind
+    uses, say) taught the network nothing, so it enters as 0 for every row instead of
+    as an input direction the network never saw vary."""
 
     Z_CLIP = 8.0
 
     def __init__(self, X):
         self.mu = X.mean(axis=0)
-        self.sd = X.std(axis=0)
-        self.sd[self.sd < 1e-9] = 1.0
+        sd = X.std(axis=0)
+        self.live = sd >= 1e-9
+        self.sd = np.where(self.live, sd, 1.0)
 
     def __call__(self, X):
-        return np.clip((X - self.mu) / self.sd, -self.Z_CLIP, self.Z_CLIP)
+        z = np.clip((X - self.mu) / self.sd, -self.Z_CLIP, self.Z_CLIP)
+        return np.where(self.live, z, 0.0)
 
 
 def train(model, Xtr, ytr, Xva, yva, lr=1e-3, batch=512, max_epochs=500, patience=20, seed=5, log=None):

@@ -11,8 +11,9 @@ gemv, layernorm, softmax, hist, triad; gemm_variants, the solo throughput of eve
 variant at four shapes; config5_kernels, one launch of each configuration-5
 decoder-layer kernel in order; and victim_bandwidth, which times every memory-bound
 configuration-2 victim alone over grids of 0 (default), 1, 2, 4, 8 and 16 blocks per
-SM (20 launches after a warm measurement), then a triad moving the same bytes per
-launch, and prints one JSON line per run; and
+SM (20 launches after a warm measurement; the GEMV also as variant 1, its rows
+streamed into shared memory), then a triad moving the same bytes per launch, and
+prints one JSON line per run; and
 l2_set_sweep, which times the stream kernel on every SM (256 rounds per block) over
 sets of 8..96 MiB for 2 x 512, 4 x 512 and 2 x 256 threads per SM; and stream_staging,
 which times the HBM (4 GiB) and L2 (16 MiB) stressors with register loads and with TMA
@@ -46,7 +47,7 @@ def main(argv=None):
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--sm-fraction", type=float, default=1.0)
     ap.add_argument("--variant", type=int, default=None,
-                    help="GEMM variant (0, 1, 2 = CTA-pair tiles; default: the workload's)")
+                    help="GEMM variant (0-4) or GEMV variant (0, 1 = rows by bulk copies); default: the workload's")
     ap.add_argument("--block", type=int, default=None, help="stressors: threads per block")
     ap.add_argument("--bps", type=int, default=None, help="stressors: blocks per SM")
     ap.add_argument("--ilp", type=int, default=None, help="FMA / FP64 stressors: chains per thread")
@@ -144,6 +145,20 @@ def main(argv=None):
                 us = t["event_ms"] * 1e3 / 20
                 print(json.dumps({"victim": names[k], "grid": g or prof["grid"], "us_per_launch": round(us, 2),
                                   "gbs": round(prof["bytes_per_launch"] / (us * 1e-6) / 1e9, 1)}))
+            if k == A.IFR_V_GEMV:
+                # the bulk-copy variant (rows streamed into shared memory) on 1 and 2
+                # blocks per SM (default: 2)
+                v.variant, v.grid = 1, 0
+                prof1 = ctx.victim_profile(v)
+                for g in (0, S):
+                    v.grid, v.repeats = g, 20
+                    ctx.victim_launch(v)
+                    t = ctx.victim_launch(v)
+                    us = t["event_ms"] * 1e3 / 20
+                    print(json.dumps({"victim": "gemv variant 1", "grid": g or prof1["grid"],
+                                      "us_per_launch": round(us, 2), "status": t["status"],
+                                      "gbs": round(prof1["bytes_per_launch"] / (us * 1e-6) / 1e9, 1)}))
+                v.variant, v.grid = 0, 0
             # a triad moving the same bytes per launch, timed the same way: the rate a
             # plain stream of this length reaches (launch ramp and tail included)
             n = int(prof["bytes_per_launch"] // 12) // 4 * 4
@@ -187,7 +202,7 @@ def main(argv=None):
             raise SystemExit("unknown case %r" % a.case)
         v = pick[0]
         v.repeats = 1
-        if a.case == "gemm" and a.variant is not None:
+        if a.case in ("gemm", "gemv") and a.variant is not None:
             v.variant = a.variant
         for _ in range(a.repeat):
             t = ctx.victim_launch(v)

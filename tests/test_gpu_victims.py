@@ -117,14 +117,22 @@ def test_softmax_wide_dynamic_range(ctx, cols):
     assert np.allclose(got[11], 1.0 / cols, rtol=1e-6)
 
 
-# rows of up to 256 columns take the short-row kernel (several rows per warp)
-@pytest.mark.parametrize("rows,cols", [(1, 8), (37, 1000), (300, 4096), (8192, 8192), (1000, 128), (77, 256),
-                                       (333, 200), (5, 64), (100003, 8)])
-def test_gemv(ctx, rows, cols):
+# variant 0: rows of up to 256 columns take the short-row kernel (several rows per
+# warp).  Variant 1 (rows streamed into shared memory in 4 KiB segments, a ring of two
+# per warp): rows shorter than a segment, rows that end in a short segment (1000, 2056
+# and 4104 columns), more warps than rows, several rows per warp, the widest x (24576
+# columns), and the full 8192 x 8192 matrix; three launches each.
+@pytest.mark.parametrize("variant,rows,cols", [(0, 1, 8), (0, 37, 1000), (0, 300, 4096), (0, 8192, 8192),
+                                               (0, 1000, 128), (0, 77, 256), (0, 333, 200), (0, 5, 64),
+                                               (0, 100003, 8),
+                                               (1, 1, 8), (1, 37, 1000), (1, 300, 4096), (1, 8192, 8192),
+                                               (1, 5, 2056), (1, 2401, 4104), (1, 100003, 8), (1, 64, 24576)])
+def test_gemv(ctx, variant, rows, cols):
     Ab = I.torch_normal_bf16(7, rows * cols, "cuda").view(rows, cols)
     xb = I.torch_normal_bf16(8, cols, "cuda")
-    y = torch.empty(rows, device="cuda")
-    t = ctx.victim_launch(ifr.victim_cfg(A.IFR_V_GEMV, Ab, xb, y, m=rows, k=cols))
+    y = torch.full((rows,), float("nan"), device="cuda")
+    t = ctx.victim_launch(ifr.victim_cfg(A.IFR_V_GEMV, Ab, xb, y, m=rows, k=cols, variant=variant,
+                                         repeats=3 if variant else 1))
     assert t["status"] == 0
     sel = np.arange(rows)  # every row
     A_np = oracle.f32_bits_to_bf16_bits(I.np_normal_bf16(7, np.arange(rows * cols))).reshape(rows, cols)
@@ -135,6 +143,28 @@ def test_gemv(ctx, rows, cols):
     rms = np.sqrt(np.mean(ref * ref))
     assert np.all(np.abs(got - ref) <= BF16_TOL * np.maximum(np.abs(ref), rms))
     assert np.linalg.norm(got - ref) <= BF16_TOL * np.linalg.norm(ref)
+
+
+def test_gemv_bulk_variant_is_solo_only(ctx):
+    # the bulk-copy GEMV holds 64 KiB of rings plus x per block: solo launches
+    # only; GEMV has no variant 2, and the other row victims have no variant 1
+    Ab = I.torch_normal_bf16(7, 256 * 1024, "cuda").view(256, 1024)
+    xb = I.torch_normal_bf16(8, 1024, "cuda")
+    y = torch.empty(256, device="cuda")
+    bulk = ifr.victim_cfg(A.IFR_V_GEMV, Ab, xb, y, m=256, k=1024, variant=1)
+    plain = ifr.victim_cfg(A.IFR_V_GEMV, Ab, xb, y, m=256, k=1024, variant=0)
+    fma = ifr.stressor_cfg(A.IFR_S_FMA, sm_count=1, block=128, max_rounds=1)
+    for call in (lambda: ctx.sweep([bulk], [], repeats=1), lambda: ctx.corun(bulk, plain),
+                 lambda: ctx.corun(plain, bulk), lambda: ctx.colocate(fma, bulk)):
+        with pytest.raises(ifr.IfrError) as e:
+            call()
+        assert e.value.status == A.IFR_ERR_ARG
+    assert ctx.victim_launch(bulk)["status"] == 0
+    x = torch.empty(256 * 256, device="cuda")
+    for bad in (ifr.victim_cfg(A.IFR_V_GEMV, Ab, xb, y, m=256, k=1024, variant=2),
+                ifr.victim_cfg(A.IFR_V_LAYERNORM, x, None, x, m=256, n=256, variant=1)):
+        with pytest.raises(ifr.IfrError):
+            ctx.victim_launch(bad)
 
 
 @pytest.mark.parametrize("n", [1, 3, 1000003, 1 << 26])

@@ -63,3 +63,15 @@ def test_kernel_corunner_features_pressure_and_fracs():
     assert math.isclose(f["frac_tensor"], 1e11 / 1e-4 / 1.7e15) and f["frac_fp32"] == 0.0
     assert math.isclose(f["log_pressure_hbm_triad"], math.log(2.0)) and f["log_pressure_short_gemv"] == 0.0
     assert math.isclose(f["pressure_max"], math.log(2.0))
+
+
+def test_standardizer_zeroes_features_constant_in_training():
+    rng = np.random.default_rng(0)
+    X = rng.normal(size=(50, 4))
+    X[:, 2] = 0.0  # never varies on the training side
+    z = PR.Standardizer(X)
+    held = np.array([[0.1, -0.2, 0.97, 1e6]])
+    out = z(held)
+    assert out[0, 2] == 0.0 and out[0, 3] == PR.Standardizer.Z_CLIP
+    assert np.allclose(z(X)[:, [0, 1, 3]].mean(axis=0), 0.0, atol=1e-12)
+    assert np.all(z(X)[:, 2] == 0.0)
