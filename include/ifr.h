@@ -453,7 +453,17 @@ typedef struct {
     const ifr_stressor_cfg *levels;      /* [n_stressors][n_levels] full configurations */
     int32_t repeats;                     /* measurements per cell */
     int32_t batched;                     /* 0: launch per cell; 1: one captured CUDA graph
-                                            per (stressor, level) over all victims */
+                                            per (stressor, level) over all victims, each
+                                            victim its own launches; 2: the same graphs
+                                            with grouped persistent victims: layernorm
+                                            and softmax victims of one row template, and
+                                            GEMV victims of more than 256 columns, run
+                                            as one launch per group (at most 32) that
+                                            walks their rows in order, each victim
+                                            still timed on its own (the spans of
+                                            neighbours overlap at the boundary); other
+                                            victims run alone.  Other values:
+                                            IFR_ERR_ARG */
 } ifr_sweep_plan;
 
 typedef struct {

@@ -229,9 +229,10 @@ class Context:
         return _struct_dict(r)
 
     # -- sweep
-    def sweep(self, victims, levels, repeats: int = 3, batched: bool = False):
+    def sweep(self, victims, levels, repeats: int = 3, batched: bool = False, grouped: bool = False):
         """victims: list of ifr_victim_cfg; levels: [n_stressors][n_levels] of
-        ifr_stressor_cfg.  Returns the list of ifr_cell_result."""
+        ifr_stressor_cfg; grouped (with batched): grouped persistent victims.
+        Returns the list of ifr_cell_result."""
         self._sync()
         nv = len(victims)
         ns = len(levels)
@@ -239,7 +240,7 @@ class Context:
         V = (ifr_victim_cfg * nv)(*victims)
         flat = [c for row in levels for c in row]
         S = (ifr_stressor_cfg * max(1, len(flat)))(*flat) if flat else (ifr_stressor_cfg * 1)()
-        plan = ifr_sweep_plan(nv, V, ns, nl, S, repeats, 1 if batched else 0)
+        plan = ifr_sweep_plan(nv, V, ns, nl, S, repeats, (2 if grouped else 1) if batched else 0)
         cap = repeats * nv * (1 + ns * (nl + 1))
         cells = (ifr_cell_result * cap)()
         n = C.c_size_t(0)

@@ -386,6 +386,226 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_kernel(const __grid
     }
 }
 
+// ------------------------------------------------------------------ grouped GEMM
+// The grouped victims of a graph-batched sweep: up to IFR_GROUP_MAX GEMMs of
+// one tile width run as one persistent launch of variant 0's tiles (three stages, one
+// accumulator).  Units are the concatenation of the problems' tiles in order
+// (problem q owns units tile0[q] ..): the first unit of a CTA is its index, later
+// ones come from the device counter of problem 0's record, as in the single kernel,
+// so the CTAs move through the problems in order and neighbouring problems overlap
+// only at the boundary.  Each problem keeps its own measurement record: the producer
+// stamps entry at a tile's first K slice and the epilogue stamps exit (time, SM,
+// count) at a tile's end, so a problem's span runs from its first tile's start to its
+// last tile's end.  Waits are bounded as in the single kernel; a CTA that times out
+// records IFR_ERR_TIMEOUT in every problem's record.
+struct alignas(64) GemmProblem {
+    CUtensorMap ta, tb;
+    float *C;
+    DevTiming *tm;
+    int32_t N, K, tiles_m, tiles_n, tile0, group_m;
+};
+struct GemmGroup {
+    GemmProblem p[IFR_GROUP_MAX];
+    int32_t n, total;
+};
+
+__device__ __forceinline__ int group_problem(const GemmGroup &g, int u) {
+    int q = 0;
+    while (q + 1 < g.n && u >= g.p[q + 1].tile0) ++q;
+    return q;
+}
+
+__device__ __forceinline__ void g_tile_exit(DevTiming *tm, bool count) {
+    const unsigned long long t = ifr_gtimer();
+    atomicMax((unsigned long long *)&tm->t_max, t);
+    if (tm->progress) atomicMax((unsigned long long *)tm->progress, t);
+    if (count) {
+        atomicAdd(&tm->blocks, 1u);
+        const uint32_t s = ifr_smid();
+        if (s < IFR_MAX_SMS) atomicOr(&tm->sm_bits[s >> 5], 1u << (s & 31));
+    }
+}
+
+template <int BN>
+__global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_group_kernel(const __grid_constant__ GemmGroup g) {
+    constexpr int STAGES = 3;
+    using Cf = GemmCfg<BN, STAGES>;
+    constexpr int CHUNKS = BN / 16;
+    extern __shared__ uint8_t g_smem_raw[];
+    uint8_t *base = (uint8_t *)(((uintptr_t)g_smem_raw + 1023u) & ~(uintptr_t)1023u);
+    uint64_t *full = (uint64_t *)(base + STAGES * Cf::STAGE);
+    uint64_t *empty = full + STAGES;
+    uint64_t *tfull = empty + STAGES;
+    uint64_t *tempty = tfull + 1;
+    uint64_t *sfull = tempty + 1;   // [RING] unit index published
+    uint64_t *sempty = sfull + RING;  // [RING] unit index read by the MMA lane and 4 epilogue warps
+    int32_t *ring = (int32_t *)(sempty + RING);
+    uint32_t *tmem_slot = (uint32_t *)(ring + RING);
+    volatile int *fail = (volatile int *)(tmem_slot + 1);
+    DevTiming *const ctl = g.p[0].tm;  // holds the unit counter
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t deadline = ifr_gtimer() + kGemmTimeoutNs;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        for (int r = 0; r < RING; ++r) {
+            tc::mbar_init(&sfull[r], 1);
+            tc::mbar_init(&sempty[r], 1 + EPI_WARPS);
+        }
+        tc::mbar_init(tfull, 1);
+        tc::mbar_init(tempty, EPI_WARPS);
+        *fail = 0;
+        tc::fence_mbar_init();
+        for (int q = 0; q < g.n; ++q) {
+            tc::prefetch_tmap(&g.p[q].ta);
+            tc::prefetch_tmap(&g.p[q].tb);
+        }
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tmem_slot, BN);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        int64_t gs = 0;
+        uint32_t next = blockIdx.x;
+        for (int j = 0;; ++j) {
+            const int r = j % RING;
+            if (j >= RING && !tc::mbar_wait(&sempty[r], (uint32_t)((j / RING) - 1) & 1u, deadline)) *fail = 1;
+            const int unit = (*fail || next >= (uint32_t)g.total) ? -1 : (int)next;
+            ring[r] = unit;
+            tc::mbar_arrive(&sfull[r]);
+            if (unit < 0) break;
+            const int q = group_problem(g, unit);
+            const GemmProblem &pb = g.p[q];
+            int tmi, tni;
+            tile_coords(unit - pb.tile0, pb.tiles_m, pb.tiles_n, pb.group_m, tmi, tni);
+            const int m0 = tmi * BM, n0 = tni * BN, KT = pb.K / BK;
+            g_stamp(pb.tm, true);
+            for (int kt = 0; kt < KT; ++kt, ++gs) {
+                const int s = (int)(gs % STAGES);
+                if (kt == KT - 1) next = gridDim.x + atomicAdd(&ctl->tile_next, 1u);
+                if (gs >= STAGES && !tc::mbar_wait(&empty[s], (uint32_t)((gs / STAGES) - 1) & 1u, deadline)) {
+                    *fail = 1;
+                    break;
+                }
+                uint8_t *sa = base + s * Cf::STAGE;
+                tc::mbar_arrive_expect_tx(&full[s], (uint32_t)Cf::STAGE);
+                tc::tma_load_2d(sa, &pb.ta, &full[s], kt * BK, m0);
+                tc::tma_load_2d(sa + Cf::A_BYTES, &pb.tb, &full[s], kt * BK, n0);
+            }
+        }
+        // drain: the copies of the last stages have landed before the CTA may exit
+        for (int64_t q = gs - STAGES < 0 ? 0 : gs - STAGES; q < gs; ++q)
+            tc::mbar_wait(&full[q % STAGES], (uint32_t)(q / STAGES) & 1u, deadline + 100000000ull);
+    } else if (warp == 1 && lane == 0) {
+        constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+        int64_t gs = 0;
+        for (int j = 0;; ++j) {
+            const int r = j % RING;
+            const bool got = tc::mbar_wait(&sfull[r], (uint32_t)(j / RING) & 1u, deadline + 50000000ull);
+            const int unit = got ? ring[r] : -1;
+            tc::mbar_arrive(&sempty[r]);
+            if (!got) *fail = 1;
+            if (unit < 0) break;
+            const int KT = g.p[group_problem(g, unit)].K / BK;
+            if (j >= 1 && !tc::mbar_wait(tempty, (uint32_t)((j - 1) & 1), deadline)) {
+                *fail = 1;
+                tc::mma_commit(tfull);
+                continue;  // read the ring on to its end marker
+            }
+            tc::fence_after();
+            for (int kt = 0; kt < KT; ++kt, ++gs) {
+                const int s = (int)(gs % STAGES);
+                if (!tc::mbar_wait(&full[s], (uint32_t)(gs / STAGES) & 1u, deadline)) {
+                    *fail = 1;
+                    break;
+                }
+                tc::fence_after();
+                const uint32_t sa = tc::smem_u32(base + s * Cf::STAGE);
+                const uint64_t adesc = tc::desc_sw128(sa);
+                const uint64_t bdesc = tc::desc_sw128(sa + Cf::A_BYTES);
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk)
+                    tc::mma_bf16(tmem, adesc + 2ull * kk, bdesc + 2ull * kk, idesc, (uint32_t)((kt | kk) != 0));
+                tc::mma_commit(&empty[s]);
+            }
+            tc::mma_commit(tfull);  // also on failure, so the epilogue's wait completes
+        }
+    } else if (warp >= 2) {
+        const int qd = warp & 3;  // TMEM lane quadrant this warp may access
+        const uint32_t trow = tmem + ((uint32_t)(qd * 32) << 16);
+        for (int j = 0;; ++j) {
+            const int r = j % RING;
+            const bool got = tc::mbar_wait(&sfull[r], (uint32_t)(j / RING) & 1u, deadline + 50000000ull);
+            const int unit = got ? ring[r] : -1;
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&sempty[r]);
+            if (!__all_sync(0xffffffffu, got)) {
+                if (lane == 0) *fail = 1;
+                break;
+            }
+            if (unit < 0) break;
+            const bool ok = tc::mbar_wait(tfull, (uint32_t)(j & 1), deadline + 100000000ull);
+            tc::fence_after();
+            if (!__all_sync(0xffffffffu, ok && !*fail)) {
+                if (lane == 0) *fail = 1;
+                break;
+            }
+            const GemmProblem &pb = g.p[group_problem(g, unit)];
+            int tmi, tni;
+            tile_coords(unit - pb.tile0, pb.tiles_m, pb.tiles_n, pb.group_m, tmi, tni);
+            const int m0 = tmi * BM, n0 = tni * BN;
+            float *crow = pb.C + (size_t)(m0 + qd * 32 + lane) * (size_t)pb.N + n0;
+            uint32_t ra[16], rb[16];
+            tc::tmem_ld16(trow, ra);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int c = 0; c < CHUNKS; c += 2) {
+                tc::tmem_ld16(trow + (uint32_t)((c + 1) * 16), rb);
+                store_row16(crow + c * 16, ra);
+                tc::tmem_ld_wait();
+                if (c + 2 < CHUNKS) {
+                    tc::tmem_ld16(trow + (uint32_t)((c + 2) * 16), ra);
+                    store_row16(crow + (c + 1) * 16, rb);
+                    tc::tmem_ld_wait();
+                } else {
+                    tc::fence_before();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(tempty);  // accumulator drained
+                    store_row16(crow + (c + 1) * 16, rb);
+                }
+            }
+            // every epilogue warp stamps the tile's end (the latest of the four is the
+            // tile's exit); warp 2 also counts the tile and its SM
+            __syncwarp();
+            if (lane == 0) g_tile_exit(pb.tm, warp == 2);
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc::fence_after();
+        tc::tmem_dealloc(tmem, BN);
+    }
+    if (threadIdx.x == 0 && *fail)
+        for (int q = 0; q < g.n; ++q) g.p[q].tm->status = IFR_ERR_TIMEOUT;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&ctl->tile_done, 1u) == gridDim.x - 1u) {
+            atomicExch(&ctl->tile_next, 0u);
+            atomicExch(&ctl->tile_done, 0u);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ 2-SM pair tiles
 // Variant 2: a cluster of two CTAs on two SMs takes 256 x 256 output tiles with
 // tcgen05.mma.cta_group::2 (M = 256, N = 256, K = 16), issued by the even CTA (the
@@ -1146,6 +1366,17 @@ int launch_gemm_mc(const ifr_victim_cfg *c, cudaStream_t stream, int group_m, De
     return e == cudaSuccess ? IFR_OK : IFR_ERR_LAUNCH;
 }
 
+template <int BN>
+const void *gemm_group_fn() {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(gemm_bf16_group_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             GemmCfg<BN, 3>::SMEM);
+        attr = true;
+    }
+    return (const void *)gemm_bf16_group_kernel<BN>;
+}
+
 }  // namespace
 
 int ifr_gemm_shape(const ifr_victim_cfg *c, VictimShape *s) {
@@ -1209,13 +1440,71 @@ int ifr_gemm_enqueue(ifr_ctx *ctx, const ifr_victim_cfg *c, cudaStream_t stream,
                 : launch_gemm<128, 3, 1>(ctx, c, stream, gm, false, tm);
 }
 
+// Grouping key of a GEMM victim (0 = alone): variant-0 GEMMs group by tile width.
+int ifr_gemm_group_key(const ifr_victim_cfg *c) {
+    if (c->variant != 0 || c->grid) return 0;
+    return c->n % 256 == 0 ? 402 : 401;
+}
+
+// K grouped launches of GEMM victims vs[0..n-1] of one tile width (validated by the
+// caller), victim i stamping into tms[i].
+int ifr_gemm_enqueue_group(ifr_ctx *ctx, const ifr_victim_cfg *const *vs, DevTiming *const *tms, int n,
+                           cudaStream_t stream) {
+    if (n <= 0 || n > IFR_GROUP_MAX) return IFR_ERR_ARG;
+    g_num_sms = ctx->info.num_sms;
+    const int key = ifr_gemm_group_key(vs[0]);
+    if (key <= 0) return IFR_ERR_ARG;
+    const bool wide = key == 402;
+    const int BN = wide ? 256 : 128;
+    GemmGroup g;
+    memset(&g, 0, sizeof g);
+    int64_t tile0 = 0;
+    for (int i = 0; i < n; ++i) {
+        const ifr_victim_cfg *c = vs[i];
+        if (ifr_gemm_group_key(c) != key || c->m > 65535 * BM || c->n > (1ll << 30) || c->k > (1ll << 30))
+            return IFR_ERR_ARG;
+        GemmProblem &pb = g.p[i];
+        int rc = make_map(&pb.ta, c->in0, c->m, c->k, BM);
+        if (!rc) rc = make_map(&pb.tb, c->in1, c->n, c->k, BN);
+        if (rc) return rc;
+        pb.C = (float *)c->out;
+        pb.tm = tms[i];
+        pb.N = (int32_t)c->n;
+        pb.K = (int32_t)c->k;
+        pb.tiles_m = (int32_t)(c->m / BM);
+        pb.tiles_n = (int32_t)(c->n / BN);
+        pb.tile0 = (int32_t)tile0;
+        const double operand_bytes = 2.0 * ((double)c->m + (double)c->n) * (double)c->k;
+        pb.group_m = operand_bytes > (double)ctx->info.l2_bytes ? GROUP_M : 1;
+        tile0 += (int64_t)pb.tiles_m * pb.tiles_n;
+        if (tile0 >= (1ll << 31)) return IFR_ERR_ARG;
+    }
+    g.n = n;
+    g.total = (int32_t)tile0;
+    const void *fn = wide ? gemm_group_fn<256>() : gemm_group_fn<128>();
+    ifr_carveout(fn);
+    const int grid = g.total < g_num_sms ? g.total : g_num_sms;
+    const int K = vs[0]->repeats > 0 ? vs[0]->repeats : 1;
+    for (int rep = 0; rep < K; ++rep) {
+        if (wide)
+            gemm_bf16_group_kernel<256><<<grid, GEMM_THREADS, GemmCfg<256, 3>::SMEM, stream>>>(g);
+        else
+            gemm_bf16_group_kernel<128><<<grid, GEMM_THREADS, GemmCfg<128, 3>::SMEM, stream>>>(g);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return ifr_cuda_fail(e, "grouped GEMM launch", __FILE__, __LINE__);
+        ctx->kernel_launches += 1;
+    }
+    return IFR_OK;
+}
+
 // After a launch that failed part-way the split counters may be off by a few
 // arrivals: the next split launch starts from zero.
 void ifr_gemm_forget_split(ifr_ctx *ctx) { ctx->gemm_cnt_key = -1; }
 
 int ifr_preload_gemm() {
     const void *fns[] = {gemm_fn<128, 3, 1>(), gemm_fn<256, 3, 1>(), gemm_fn<128, 4, 1>(), gemm_fn<256, 4, 1>(),
-                         gemm_fn<128, 4, 2>(), gemm_fn<256, 4, 2>(), gemm_pair_fn<6, 2, true>(), gemm_mc_fn<4>()};
+                         gemm_fn<128, 4, 2>(), gemm_fn<256, 4, 2>(), gemm_pair_fn<6, 2, true>(), gemm_mc_fn<4>(),
+                         gemm_group_fn<128>(), gemm_group_fn<256>()};
     for (const void *f : fns) {
         int rc = ifr_preload(f);
         if (rc) return rc;

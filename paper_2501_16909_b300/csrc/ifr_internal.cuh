@@ -192,6 +192,14 @@ void ifr_timing_to_host(const DevTiming &d, int repeats, ifr_timing *out);
 int ifr_ensure_timing(ifr_ctx *ctx, int n);
 
 // Launch shape and algorithmic work of one victim launch.
+// Grouped victims (graph-batched sweeps with grouping): the grouping key of a victim
+// (victims with equal keys > 0 may share one persistent launch; 0 = launched alone)
+// and the grouped launch of n such victims, victim i stamping into tms[i].
+#define IFR_GROUP_MAX 16
+int ifr_victim_group_key(ifr_ctx *ctx, const ifr_victim_cfg *cfg);
+int ifr_victims_enqueue_group(ifr_ctx *ctx, const ifr_victim_cfg *const *victims, DevTiming *const *tms, int n,
+                              cudaStream_t stream);
+
 struct VictimShape {
     const void *fn;
     int grid, block, smem, tmem_cols, uses_tensor;
@@ -202,4 +210,7 @@ int ifr_victim_shape(ifr_ctx *ctx, const ifr_victim_cfg *cfg, VictimShape *s);
 // GEMM (ifr_gemm.cu)
 int ifr_gemm_enqueue(ifr_ctx *ctx, const ifr_victim_cfg *cfg, cudaStream_t stream, DevTiming *tm);
 int ifr_gemm_shape(const ifr_victim_cfg *cfg, VictimShape *s);
+int ifr_gemm_group_key(const ifr_victim_cfg *cfg);
+int ifr_gemm_enqueue_group(ifr_ctx *ctx, const ifr_victim_cfg *const *victims, DevTiming *const *tms, int n,
+                           cudaStream_t stream);
 void ifr_gemm_forget_split(ifr_ctx *ctx);

@@ -7,7 +7,9 @@
 //                     -> stop flag (copy-engine write, so it needs no SM slot)
 // Batched mode, per (stressor, level): the same sequence with all victims
 // back to back under one stressor run, captured once into a CUDA graph and
-// replayed for every repeat; per-victim timings land in separate slots.
+// replayed for every repeat; per-victim timings land in separate slots.  Grouped
+// batched mode: the same graphs, with victims of one row kernel run as one
+// persistent grouped launch that walks their rows (ifr_victims_enqueue_group).
 #include <math.h>
 #include <string.h>
 #include <time.h>
@@ -109,7 +111,39 @@ int measure_cell_plain(ifr_ctx *ctx, const ifr_victim_cfg *v, const ifr_stressor
     return IFR_OK;
 }
 
-// Capture one graph: optional stressor + all victims back to back.
+// The victims of a grouped batch: victims with the same grouping key and launch count
+// run as one grouped launch (at most IFR_GROUP_MAX victims each), placed where the
+// first of them stands in the plan; the others run alone, in plan order.  Each victim
+// keeps its own measurement record.
+int enqueue_victims_grouped(ifr_ctx *ctx, const ifr_sweep_plan *p, cudaStream_t sv) {
+    const int nv = p->n_victims;
+    std::vector<int> key((size_t)nv), done((size_t)nv, 0);
+    for (int v = 0; v < nv; ++v) key[v] = ifr_victim_group_key(ctx, &p->victims[v]);
+    auto reps = [&](int v) { return p->victims[v].repeats > 0 ? p->victims[v].repeats : 1; };
+    for (int v = 0; v < nv; ++v) {
+        if (done[v]) continue;
+        done[v] = 1;
+        int rc;
+        if (key[v] <= 0) {
+            rc = ifr_victim_enqueue(ctx, &p->victims[v], sv, ctx->d_timing + v);
+        } else {
+            std::vector<const ifr_victim_cfg *> vs(1, &p->victims[v]);
+            std::vector<DevTiming *> tms(1, ctx->d_timing + v);
+            for (int w = v + 1; w < nv && (int)vs.size() < IFR_GROUP_MAX; ++w)
+                if (!done[w] && key[w] == key[v] && reps(w) == reps(v)) {
+                    done[w] = 1;
+                    vs.push_back(&p->victims[w]);
+                    tms.push_back(ctx->d_timing + w);
+                }
+            rc = ifr_victims_enqueue_group(ctx, vs.data(), tms.data(), (int)vs.size(), sv);
+        }
+        if (rc) return rc;
+    }
+    return IFR_OK;
+}
+
+// Capture one graph: optional stressor + all victims back to back (grouped when the
+// plan asks for it).
 int capture_batch(ifr_ctx *ctx, const ifr_sweep_plan *p, const ifr_stressor_cfg *scfg, int slot,
                   cudaGraphExec_t *exec, uint64_t *kernels) {
     const uint64_t before = ctx->kernel_launches;
@@ -128,7 +162,11 @@ int capture_batch(ifr_ctx *ctx, const ifr_sweep_plan *p, const ifr_stressor_cfg 
         rc = ifr_stressor_enqueue(ctx, scfg, ss, slot, 0);
         if (!rc) rc = ifr_enqueue_wait_resident(ctx, slot, sv, ctx->d_timing, kResidencyTimeoutNs);
     }
-    for (int v = 0; !rc && v < p->n_victims; ++v) rc = ifr_victim_enqueue(ctx, &p->victims[v], sv, ctx->d_timing + v);
+    if (!rc && p->batched == 2)
+        rc = enqueue_victims_grouped(ctx, p, sv);
+    else
+        for (int v = 0; !rc && v < p->n_victims; ++v)
+            rc = ifr_victim_enqueue(ctx, &p->victims[v], sv, ctx->d_timing + v);
     if (!rc && scfg) {
         rc = ifr_enqueue_stop(ctx, slot, sv);
         cudaEventRecord(join, ss);
@@ -465,7 +503,8 @@ extern "C" int ifr_colocate(ifr_ctx *ctx, const ifr_stressor_cfg *sc, const ifr_
 
 extern "C" int ifr_sweep(ifr_ctx *ctx, const ifr_sweep_plan *p, ifr_cell_result *cells, size_t cap, size_t *n_out) {
     if (!ctx || !p || !n_out || p->n_victims <= 0 || !p->victims || p->n_stressors < 0 ||
-        p->n_stressors > IFR_MAX_STRESSORS || p->n_levels < 0 || p->n_levels > IFR_MAX_LEVELS || p->repeats <= 0)
+        p->n_stressors > IFR_MAX_STRESSORS || p->n_levels < 0 || p->n_levels > IFR_MAX_LEVELS || p->repeats <= 0 ||
+        p->batched < 0 || p->batched > 2)
         return IFR_ERR_ARG;
     if (p->n_stressors > 0 && (p->n_levels <= 0 || !p->levels)) return IFR_ERR_ARG;
     *n_out = 0;

@@ -167,105 +167,110 @@ __device__ __forceinline__ float block_max(float v, float *red) {
 // and 16-byte aligned rows; otherwise (any width) the last slot is padded with the
 // row mean, which adds nothing to the variance, and stores are per column.
 template <int NT, int VPT, bool VEC>
+__device__ __forceinline__ void layernorm_row(const float *__restrict__ xr, float *__restrict__ yr, int cols,
+                                              float eps, float *red) {
+    const int c4 = (cols + 3) >> 2;
+    const float inv_n = 1.0f / (float)cols;
+    float4 v[VPT];
+    float s = 0.f;
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) {
+        const int j = threadIdx.x + u * NT;
+        v[u] = j < c4 ? ld_slot<VEC>(xr, j, cols, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+        s += (v[u].x + v[u].y) + (v[u].z + v[u].w);
+    }
+    const float mean = block_sum<NT>(s, red) * inv_n;
+    float q = 0.f;
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) {
+        const int j = threadIdx.x + u * NT;
+        if (j < c4) {
+            if constexpr (!VEC) {
+                const int e = 4 * j;
+                if (e + 1 >= cols) v[u].y = mean;
+                if (e + 2 >= cols) v[u].z = mean;
+                if (e + 3 >= cols) v[u].w = mean;
+            }
+            const float a = v[u].x - mean, b = v[u].y - mean, c = v[u].z - mean, d = v[u].w - mean;
+            q += (a * a + b * b) + (c * c + d * d);
+        }
+    }
+    const float var = block_sum<NT>(q, red) * inv_n;
+    const float inv = 1.0f / sqrtf(var + eps);
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) {
+        const int j = threadIdx.x + u * NT;
+        if (j < c4) {
+            float4 o;
+            o.x = (v[u].x - mean) * inv;
+            o.y = (v[u].y - mean) * inv;
+            o.z = (v[u].z - mean) * inv;
+            o.w = (v[u].w - mean) * inv;
+            st_slot<VEC>(yr, j, cols, o);
+        }
+    }
+}
+
+template <int NT, int VPT, bool VEC>
 __global__ void __launch_bounds__(NT) layernorm_kernel(const float *__restrict__ x, float *__restrict__ y,
                                                        int64_t rows, int cols, float eps, DevTiming *tm) {
     __shared__ float red[32];
     v_enter(tm);
-    const int c4 = (cols + 3) >> 2;
-    const float inv_n = 1.0f / (float)cols;
-    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
-        const float *xr = x + r * cols;
-        float4 v[VPT];
-        float s = 0.f;
-#pragma unroll
-        for (int u = 0; u < VPT; ++u) {
-            const int j = threadIdx.x + u * NT;
-            v[u] = j < c4 ? ld_slot<VEC>(xr, j, cols, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
-            s += (v[u].x + v[u].y) + (v[u].z + v[u].w);
-        }
-        const float mean = block_sum<NT>(s, red) * inv_n;
-        float q = 0.f;
-#pragma unroll
-        for (int u = 0; u < VPT; ++u) {
-            const int j = threadIdx.x + u * NT;
-            if (j < c4) {
-                if constexpr (!VEC) {
-                    const int e = 4 * j;
-                    if (e + 1 >= cols) v[u].y = mean;
-                    if (e + 2 >= cols) v[u].z = mean;
-                    if (e + 3 >= cols) v[u].w = mean;
-                }
-                const float a = v[u].x - mean, b = v[u].y - mean, c = v[u].z - mean, d = v[u].w - mean;
-                q += (a * a + b * b) + (c * c + d * d);
-            }
-        }
-        const float var = block_sum<NT>(q, red) * inv_n;
-        const float inv = 1.0f / sqrtf(var + eps);
-        float *yr = y + r * cols;
-#pragma unroll
-        for (int u = 0; u < VPT; ++u) {
-            const int j = threadIdx.x + u * NT;
-            if (j < c4) {
-                float4 o;
-                o.x = (v[u].x - mean) * inv;
-                o.y = (v[u].y - mean) * inv;
-                o.z = (v[u].z - mean) * inv;
-                o.w = (v[u].w - mean) * inv;
-                st_slot<VEC>(yr, j, cols, o);
-            }
-        }
-    }
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x)
+        layernorm_row<NT, VPT, VEC>(x + r * cols, y + r * cols, cols, eps, red);
     v_exit(tm);
 }
 
 // Row softmax: max, sum of exp(x - max), divide.  Same layout as layernorm; columns
 // past the row's end read as -inf, so they add nothing to the max or the sum.
 template <int NT, int VPT, bool VEC>
+__device__ __forceinline__ void softmax_row(const float *__restrict__ xr, float *__restrict__ yr, int cols,
+                                            float *red) {
+    const int c4 = (cols + 3) >> 2;
+    float4 v[VPT];
+    float m = -INFINITY;
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) {
+        const int j = threadIdx.x + u * NT;
+        if (j < c4) {
+            v[u] = ld_slot<VEC>(xr, j, cols, -INFINITY);
+            m = fmaxf(m, fmaxf(fmaxf(v[u].x, v[u].y), fmaxf(v[u].z, v[u].w)));
+        }
+    }
+    const float mx = block_max<NT>(m, red);
+    float s = 0.f;
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) {
+        const int j = threadIdx.x + u * NT;
+        if (j < c4) {
+            v[u].x = expf(v[u].x - mx);
+            v[u].y = expf(v[u].y - mx);
+            v[u].z = expf(v[u].z - mx);
+            v[u].w = expf(v[u].w - mx);
+            s += (v[u].x + v[u].y) + (v[u].z + v[u].w);
+        }
+    }
+    const float inv = 1.0f / block_sum<NT>(s, red);
+#pragma unroll
+    for (int u = 0; u < VPT; ++u) {
+        const int j = threadIdx.x + u * NT;
+        if (j < c4) {
+            float4 o;
+            o.x = v[u].x * inv;
+            o.y = v[u].y * inv;
+            o.z = v[u].z * inv;
+            o.w = v[u].w * inv;
+            st_slot<VEC>(yr, j, cols, o);
+        }
+    }
+}
+
+template <int NT, int VPT, bool VEC>
 __global__ void __launch_bounds__(NT) softmax_kernel(const float *__restrict__ x, float *__restrict__ y,
                                                      int64_t rows, int cols, DevTiming *tm) {
     __shared__ float red[32];
     v_enter(tm);
-    const int c4 = (cols + 3) >> 2;
-    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
-        const float *xr = x + r * cols;
-        float4 v[VPT];
-        float m = -INFINITY;
-#pragma unroll
-        for (int u = 0; u < VPT; ++u) {
-            const int j = threadIdx.x + u * NT;
-            if (j < c4) {
-                v[u] = ld_slot<VEC>(xr, j, cols, -INFINITY);
-                m = fmaxf(m, fmaxf(fmaxf(v[u].x, v[u].y), fmaxf(v[u].z, v[u].w)));
-            }
-        }
-        const float mx = block_max<NT>(m, red);
-        float s = 0.f;
-#pragma unroll
-        for (int u = 0; u < VPT; ++u) {
-            const int j = threadIdx.x + u * NT;
-            if (j < c4) {
-                v[u].x = expf(v[u].x - mx);
-                v[u].y = expf(v[u].y - mx);
-                v[u].z = expf(v[u].z - mx);
-                v[u].w = expf(v[u].w - mx);
-                s += (v[u].x + v[u].y) + (v[u].z + v[u].w);
-            }
-        }
-        const float inv = 1.0f / block_sum<NT>(s, red);
-        float *yr = y + r * cols;
-#pragma unroll
-        for (int u = 0; u < VPT; ++u) {
-            const int j = threadIdx.x + u * NT;
-            if (j < c4) {
-                float4 o;
-                o.x = v[u].x * inv;
-                o.y = v[u].y * inv;
-                o.z = v[u].z * inv;
-                o.w = v[u].w * inv;
-                st_slot<VEC>(yr, j, cols, o);
-            }
-        }
-    }
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) softmax_row<NT, VPT, VEC>(x + r * cols, y + r * cols, cols, red);
     v_exit(tm);
 }
 
@@ -508,6 +513,144 @@ const void *gemv_short_fn(int lanes) {
         case 16: return (const void *)gemv_short_kernel<16>;
         default: return (const void *)gemv_short_kernel<32>;
     }
+}
+
+// ------------------------------------------------------------------ grouped victims
+// A grouped launch runs several victims of one row kernel (one template: same block
+// shape and row capacity) as one persistent launch, for the graph-batched sweep: the
+// blocks (layernorm, softmax) or warps (GEMV) walk the concatenation of the victims'
+// rows in order, block or warp b taking rows b, b + G, ...  Each victim keeps its own
+// measurement record: a block or warp stamps entry when its walk enters a victim's
+// rows and exit when it leaves them, so a victim's span runs from the first entry into
+// its rows to the last exit from them (neighbouring victims overlap at the boundary,
+// as in any grouped kernel).  Row arithmetic is the single-victim kernels' own.
+struct RowVictim {
+    const void *in0, *in1;
+    void *out;
+    int64_t row0, rows;
+    DevTiming *tm;
+    int32_t cols;
+    float eps;
+};
+struct RowGroup {
+    int32_t n;
+    int64_t total;
+    RowVictim v[IFR_GROUP_MAX];
+};
+
+// The victim of global row r, searching forward from the walker's current one.
+__device__ __forceinline__ int group_victim(const RowGroup &g, int from, int64_t r) {
+    int v = from < 0 ? 0 : from;
+    while (v + 1 < g.n && r >= g.v[v + 1].row0) ++v;
+    return v;
+}
+
+template <int NT, int VPT, bool VEC, bool LN>
+__global__ void __launch_bounds__(NT) rows_group_kernel(const __grid_constant__ RowGroup g) {
+    __shared__ float red[32];
+    int cur = -1;
+    for (int64_t r = blockIdx.x; r < g.total; r += gridDim.x) {
+        const int v = group_victim(g, cur, r);
+        if (v != cur) {
+            if (cur >= 0) v_exit(g.v[cur].tm);
+            v_enter(g.v[v].tm);
+            cur = v;
+        }
+        const RowVictim &d = g.v[v];
+        const int64_t lr = r - d.row0;
+        const float *xr = (const float *)d.in0 + lr * d.cols;
+        float *yr = (float *)d.out + lr * d.cols;
+        if constexpr (LN)
+            layernorm_row<NT, VPT, VEC>(xr, yr, d.cols, d.eps, red);
+        else
+            softmax_row<NT, VPT, VEC>(xr, yr, d.cols, red);
+    }
+    if (cur >= 0) v_exit(g.v[cur].tm);
+}
+
+// Per-warp stamps for the grouped GEMV, whose warps of one block can be in different
+// victims' rows.
+__device__ __forceinline__ void w_enter(DevTiming *tm, int lane) {
+    if (lane == 0) {
+        const unsigned long long t = ifr_gtimer();
+        atomicMin((unsigned long long *)&tm->t_min, t);
+        if (tm->progress) atomicMax((unsigned long long *)tm->progress, t);
+    }
+}
+__device__ __forceinline__ void w_exit(DevTiming *tm, int lane) {
+    __syncwarp();
+    if (lane == 0) {
+        const unsigned long long t = ifr_gtimer();
+        atomicMax((unsigned long long *)&tm->t_max, t);
+        if (tm->progress) atomicMax((unsigned long long *)tm->progress, t);
+        atomicAdd(&tm->blocks, 1u);
+        const uint32_t s = ifr_smid();
+        if (s < IFR_MAX_SMS) atomicOr(&tm->sm_bits[s >> 5], 1u << (s & 31));
+    }
+}
+
+// Grouped GEMV (rows of more than 256 columns): one warp per row as in gemv_kernel,
+// with x read through the L1 (each victim has its own x, and the warps of a block can
+// be in different victims, so x is not staged per block).
+__global__ void __launch_bounds__(256) gemv_group_kernel(const __grid_constant__ RowGroup g) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
+    int cur = -1;
+    for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; r < g.total; r += W) {
+        const int v = group_victim(g, cur, r);
+        if (v != cur) {
+            if (cur >= 0) w_exit(g.v[cur].tm, lane);
+            w_enter(g.v[v].tm, lane);
+            cur = v;
+        }
+        const RowVictim &d = g.v[v];
+        const int c8 = d.cols >> 3;
+        const uint4 *ar = (const uint4 *)((const __nv_bfloat16 *)d.in0 + (r - d.row0) * d.cols);
+        const uint4 *xv4 = (const uint4 *)d.in1;
+        float acc = 0.f;
+        int j = lane;
+        for (; j + 96 < c8; j += 128) {
+            uint4 av[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                int4 t;
+                asm volatile("ld.global.nc.L1::no_allocate.v4.s32 {%0,%1,%2,%3}, [%4];"
+                             : "=r"(t.x), "=r"(t.y), "=r"(t.z), "=r"(t.w)
+                             : "l"(ar + j + 32 * u));
+                av[u] = make_uint4((uint32_t)t.x, (uint32_t)t.y, (uint32_t)t.z, (uint32_t)t.w);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint4 xv = __ldg(xv4 + j + 32 * u);
+                const __nv_bfloat162 *a2 = (const __nv_bfloat162 *)&av[u];
+                const __nv_bfloat162 *x2 = (const __nv_bfloat162 *)&xv;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float2 af = __bfloat1622float2(a2[e]);
+                    const float2 xf = __bfloat1622float2(x2[e]);
+                    acc = fmaf(af.x, xf.x, acc);
+                    acc = fmaf(af.y, xf.y, acc);
+                }
+            }
+        }
+        for (; j < c8; j += 32) {
+            const uint4 av = ar[j];
+            const uint4 xv = __ldg(xv4 + j);
+            const __nv_bfloat162 *a2 = (const __nv_bfloat162 *)&av;
+            const __nv_bfloat162 *x2 = (const __nv_bfloat162 *)&xv;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float2 af = __bfloat1622float2(a2[e]);
+                const float2 xf = __bfloat1622float2(x2[e]);
+                acc = fmaf(af.x, xf.x, acc);
+                acc = fmaf(af.y, xf.y, acc);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) ((float *)d.out)[r - d.row0] = acc;
+    }
+    if (cur >= 0) w_exit(g.v[cur].tm, lane);
 }
 
 // ------------------------------------------------------------------ histogram
@@ -775,6 +918,98 @@ int ifr_victim_enqueue(ifr_ctx *ctx, const ifr_victim_cfg *c, cudaStream_t strea
     return IFR_OK;
 }
 
+// Grouping key (0 = launched alone): layernorm and softmax victims group by kind, row
+// template (the column capacity class) and load path; GEMV victims with rows of more
+// than 256 columns (variant 0) form one group; variant-0 GEMMs group by tile width; a
+// victim with an explicit grid keeps its own launch, and the other kinds run alone.
+int ifr_victim_group_key(ifr_ctx *ctx, const ifr_victim_cfg *c) {
+    (void)ctx;
+    if (c->grid) return 0;
+    switch (c->kind) {
+        case IFR_V_LAYERNORM:
+        case IFR_V_SOFTMAX: {
+            const int c4 = (int)((c->n + 3) / 4);
+            const int cls = c4 <= 256 * 4 ? 1 : (c4 <= 256 * 8 ? 2 : 3);
+            return (c->kind == IFR_V_LAYERNORM ? 100 : 200) + cls * 2 + (rows_vec(c) ? 1 : 0);
+        }
+        case IFR_V_GEMV: return (c->variant == 0 && !gemv_short_lanes(c->k)) ? 300 : 0;
+        case IFR_V_GEMM: return ifr_gemm_group_key(c);
+        default: return 0;
+    }
+}
+
+template <int NT, int VPT, bool VEC, bool LN>
+void launch_rows_group(const RowGroup &g, int grid, cudaStream_t st) {
+    ifr_carveout((const void *)rows_group_kernel<NT, VPT, VEC, LN>);
+    rows_group_kernel<NT, VPT, VEC, LN><<<grid, NT, 0, st>>>(g);
+}
+
+template <bool LN>
+void launch_rows_group_cls(const RowGroup &g, int cls, bool vec, int grid, cudaStream_t st) {
+    if (vec) {
+        if (cls == 1) launch_rows_group<256, 4, true, LN>(g, grid, st);
+        else if (cls == 2) launch_rows_group<256, 8, true, LN>(g, grid, st);
+        else launch_rows_group<1024, 8, true, LN>(g, grid, st);
+    } else {
+        if (cls == 1) launch_rows_group<256, 4, false, LN>(g, grid, st);
+        else if (cls == 2) launch_rows_group<256, 8, false, LN>(g, grid, st);
+        else launch_rows_group<1024, 8, false, LN>(g, grid, st);
+    }
+}
+
+// K grouped launches of victims vs[0..n-1] (one grouping key, one launch count K),
+// victim i stamping into tms[i].  Grids as the single-victim defaults: 8 blocks of
+// 256 threads (2 of 1024) per SM, at most one block per row (GEMV: per 8 rows).
+int ifr_victims_enqueue_group(ifr_ctx *ctx, const ifr_victim_cfg *const *vs, DevTiming *const *tms, int n,
+                              cudaStream_t stream) {
+    if (!ctx || !vs || !tms || n <= 0 || n > IFR_GROUP_MAX) return IFR_ERR_ARG;
+    const int key = ifr_victim_group_key(ctx, vs[0]);
+    if (key <= 0) return IFR_ERR_ARG;
+    const int K = vs[0]->repeats > 0 ? vs[0]->repeats : 1;
+    RowGroup g;
+    memset(&g, 0, sizeof g);
+    g.n = n;
+    int64_t row0 = 0;
+    for (int i = 0; i < n; ++i) {
+        const ifr_victim_cfg *c = vs[i];
+        int rc = ifr_victim_validate(ctx, c);
+        if (rc) return rc;
+        if (ifr_victim_group_key(ctx, c) != key || (c->repeats > 0 ? c->repeats : 1) != K) return IFR_ERR_ARG;
+        if (c->kind == IFR_V_GEMM) continue;
+        RowVictim &d = g.v[i];
+        d.in0 = c->in0;
+        d.in1 = c->in1;
+        d.out = c->out;
+        d.row0 = row0;
+        d.rows = c->m;
+        d.tm = tms[i];
+        d.cols = (int32_t)(c->kind == IFR_V_GEMV ? c->k : c->n);
+        d.eps = c->eps > 0.f ? c->eps : 1e-5f;
+        row0 += c->m;
+    }
+    if (vs[0]->kind == IFR_V_GEMM) return ifr_gemm_enqueue_group(ctx, vs, tms, n, stream);
+    g.total = row0;
+    const int64_t sms = ctx->info.num_sms;
+    for (int rep = 0; rep < K; ++rep) {
+        if (vs[0]->kind == IFR_V_GEMV) {
+            const int64_t need = (g.total + 7) / 8;
+            ifr_carveout((const void *)gemv_group_kernel);
+            gemv_group_kernel<<<(int)(need < sms * 8 ? need : sms * 8), 256, 0, stream>>>(g);
+        } else {
+            const int cls = (key % 100) / 2;
+            const bool vec = key % 2;
+            const int64_t per = cls == 3 ? 2 : 8;
+            const int grid = (int)(g.total < sms * per ? g.total : sms * per);
+            if (vs[0]->kind == IFR_V_LAYERNORM) launch_rows_group_cls<true>(g, cls, vec, grid, stream);
+            else launch_rows_group_cls<false>(g, cls, vec, grid, stream);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return ifr_cuda_fail(e, "grouped victim launch", __FILE__, __LINE__);
+        ctx->kernel_launches += 1;
+    }
+    return IFR_OK;
+}
+
 extern "C" int ifr_victim_profile(ifr_ctx *ctx, const ifr_victim_cfg *cfg, ifr_kernel_profile *out) {
     if (!ctx || !out) return IFR_ERR_ARG;
     int rc = ifr_victim_validate(ctx, cfg);
@@ -840,7 +1075,14 @@ int ifr_preload_victims() {
         (const void *)timing_reset_kernel, (const void *)triad_kernel, (const void *)gemv_kernel,
         (const void *)gemv_bulk_kernel,
         gemv_short_fn(1), gemv_short_fn(2), gemv_short_fn(4), gemv_short_fn(8), gemv_short_fn(16), gemv_short_fn(32),
-        (const void *)hist_kernel, row_fn<true>(true, 1), row_fn<true>(true, 2048), row_fn<true>(true, 4096),
+        (const void *)hist_kernel, (const void *)gemv_group_kernel,
+        (const void *)rows_group_kernel<256, 4, true, true>, (const void *)rows_group_kernel<256, 8, true, true>,
+        (const void *)rows_group_kernel<1024, 8, true, true>, (const void *)rows_group_kernel<256, 4, false, true>,
+        (const void *)rows_group_kernel<256, 8, false, true>, (const void *)rows_group_kernel<1024, 8, false, true>,
+        (const void *)rows_group_kernel<256, 4, true, false>, (const void *)rows_group_kernel<256, 8, true, false>,
+        (const void *)rows_group_kernel<1024, 8, true, false>, (const void *)rows_group_kernel<256, 4, false, false>,
+        (const void *)rows_group_kernel<256, 8, false, false>, (const void *)rows_group_kernel<1024, 8, false, false>,
+        row_fn<true>(true, 1), row_fn<true>(true, 2048), row_fn<true>(true, 4096),
         row_fn<true>(false, 1), row_fn<true>(false, 2048), row_fn<true>(false, 4096), row_fn<false>(true, 1),
         row_fn<false>(true, 2048), row_fn<false>(true, 4096), row_fn<false>(false, 1), row_fn<false>(false, 2048),
         row_fn<false>(false, 4096)};

@@ -7,7 +7,9 @@ memory and the L2), so after a batched sweep every victim's output is compared
 with the oracle: ten configuration-3 victims of uneven shapes (four GEMMs, one of
 676 output tiles on 148 SMs, so the last wave is ragged; two GEMVs, two softmax,
 two layernorm) beside a full HBM stream stressor and a full tensor-pipe stressor.
-Outputs are filled with NaN first, so an output the sweep never wrote fails.
+Outputs are filled with NaN first, so an output the sweep never wrote fails.  The
+same check runs on the grouped batched sweep, where victims of one row kernel share
+one persistent launch.
 """
 import numpy as np
 import pytest
@@ -59,7 +61,11 @@ def _check_gemm(i, shape, C_gpu, rng):
         assert np.linalg.norm(got - full) <= BF16_TOL * np.linalg.norm(full), i
 
 
-def test_batched_sweep_victim_outputs_match_oracle():
+# grouped: the two GEMVs, the two softmax and the two layernorm victims each run as one
+# grouped persistent launch that walks both victims' rows, and the GEMMs as two grouped
+# launches (one per tile width, one of them 682 tiles of two problems)
+@pytest.mark.parametrize("grouped", [False, True])
+def test_batched_sweep_victim_outputs_match_oracle(grouped):
     need_gpu()
     shapes = W.config3_shapes()
     with ifr.Context(0) as ctx:
@@ -72,12 +78,28 @@ def test_batched_sweep_victim_outputs_match_oracle():
         bufs = {"hbm": I.torch_u32_as_i32(1, (1 << 30) // 4, "cuda"), "l2": None}
         levels = [[W.stressor_level_cfg(A.IFR_S_HBM, S, bufs, seed=1)],
                   [W.stressor_level_cfg(A.IFR_S_TENSOR, S, bufs, seed=2)]]
-        cells = ctx.sweep(victims, levels, repeats=1, batched=True)
+        if grouped:
+            # the same sweep ungrouped first, for its launch count
+            n0 = ctx.launch_count()
+            ctx.sweep(victims, levels, repeats=1, batched=True)
+            ungrouped = ctx.launch_count() - n0
+            for i in SUBSET:
+                t[i][-1].fill_(float("nan"))
+        n0 = ctx.launch_count()
+        cells = ctx.sweep(victims, levels, repeats=1, batched=True, grouped=grouped)
+        launches = ctx.launch_count() - n0
         assert len(cells) == len(victims) * (1 + 2 * 2)
+        # every victim measured on its own record, also inside a grouped launch
+        assert all(c.timing.t_end_ns > c.timing.t_start_ns > 0 and c.timing.blocks > 0 for c in cells)
         co = [c for c in cells if c.stressor >= 0 and c.level == 1]
         assert all(c.stress.blocks_active == c.stress.planned_active > 0 for c in co)
         assert sum(c.valid for c in co) >= 0.8 * len(co)
         torch.cuda.synchronize()
+    if grouped:
+        # 5 graphs (solo, two levels of two stressors), each with 5 grouped launches in
+        # place of 10 single-victim launches (two GEMMs of each tile width, two GEMVs,
+        # two softmax, two layernorm)
+        assert launches == ungrouped - 5 * 5
     rng = np.random.default_rng(0)
     for i in SUBSET:
         kind, a, b, c = shapes[i]

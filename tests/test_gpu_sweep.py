@@ -140,3 +140,71 @@ def test_head_of_line_blocked_cell_is_recorded(setup):
     co = [c for c in cells if c.stressor == 0 and c.level == 1]
     assert co and not co[0].valid
     assert co[0].stress.status == A.IFR_ERR_HOL and co[0].status == A.IFR_ERR_HOL
+
+
+def test_grouped_solo_sweep_ragged_row_victims(setup):
+    """Grouped persistent victims on their own (no stressor): layernorm victims of one
+    template with 1, 7 and 3001 rows, two of them of a width that is not a multiple of
+    4 (a group of its own, the unaligned load path), softmax victims of one row and
+    2049 rows, GEMV victims of 9 and 4097 rows, and GEMMs of both tile widths (a
+    one-tile problem beside 2- to 150-tile ones; the 128-wide group holds more tiles
+    than the GPU has SMs); three launches each.  Every output
+    against the oracle, every victim on its own record, and a plan mode outside 0..2
+    refused."""
+    import oracle
+    from tests.gpu_common import BF16_TOL, assert_fp32_close
+
+    ctx = setup[0]
+    specs = [("ln", 1, 1024), ("ln", 7, 1024), ("ln", 3001, 1024), ("ln", 5, 1023), ("ln", 333, 1023),
+             ("sm", 1, 2048), ("sm", 2049, 2048), ("gemv", 9, 4096), ("gemv", 4097, 4096),
+             ("gemm", 256, 256, 64), ("gemm", 384, 640, 192), ("gemm", 2048, 1024, 1024), ("gemm", 128, 128, 64),
+             ("gemm", 1280, 1920, 256)]
+    victims, keep = [], []
+    for i, (k, rows, cols, *kk) in enumerate(specs):
+        if k == "gemm":
+            Ab = I.torch_normal_bf16(70 + i, rows * kk[0], "cuda").view(rows, kk[0])
+            Bb = I.torch_normal_bf16(90 + i, cols * kk[0], "cuda").view(cols, kk[0])
+            y = torch.full((rows, cols), float("nan"), device="cuda")
+            victims.append(ifr.victim_cfg(A.IFR_V_GEMM, Ab, Bb, y, m=rows, n=cols, k=kk[0], repeats=3))
+            inputs = (Ab, Bb)
+        elif k == "gemv":
+            Ab = I.torch_normal_bf16(70 + i, rows * cols, "cuda").view(rows, cols)
+            xb = I.torch_normal_bf16(90 + i, cols, "cuda")
+            y = torch.full((rows,), float("nan"), device="cuda")
+            victims.append(ifr.victim_cfg(A.IFR_V_GEMV, Ab, xb, y, m=rows, k=cols, repeats=3))
+            inputs = (Ab, xb)
+        else:
+            x = I.torch_uniform_pm1(70 + i, rows * cols, "cuda").view(rows, cols)
+            y = torch.full_like(x, float("nan"))
+            kind = A.IFR_V_LAYERNORM if k == "ln" else A.IFR_V_SOFTMAX
+            victims.append(ifr.victim_cfg(kind, x, None, y, m=rows, n=cols, repeats=3))
+            inputs = (x,)
+        keep.append((k, rows, cols, y, inputs))  # the configs hold raw pointers: keep the tensors
+    cells = ctx.sweep(victims, [], repeats=1, batched=True, grouped=True)
+    assert len(cells) == len(victims)
+    for c in cells:
+        assert c.valid and c.timing.t_end_ns > c.timing.t_start_ns and c.timing.blocks > 0
+    for i, (k, rows, cols, y, inputs) in enumerate(keep):
+        if k == "gemm":
+            ref = inputs[0].double().cpu() @ inputs[1].double().cpu().T
+            got = y.double().cpu()
+            rms = float(ref.pow(2).mean().sqrt())
+            assert bool(((got - ref).abs() <= BF16_TOL * torch.maximum(ref.abs(), torch.tensor(rms))).all()), i
+        elif k == "gemv":
+            A_np = oracle.f32_bits_to_bf16_bits(I.np_normal_bf16(70 + i, np.arange(rows * cols))).reshape(rows, cols)
+            x_np = oracle.f32_bits_to_bf16_bits(I.np_normal_bf16(90 + i, np.arange(cols)))
+            ref = oracle.gemv_rows(A_np, x_np, np.arange(rows))
+            got = y.cpu().numpy().astype(np.float64)
+            rms = np.sqrt(np.mean(ref * ref))
+            assert np.all(np.abs(got - ref) <= BF16_TOL * np.maximum(np.abs(ref), rms)), i
+        else:
+            xs = I.np_uniform_pm1(70 + i, np.arange(rows * cols)).reshape(rows, cols)
+            ref = oracle.layernorm_rows(xs, np.arange(rows), 1e-5) if k == "ln" else oracle.softmax_rows(
+                xs, np.arange(rows))
+            assert_fp32_close(y.cpu().numpy(), ref)
+    import ctypes as C
+
+    plan = A.ifr_sweep_plan(1, (A.ifr_victim_cfg * 1)(victims[0]), 0, 0, (A.ifr_stressor_cfg * 1)(), 1, 3)
+    out = (A.ifr_cell_result * 4)()
+    n = C.c_size_t(0)
+    assert A.load().ifr_sweep(ctx._h, C.byref(plan), out, 4, C.byref(n)) == A.IFR_ERR_ARG
