@@ -455,15 +455,19 @@ typedef struct {
     int32_t batched;                     /* 0: launch per cell; 1: one captured CUDA graph
                                             per (stressor, level) over all victims, each
                                             victim its own launches; 2: the same graphs
-                                            with grouped persistent victims: layernorm
-                                            and softmax victims of one row template, and
-                                            GEMV victims of more than 256 columns, run
-                                            as one launch per group (at most 32) that
-                                            walks their rows in order, each victim
-                                            still timed on its own (the spans of
-                                            neighbours overlap at the boundary); other
-                                            victims run alone.  Other values:
-                                            IFR_ERR_ARG */
+                                            with grouped persistent victims:
+                                            layernorm and softmax victims of one row
+                                            template, GEMV victims of more than 256
+                                            columns, and variant-0 GEMMs of one tile
+                                            width run as one launch per group (at most
+                                            16) whose walkers claim rows or tiles in
+                                            order and start a victim only after the
+                                            previous one has finished, each victim
+                                            timed on its own; other victims run alone.
+                                            Walkers that claim work on demand make the
+                                            victims less sensitive than their own
+                                            launches (mode 1 is the measurement mode).
+                                            Other values: IFR_ERR_ARG */
 } ifr_sweep_plan;
 
 typedef struct {

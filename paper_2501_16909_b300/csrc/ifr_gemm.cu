@@ -390,14 +390,17 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_kernel(const __grid
 // The grouped victims of a graph-batched sweep: up to IFR_GROUP_MAX GEMMs of
 // one tile width run as one persistent launch of variant 0's tiles (three stages, one
 // accumulator).  Units are the concatenation of the problems' tiles in order
-// (problem q owns units tile0[q] ..): the first unit of a CTA is its index, later
-// ones come from the device counter of problem 0's record, as in the single kernel,
-// so the CTAs move through the problems in order and neighbouring problems overlap
-// only at the boundary.  Each problem keeps its own measurement record: the producer
-// stamps entry at a tile's first K slice and the epilogue stamps exit (time, SM,
-// count) at a tile's end, so a problem's span runs from its first tile's start to its
-// last tile's end.  Waits are bounded as in the single kernel; a CTA that times out
-// records IFR_ERR_TIMEOUT in every problem's record.
+// (problem q owns units tile0[q] ..), every unit claimed from the device counter of
+// problem 0's record.  A producer that takes its first tile of problem q waits until
+// every tile of problem q - 1 is stored (the four epilogue warps of each tile count
+// themselves in problem q - 1's record), so the problems still run one after
+// another, as separate launches would, without the launch gaps; the wait cannot
+// deadlock, since every tile of an earlier problem was claimed before, by a running
+// CTA.  Each problem keeps its own measurement record: the producer stamps entry at a
+// tile's first K slice (after the wait) and each epilogue warp stamps exit at the
+// tile's end, so a problem's span runs from its first tile's start to its last tile's
+// end.  Waits are bounded as in the single kernel; a CTA that times out records
+// IFR_ERR_TIMEOUT in every problem's record.
 struct alignas(64) GemmProblem {
     CUtensorMap ta, tb;
     float *C;
@@ -413,6 +416,20 @@ __device__ __forceinline__ int group_problem(const GemmGroup &g, int u) {
     int q = 0;
     while (q + 1 < g.n && u >= g.p[q + 1].tile0) ++q;
     return q;
+}
+
+// Bounded wait (the producer thread) until every tile of problem q - 1 is stored.
+__device__ __forceinline__ bool group_wait_tiles(const GemmGroup &g, int q, uint64_t deadline) {
+    if (q == 0) return true;
+    const GemmProblem &pp = g.p[q - 1];
+    const uint32_t want = (uint32_t)(EPI_WARPS * pp.tiles_m * pp.tiles_n);
+    uint32_t it = 0;
+    while (*(const volatile uint32_t *)&pp.tm->done < want) {
+        if (ifr_gtimer() > deadline || ++it > (1u << 24)) return false;
+        __nanosleep(200);
+    }
+    __threadfence();
+    return true;
 }
 
 __device__ __forceinline__ void g_tile_exit(DevTiming *tm, bool count) {
@@ -475,7 +492,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_group_kernel(const 
 
     if (warp == 0 && lane == 0) {
         int64_t gs = 0;
-        uint32_t next = blockIdx.x;
+        uint32_t next = atomicAdd(&ctl->tile_next, 1u);
+        int waited = 0;  // problems before `waited` are known finished
         for (int j = 0;; ++j) {
             const int r = j % RING;
             if (j >= RING && !tc::mbar_wait(&sempty[r], (uint32_t)((j / RING) - 1) & 1u, deadline)) *fail = 1;
@@ -485,13 +503,17 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_group_kernel(const 
             if (unit < 0) break;
             const int q = group_problem(g, unit);
             const GemmProblem &pb = g.p[q];
+            if (q > waited) {
+                if (!group_wait_tiles(g, q, deadline)) *fail = 1;
+                waited = q;
+            }
             int tmi, tni;
             tile_coords(unit - pb.tile0, pb.tiles_m, pb.tiles_n, pb.group_m, tmi, tni);
             const int m0 = tmi * BM, n0 = tni * BN, KT = pb.K / BK;
             g_stamp(pb.tm, true);
             for (int kt = 0; kt < KT; ++kt, ++gs) {
                 const int s = (int)(gs % STAGES);
-                if (kt == KT - 1) next = gridDim.x + atomicAdd(&ctl->tile_next, 1u);
+                if (kt == KT - 1) next = atomicAdd(&ctl->tile_next, 1u);
                 if (gs >= STAGES && !tc::mbar_wait(&empty[s], (uint32_t)((gs / STAGES) - 1) & 1u, deadline)) {
                     *fail = 1;
                     break;
@@ -584,9 +606,14 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_group_kernel(const 
                 }
             }
             // every epilogue warp stamps the tile's end (the latest of the four is the
-            // tile's exit); warp 2 also counts the tile and its SM
+            // tile's exit) and counts itself for the ordering of the next problem;
+            // warp 2 also counts the tile and its SM
             __syncwarp();
-            if (lane == 0) g_tile_exit(pb.tm, warp == 2);
+            if (lane == 0) {
+                g_tile_exit(pb.tm, warp == 2);
+                __threadfence();
+                atomicAdd(&pb.tm->done, 1u);
+            }
         }
     }
     tc::fence_before();
@@ -600,6 +627,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_bf16_group_kernel(const 
     if (threadIdx.x == 0) {
         __threadfence();
         if (atomicAdd(&ctl->tile_done, 1u) == gridDim.x - 1u) {
+            for (int q = 0; q < g.n; ++q) atomicExch(&g.p[q].tm->done, 0u);
             atomicExch(&ctl->tile_next, 0u);
             atomicExch(&ctl->tile_done, 0u);
         }

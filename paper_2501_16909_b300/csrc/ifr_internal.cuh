@@ -76,6 +76,7 @@ struct DevTiming {
     uint64_t *progress;  // context-wide "last victim block entry/exit" (%globaltimer)
     uint32_t tile_next;  // GEMM: next output tile to hand out (0 between launches)
     uint32_t tile_done;  // GEMM: CTAs of the running launch that have finished
+    uint32_t done;       // grouped launches: rows (GEMM: tile-warps) of this victim finished
 };
 
 // Kernel parameters of a stressor launch (passed by value).

@@ -8,8 +8,8 @@
 // Batched mode, per (stressor, level): the same sequence with all victims
 // back to back under one stressor run, captured once into a CUDA graph and
 // replayed for every repeat; per-victim timings land in separate slots.  Grouped
-// batched mode: the same graphs, with victims of one row kernel run as one
-// persistent grouped launch that walks their rows (ifr_victims_enqueue_group).
+// batched mode: the same graphs, with victims of one kernel run as one persistent
+// grouped launch that walks their rows or tiles in order (ifr_victims_enqueue_group).
 #include <math.h>
 #include <string.h>
 #include <time.h>

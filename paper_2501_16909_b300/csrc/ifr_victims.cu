@@ -38,6 +38,7 @@ __global__ void timing_reset_kernel(DevTiming *tm, int n, uint64_t *progress) {
         tm[i].status = 0;
         tm[i].tile_next = 0u;
         tm[i].tile_done = 0u;
+        tm[i].done = 0u;
         for (int j = 0; j < IFR_MAX_SMS / 32; ++j) tm[i].sm_bits[j] = 0u;
     }
 }
@@ -518,12 +519,17 @@ const void *gemv_short_fn(int lanes) {
 // ------------------------------------------------------------------ grouped victims
 // A grouped launch runs several victims of one row kernel (one template: same block
 // shape and row capacity) as one persistent launch, for the graph-batched sweep: the
-// blocks (layernorm, softmax) or warps (GEMV) walk the concatenation of the victims'
-// rows in order, block or warp b taking rows b, b + G, ...  Each victim keeps its own
-// measurement record: a block or warp stamps entry when its walk enters a victim's
-// rows and exit when it leaves them, so a victim's span runs from the first entry into
-// its rows to the last exit from them (neighbouring victims overlap at the boundary,
-// as in any grouped kernel).  Row arithmetic is the single-victim kernels' own.
+// blocks (layernorm, softmax) or warps (GEMV) claim rows of the concatenation of the
+// victims' rows in order from a counter, and a walker that claims the first row it
+// takes of victim v waits until every row of victim v - 1 is finished, so the victims
+// still run one after another, as separate launches would, without the launch gaps.
+// Each victim keeps its own measurement record: a walker stamps entry when it starts
+// a victim's rows and exit when it leaves them.  Waiting cannot deadlock: every row
+// of an earlier victim was claimed before, by a walker that is running and finishes
+// it.  Waits are bounded; a walker that gives up records IFR_ERR_TIMEOUT and goes on.
+// The unit counter sits in victim 0's record, the finished-row counts in each
+// victim's; the last walker of a launch to finish returns them to zero.  Row
+// arithmetic is the single-victim kernels' own.
 struct RowVictim {
     const void *in0, *in1;
     void *out;
@@ -537,6 +543,7 @@ struct RowGroup {
     int64_t total;
     RowVictim v[IFR_GROUP_MAX];
 };
+constexpr uint64_t kGroupWaitNs = 2000000000ull;
 
 // The victim of global row r, searching forward from the walker's current one.
 __device__ __forceinline__ int group_victim(const RowGroup &g, int from, int64_t r) {
@@ -545,14 +552,49 @@ __device__ __forceinline__ int group_victim(const RowGroup &g, int from, int64_t
     return v;
 }
 
+// Bounded wait (one thread) until victim v - 1 of the group has finished all its rows.
+__device__ __forceinline__ void group_wait_prev(const RowGroup &g, int v, uint64_t deadline) {
+    if (v == 0) return;
+    const DevTiming *prev = g.v[v - 1].tm;
+    const uint32_t want = (uint32_t)g.v[v - 1].rows;
+    uint32_t it = 0;
+    while (*(const volatile uint32_t *)&prev->done < want) {
+        if (ifr_gtimer() > deadline || ++it > (1u << 24)) {
+            g.v[v].tm->status = IFR_ERR_TIMEOUT;
+            return;
+        }
+        __nanosleep(200);
+    }
+    __threadfence();
+}
+
+// The last walker of a grouped launch resets the group's counters for the next one.
+__device__ __forceinline__ void group_walker_done(const RowGroup &g, uint32_t walkers) {
+    DevTiming *ctl = g.v[0].tm;
+    __threadfence();
+    if (atomicAdd(&ctl->tile_done, 1u) == walkers - 1u) {
+        for (int v = 0; v < g.n; ++v) atomicExch(&g.v[v].tm->done, 0u);
+        atomicExch(&ctl->tile_next, 0u);
+        atomicExch(&ctl->tile_done, 0u);
+    }
+}
+
 template <int NT, int VPT, bool VEC, bool LN>
 __global__ void __launch_bounds__(NT) rows_group_kernel(const __grid_constant__ RowGroup g) {
     __shared__ float red[32];
+    __shared__ int64_t s_r;
+    const uint64_t deadline = ifr_gtimer() + kGroupWaitNs;
     int cur = -1;
-    for (int64_t r = blockIdx.x; r < g.total; r += gridDim.x) {
+    for (;;) {
+        if (threadIdx.x == 0) s_r = (int64_t)atomicAdd(&g.v[0].tm->tile_next, 1u);
+        __syncthreads();
+        const int64_t r = s_r;
+        if (r >= g.total) break;
         const int v = group_victim(g, cur, r);
         if (v != cur) {
-            if (cur >= 0) v_exit(g.v[cur].tm);
+            if (threadIdx.x == 0) group_wait_prev(g, v, deadline);
+            if (cur >= 0) v_exit(g.v[cur].tm);  // includes the block barrier after the wait
+            else __syncthreads();
             v_enter(g.v[v].tm);
             cur = v;
         }
@@ -564,8 +606,14 @@ __global__ void __launch_bounds__(NT) rows_group_kernel(const __grid_constant__ 
             layernorm_row<NT, VPT, VEC>(xr, yr, d.cols, d.eps, red);
         else
             softmax_row<NT, VPT, VEC>(xr, yr, d.cols, red);
+        __syncthreads();  // the row's stores are issued; s_r may be overwritten
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(&g.v[v].tm->done, 1u);
+        }
     }
     if (cur >= 0) v_exit(g.v[cur].tm);
+    if (threadIdx.x == 0) group_walker_done(g, gridDim.x);
 }
 
 // Per-warp stamps for the grouped GEMV, whose warps of one block can be in different
@@ -590,16 +638,22 @@ __device__ __forceinline__ void w_exit(DevTiming *tm, int lane) {
 }
 
 // Grouped GEMV (rows of more than 256 columns): one warp per row as in gemv_kernel,
-// with x read through the L1 (each victim has its own x, and the warps of a block can
-// be in different victims, so x is not staged per block).
+// each warp a walker, with x read through the L1 (each victim has its own x, and the
+// warps of a block can be in different victims, so x is not staged per block).
 __global__ void __launch_bounds__(256) gemv_group_kernel(const __grid_constant__ RowGroup g) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
-    int cur = -1;
-    for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; r < g.total; r += W) {
-        const int v = group_victim(g, cur, r);
+    const int lane = threadIdx.x & 31;
+    const uint64_t deadline = ifr_gtimer() + kGroupWaitNs;
+    int cur = -1, v = 0;
+    for (;;) {
+        int64_t r = 0;
+        if (lane == 0) r = (int64_t)atomicAdd(&g.v[0].tm->tile_next, 1u);
+        r = __shfl_sync(0xffffffffu, r, 0);
+        if (r >= g.total) break;
+        v = group_victim(g, cur, r);
         if (v != cur) {
+            if (lane == 0) group_wait_prev(g, v, deadline);
             if (cur >= 0) w_exit(g.v[cur].tm, lane);
+            __syncwarp();
             w_enter(g.v[v].tm, lane);
             cur = v;
         }
@@ -648,9 +702,14 @@ __global__ void __launch_bounds__(256) gemv_group_kernel(const __grid_constant__
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) ((float *)d.out)[r - d.row0] = acc;
+        if (lane == 0) {
+            ((float *)d.out)[r - d.row0] = acc;
+            __threadfence();
+            atomicAdd(&d.tm->done, 1u);
+        }
     }
     if (cur >= 0) w_exit(g.v[cur].tm, lane);
+    if (lane == 0) group_walker_done(g, gridDim.x * (blockDim.x >> 5));
 }
 
 // ------------------------------------------------------------------ histogram
@@ -989,6 +1048,7 @@ int ifr_victims_enqueue_group(ifr_ctx *ctx, const ifr_victim_cfg *const *vs, Dev
     }
     if (vs[0]->kind == IFR_V_GEMM) return ifr_gemm_enqueue_group(ctx, vs, tms, n, stream);
     g.total = row0;
+    if (g.total >= (1ll << 31)) return IFR_ERR_ARG;  // 32-bit unit counter
     const int64_t sms = ctx->info.num_sms;
     for (int rep = 0; rep < K; ++rep) {
         if (vs[0]->kind == IFR_V_GEMV) {

@@ -6,10 +6,12 @@
    workloads.config3_shapes) and the stressors' buffers;
 2. autotunes, per stressor kind, the launch shape of each target intensity l/L of
    its full-intensity rate (autotune.Tuner, +-5 %);
-3. runs the plain launch-per-cell sweep and the graph-batched sweep on the same
-   inputs and levels, timing each with the host clock around the ABI call;
-4. reports cells/s of both, the fraction of valid cells, and how closely the
-   two modes agree on each (victim, stressor, level) slowdown;
+3. runs the graph-batched sweep, the same with grouped persistent victims, and the
+   plain launch-per-cell sweep on the same inputs and levels, timing each with the
+   host clock around the ABI call;
+4. reports cells/s of each, the fraction of valid cells, and how closely each
+   batched mode agrees with the plain sweep on every (victim, stressor, level)
+   slowdown;
 5. optionally writes one JSON row per measured cell (raw timestamps included),
    the data the slowdown predictor is trained on.
 """
@@ -88,6 +90,13 @@ def main(argv=None):
     out["batched"] = {"cells": len(cb), "seconds": round(tb, 3), "cells_per_s": round(len(cb) / tb, 1),
                       "valid": sum(c.valid for c in cb), "hol": sum(1 for c in cb if c.status == A.IFR_ERR_HOL)}
     sd_b, t0b = slowdown_table(cb)
+    # the same graphs with grouped persistent victims
+    t0 = time.perf_counter()
+    cg = ctx.sweep(victims, lv_batched, a.repeats, batched=True, grouped=True)
+    tg = time.perf_counter() - t0
+    out["grouped"] = {"cells": len(cg), "seconds": round(tg, 3), "cells_per_s": round(len(cg) / tg, 1),
+                      "valid": sum(c.valid for c in cg), "hol": sum(1 for c in cg if c.status == A.IFR_ERR_HOL)}
+    sd_g, _ = slowdown_table(cg)
     if not a.skip_plain:
         t0 = time.perf_counter()
         cp = ctx.sweep(victims, lv_plain, a.repeats, batched=False)
@@ -96,11 +105,21 @@ def main(argv=None):
                         "valid": sum(c.valid for c in cp), "hol": sum(1 for c in cp if c.status == A.IFR_ERR_HOL)}
         out["batched_over_plain"] = round(out["batched"]["cells_per_s"] / out["plain"]["cells_per_s"], 3)
         sd_p, _ = slowdown_table(cp)
-        common = [k for k in sd_b if k in sd_p]
-        rel = sorted(abs(sd_b[k] / sd_p[k] - 1) for k in common)
-        if rel:
-            out["agreement"] = {"pairs": len(rel), "median_rel_diff": round(rel[len(rel) // 2], 4),
-                                "p90_rel_diff": round(rel[int(0.9 * (len(rel) - 1))], 4)}
+        out["grouped_over_plain"] = round(out["grouped"]["cells_per_s"] / out["plain"]["cells_per_s"], 3)
+        for name, sd in (("agreement", sd_b), ("agreement_grouped", sd_g)):
+            common = [k for k in sd if k in sd_p]
+            rel = sorted(abs(sd[k] / sd_p[k] - 1) for k in common)
+            if rel:
+                out[name] = {"pairs": len(rel), "median_rel_diff": round(rel[len(rel) // 2], 4),
+                             "p90_rel_diff": round(rel[int(0.9 * (len(rel) - 1))], 4)}
+                # per stressor kind: the median relative difference and the median of the
+                # mode's slowdown over the plain sweep's (above 1: the mode measures more)
+                per = {}
+                for k in common:
+                    per.setdefault(A.STRESSOR_NAMES[base[k[1]].kind], []).append(sd[k] / sd_p[k])
+                out[name]["by_kind"] = {kk: {"median_rel_diff": round(statistics.median(abs(x - 1) for x in v), 4),
+                                             "median_ratio": round(statistics.median(v), 4)}
+                                        for kk, v in per.items()}
     if a.out:
         with open(a.out, "w") as f:
             for c in ifr.cells_to_dicts(cb):
