@@ -95,16 +95,16 @@ class ClockSampler:
 _GEMM_SRC = ("paper_2501_16909_b300/csrc/ifr_gemm.cu",
              "e8b0c478e88782980fd46b3cd6ed4a1c2b0fd706db922701469cbc383f46822a")
 _STRESS_SRC = ("paper_2501_16909_b300/csrc/ifr_stressors.cu",
-               "858b425a2daa113157846bb21b0e573c6a56c91de8263c8e5e803f46cbf69386")
+               "5f4a6fc6cccadf7ff68c92fe11d2b26986921adcb29e645ead622bde8ab9284f")
 NCU_DRAM_BYTES = {
-    "sched": (4608 + 0,) + _STRESS_SRC,
-    "fma": (20992 + 0,) + _STRESS_SRC,
+    "sched": (4864 + 0,) + _STRESS_SRC,
+    "fma": (20736 + 0,) + _STRESS_SRC,
     "tensor": (47616 + 0,) + _STRESS_SRC,
-    "smem_cf": (17408 + 0,) + _STRESS_SRC,
-    "smem_32w": (18688 + 0,) + _STRESS_SRC,
-    "l2": (16794112 + 0,) + _STRESS_SRC,
-    "hbm": (2483067904 + 2713856,) + _STRESS_SRC,
-    "hbm_tma": (2502516480 + 2992384,) + _STRESS_SRC,
+    "smem_cf": (16896 + 0,) + _STRESS_SRC,
+    "smem_32w": (22528 + 0,) + _STRESS_SRC,
+    "l2": (16795648 + 0,) + _STRESS_SRC,
+    "hbm": (2483066624 + 2717952,) + _STRESS_SRC,
+    "hbm_tma": (2502484992 + 2684672,) + _STRESS_SRC,
     "gemm": (77078016 + 35707648,) + _GEMM_SRC,
     "gemm_v2": (75990528 + 40968448,) + _GEMM_SRC,
     "gemm_v3": (77721344 + 41471488,) + _GEMM_SRC,

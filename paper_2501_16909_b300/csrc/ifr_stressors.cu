@@ -221,13 +221,17 @@ __device__ __forceinline__ uint32_t ld_stream_word(const int4 *p) {
 // into L2 and from L2 into the SM (memory moves in sectors, not words); a word load
 // takes one register where a 16-byte load takes four.  Every loaded word enters the
 // fold (a load whose result nothing used would be dropped by the compiler).
-// BLK: the block size at compile time (128, 256, 512 or 1024), so the four loads of
+// BLK: the block size at compile time (128, 256 or 512), so the four loads of
 // a chunk address it with immediate offsets; 0 reads blockDim.x at run time and
 // takes every round chunk by chunk.  With BLK, a round whose R chunks need no wrap
 // to the block's first chunk (all but about one round in n_chunks / (A R)) issues its
 // R x 4 loads from one pointer with fixed offsets and folds them under one rotation;
-// a round that wraps takes the chunks one by one.  Chunk positions are 32-bit (the
-// host refuses sets of more than 2^30 chunks).  Measured against the same word loads
+// a round that wraps takes the chunks one by one.  The walk keeps one offset from the
+// block's first chunk, compared with the offset of its last (the host refuses sets of
+// more than 2^30 chunks, so counts fit 32 bits).  Every instantiation compiles to 32
+// registers, the budget that leaves room for a victim block beside a full-intensity
+// stressor.  (A launch bound asking for 2048 threads per SM gives the same count but
+// measured 5 % less L2 bandwidth: the compiler keeps fewer loads in flight.)  Measured against the same word loads
 // taken chunk by chunk with run-time offsets, in one process: 7.1 against 6.0-6.3
 // TB/s from HBM and 17.1-18.7 against 16.0-18.0 TB/s from L2 over four block shapes.
 template <int BLK>
@@ -244,23 +248,25 @@ __global__ void __launch_bounds__(BLK ? BLK : 1024)
     const int A = (int)p.planned;
     const int k = c.k;
     const int n_chunks = (int)p.n_chunks;
-    const int last = n_chunks - A;  // cpos >= last: the chunk after cpos is the block's first again
-    // the thread's first int4 of its first chunk; the stride of A chunks in int4
+    const bool has_work = k < n_chunks;
+    // the thread's first int4 of the block's first chunk (k); the block's chunks k,
+    // k + A, ..., k + (m - 1) A lie `stride` int4 apart, and `off` (int4 from `first`)
+    // walks them, back to 0 after the last one (off_last)
     const int4 *const first = p.buf + (int64_t)k * (4 * B) + threadIdx.x;
     const int64_t stride = (int64_t)A * (4 * B);
-    const int4 *src = first;
-    int cpos = k;
-    int64_t done = 0;
+    const int m = has_work ? (n_chunks - k + A - 1) / A : 1;
+    const int64_t off_last = (int64_t)(m - 1) * stride;
+    int64_t off = 0, done = 0;
     uint32_t pass = 0u, acc = 0u;
     int64_t round = 0;
-    const bool has_work = k < n_chunks;
     for (;; ++round) {
         if (threadIdx.x == 0) s_go[round & 1] = has_work ? round_decision(st, p, round, c) : 0;
         __syncthreads();
         if (!s_go[round & 1]) break;
         uint32_t v[R][4];
-        if (BLK && cpos + (R - 1) * A < last + A && cpos + (R - 1) * A >= 0) {
-            // chunks cpos, cpos + A, ..., cpos + (R - 1) A: all inside the cycle, one pass
+        if (BLK && off + (R - 1) * stride <= off_last) {
+            // R chunks in a row of the cycle, one pass
+            const int4 *src = first + off;
 #pragma unroll
             for (int r = 0; r < R; ++r)
 #pragma unroll
@@ -269,27 +275,26 @@ __global__ void __launch_bounds__(BLK ? BLK : 1024)
 #pragma unroll
             for (int r = 0; r < R; ++r) x ^= v[r][0] ^ v[r][1] ^ v[r][2] ^ v[r][3];
             acc ^= ifr_rotl(x, pass);
-            cpos += R * A;
-            src += R * stride;
-            if (cpos > last + A - 1) {
-                cpos = k;
-                src = first;
+            off += (R - 1) * stride;
+            if (off == off_last) {
+                off = 0;
                 ++pass;
+            } else {
+                off += stride;
             }
         } else if (BLK) {
             uint32_t ps[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
+                const int4 *src = first + off;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) v[r][u] = ld_stream_word(src + u * B);
                 ps[r] = pass;
-                if (cpos >= last) {
-                    cpos = k;
-                    src = first;
+                if (off == off_last) {
+                    off = 0;
                     ++pass;
                 } else {
-                    cpos += A;
-                    src += stride;
+                    off += stride;
                 }
             }
 #pragma unroll
@@ -299,18 +304,16 @@ __global__ void __launch_bounds__(BLK ? BLK : 1024)
             // registers where the offsets are not immediates)
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const int4 *q = src;
+                const int4 *q = first + off;
                 uint32_t x = 0u;
 #pragma unroll
                 for (int u = 0; u < 4; ++u, q += B) x ^= ld_stream_word(q);
                 acc ^= ifr_rotl(x, pass);
-                if (cpos >= last) {
-                    cpos = k;
-                    src = first;
+                if (off == off_last) {
+                    off = 0;
                     ++pass;
                 } else {
-                    cpos += A;
-                    src += stride;
+                    off += stride;
                 }
             }
         }
@@ -326,7 +329,6 @@ const void *stream_fn(int block) {
         case 128: return (const void *)stream_stress_kernel<128>;
         case 256: return (const void *)stream_stress_kernel<256>;
         case 512: return (const void *)stream_stress_kernel<512>;
-        case 1024: return (const void *)stream_stress_kernel<1024>;
         default: return (const void *)stream_stress_kernel<0>;
     }
 }
@@ -335,7 +337,6 @@ void launch_stream(int grid, int block, cudaStream_t stream, DevStress *st, cons
         case 128: stream_stress_kernel<128><<<grid, block, 0, stream>>>(st, p); break;
         case 256: stream_stress_kernel<256><<<grid, block, 0, stream>>>(st, p); break;
         case 512: stream_stress_kernel<512><<<grid, block, 0, stream>>>(st, p); break;
-        case 1024: stream_stress_kernel<1024><<<grid, block, 0, stream>>>(st, p); break;
         default: stream_stress_kernel<0><<<grid, block, 0, stream>>>(st, p);
     }
 }
@@ -1388,7 +1389,7 @@ extern "C" int ifr_stream_stressor_noalloc(int kind, const void *buf, int64_t wo
             // the three kernels now rather than lazily at their first launch
             void *ptr = nullptr;
             IFR_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
-            const void *fns[] = {(const void *)stress_reset_kernel, stream_fn(128), stream_fn(256), stream_fn(512), stream_fn(1024), stream_fn(0),
+            const void *fns[] = {(const void *)stress_reset_kernel, stream_fn(128), stream_fn(256), stream_fn(512), stream_fn(0),
                                  (const void *)noalloc_logs_clear_kernel};
             for (const void *f : fns) {
                 int rc = ifr_preload(f);
@@ -1430,7 +1431,7 @@ extern "C" int ifr_stream_stressor_noalloc(int kind, const void *buf, int64_t wo
 
 int ifr_preload_stressors() {
     const void *fns[] = {
-        (const void *)stress_reset_kernel, stream_fn(128), stream_fn(256), stream_fn(512), stream_fn(1024), stream_fn(0), stream_tma_fn(),
+        (const void *)stress_reset_kernel, stream_fn(128), stream_fn(256), stream_fn(512), stream_fn(0), stream_tma_fn(),
         (const void *)fma_stress_kernel<1>, (const void *)fma_stress_kernel<2>, (const void *)fma_stress_kernel<4>,
         (const void *)fma_stress_kernel<8>, (const void *)fp64_stress_kernel<1>, (const void *)fp64_stress_kernel<2>,
         (const void *)fp64_stress_kernel<4>, (const void *)fp64_stress_kernel<8>, smem_kernel_for(1),

@@ -28,7 +28,11 @@ from tests.gpu_common import need_gpu, spread_mask
 pytestmark = pytest.mark.gpu
 
 DUTIES = [0.25, 0.5, 0.75]
-PERIOD_NS = 50_000
+# duty periods: a round of the HBM stressor (8 chunks of 32 KiB per block, 296 blocks
+# streaming at full rate) takes about 12 us, so its period is longer, and its
+# on-window at D = 0.25 holds about four rounds; the FMA and shared-memory rounds are
+# short
+PERIOD_NS = {"hbm": 200_000, "fma": 50_000, "smem_cf": 50_000}
 
 
 @pytest.fixture(scope="module")
@@ -48,9 +52,12 @@ def hbm_buf():
 def _cases(ctx, hbm_buf):
     S = ctx.info["num_sms"]
     return {
-        # full SMs, 2 blocks of 512 per SM, 1 GiB set: a round is 8 chunks of 32 KiB per block
+        # full SMs, 2 blocks of 512 per SM, 1 GiB set: a round is 8 chunks of 32 KiB per
+        # block; 192 rounds run about 2.3 ms at full rate, so at D = 0.25 the run spans
+        # about 45 of its 200 us periods and the part of the last period it skips
+        # moves the rate by under 2 %
         "hbm": ifr.stressor_cfg(A.IFR_S_HBM, sm_count=S, blocks_per_sm=2, block=512, buf=hbm_buf,
-                                working_set_bytes=1 << 30, max_rounds=64, seed=0),
+                                working_set_bytes=1 << 30, max_rounds=192, seed=0),
         # 16 SMs, one warp of 4 chains each (the oracle recomputes every chain of every block)
         "fma": ifr.stressor_cfg(A.IFR_S_FMA, sm_count=16, blocks_per_sm=1, block=32, ilp=4, max_rounds=64, seed=7),
         # full SMs, 2 blocks of 256 per SM, conflict-free
@@ -89,12 +96,13 @@ def test_duty_cycle_rate_and_checksums(ctx, hbm_buf, name):
     hbuf = hbm_buf.cpu().numpy().view(np.uint32) if name == "hbm" else None
     rates = {}
     for d in [1.0] + DUTIES:
-        c = P.copy_cfg(cfg, duty=0.0 if d == 1.0 else d, period_ns=PERIOD_NS)
+        c = P.copy_cfg(cfg, duty=0.0 if d == 1.0 else d, period_ns=PERIOD_NS[name])
         rs = []
-        for _ in range(2):
+        for rep in range(2):
             res, logs = ctx.run_stressor(c, 20000)
             assert res["status"] == 0
-            _check_blocks(ctx, name, c, logs, hbuf)
+            if rep == 0:  # every block of the first run against the oracle
+                _check_blocks(ctx, name, c, logs, hbuf)
             rs.append(_rate(c, res))
         rates[d] = sum(rs) / len(rs)
     for d in DUTIES:

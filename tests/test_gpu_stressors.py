@@ -97,7 +97,7 @@ def test_stream_stressor_stop_flag_arbitrary_counts(ctx, staging):
 
 
 # every instantiation of the register-load kernel (block sizes fixed at compile time,
-# and 384 read at run time): 13 SMs x 2 blocks over 291 chunks, so each block cycles
+# and 384 and 1024 read at run time): 13 SMs x 2 blocks over 291 chunks, so each block cycles
 # through 11 or 12 chunks; 5 rounds of 8 chunks run whole rounds from one pointer and
 # rounds that wrap to the block's first chunk part-way, over 3 or 4 passes
 @pytest.mark.parametrize("block", [128, 256, 384, 512, 1024])
