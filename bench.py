@@ -93,7 +93,7 @@ class ClockSampler:
 # `gemm --variant {0,2,3}`), after the same command ran clean; the stressors' shapes
 # and rounds are those of the solo runs below, the GEMM is the same 4096^3 launch.
 _GEMM_SRC = ("paper_2501_16909_b300/csrc/ifr_gemm.cu",
-             "e8b0c478e88782980fd46b3cd6ed4a1c2b0fd706db922701469cbc383f46822a")
+             "d8eaf3b43e508a20b818daf30899f1ee96a391382bc47b48f399e40fd35408bb")
 _STRESS_SRC = ("paper_2501_16909_b300/csrc/ifr_stressors.cu",
                "5f4a6fc6cccadf7ff68c92fe11d2b26986921adcb29e645ead622bde8ab9284f")
 NCU_DRAM_BYTES = {
@@ -105,9 +105,9 @@ NCU_DRAM_BYTES = {
     "l2": (16795648 + 0,) + _STRESS_SRC,
     "hbm": (2483066624 + 2717952,) + _STRESS_SRC,
     "hbm_tma": (2502484992 + 2684672,) + _STRESS_SRC,
-    "gemm": (77078016 + 35707648,) + _GEMM_SRC,
-    "gemm_v2": (75990528 + 40968448,) + _GEMM_SRC,
-    "gemm_v3": (77721344 + 41471488,) + _GEMM_SRC,
+    "gemm": (75722496 + 35376896,) + _GEMM_SRC,
+    "gemm_v2": (77870080 + 40004608,) + _GEMM_SRC,
+    "gemm_v3": (76908032 + 41671168,) + _GEMM_SRC,
 }
 
 

@@ -12,8 +12,9 @@ provides the peaks:
 * tensor     flop/s  — SMs x 8192 flop per clock x max SM clock (the pipe's dense rate)
 * shared mem wavefronts/s — SMs x 1 wavefront per clock x max SM clock
 * scheduler  blocks/s — probe: zero-cycle 32-thread blocks on every SM
-* FP64       flop/s  — probe: best fp64 multiply-chain rate on every SM over
-                        occupancy and ILP (one multiply = one flop)
+* FP64       flop/s  — SMs x 2 fp64 multiplies per clock x max SM clock (B300's
+                        1.25 TFLOP/s dense FP64 figure, an FMA counted as two
+                        flops; the stressor counts one multiply as one flop)
 """
 from __future__ import annotations
 
@@ -37,6 +38,7 @@ CAL_ROUNDS = {A.IFR_S_HBM: 32, A.IFR_S_L2: 128, A.IFR_S_FMA: 32, A.IFR_S_TENSOR:
 # Dense BF16 tcgen05 rate of one SM per clock: 4096 multiply-adds (NVIDIA's 2.25
 # PFLOP/s dense BF16 for 148 SMs corresponds to 8192 flop per clock at 1.86 GHz).
 TENSOR_FLOP_PER_CLK = 8192
+FP64_OPS_PER_CLK = 2  # fp64 multiplies (or FMAs) per clock per SM
 
 # The L2's peak, from ncu on B300 (--clock-control none): for a kernel streaming an
 # L2-resident set, lts__t_bytes.sum.per_second / lts__lts2xbar_cycles_active.avg
@@ -124,14 +126,11 @@ def peaks(ctx, l2_buf=None):
     }
     out[A.IFR_S_L2] = (L2_PEAK_BYTES_PER_S, "ncu: L2-to-crossbar ports fully busy (lts__t_bytes rate over "
                                             "lts__lts2xbar_cycles_active, B300)")
-    best = (0.0, "")
-    for bps, ilp in ((4, 4), (8, 4), (4, 8), (8, 8)):
-        cfg = stressor_cfg(A.IFR_S_FP64, sm_count=S, blocks_per_sm=bps, block=256, ilp=ilp)
-        rate, _ = solo_rate(ctx, cfg, rounds=8)
-        if rate > best[0]:
-            best = (rate, "probe: best fp64 multiply-chain rate over 4 / 8 blocks of 256 and ILP 4 / 8 on every "
-                          "SM (%d blocks, ILP %d)" % (bps, ilp))
-    out[A.IFR_S_FP64] = best
+    # B300's dense FP64 figure, 1.25 TFLOP/s with an FMA counted as two flops, is two
+    # fp64 operations per clock per SM at the maximum clock; the stressor counts one
+    # multiply as one flop, so its peak is two multiplies per clock per SM
+    out[A.IFR_S_FP64] = (S * FP64_OPS_PER_CLK * clk, "nominal: SMs x 2 fp64 multiplies per clock (the 1.25 "
+                                                      "TFLOP/s dense FP64 figure, FMAs) x max SM clock")
     cfg = stressor_cfg(A.IFR_S_SCHED, sm_count=S, sched_blocks=100000, sched_cycles=1)
     rate, _ = solo_rate(ctx, cfg, launches=8)
     out[A.IFR_S_SCHED] = (rate, "probe: 1-cycle 32-thread blocks on every SM")
