@@ -767,6 +767,34 @@ def solo_kernel_rooflines(ctx, bufs, pk):
     return out
 
 
+def invalid_cells(cells, base, vkinds, A, cap=8):
+    """The first `cap` cells that fail the constant-interference rule, each with the
+    part of the rule it failed: the victim's or the stressor's own status, a stressor
+    with no active block, a stressor block that started after the victim's first
+    block, or one that ended before the victim's last block."""
+    out = []
+    for c in cells:
+        if c.valid:
+            continue
+        t, s = c.timing, c.stress
+        if t.status != 0:
+            why = "victim status %d" % t.status
+        elif s.status != 0:
+            why = "stressor status %d" % s.status
+        elif s.blocks_active <= 0:
+            why = "no active stressor block"
+        elif s.t_start_last_ns > t.t_start_ns:
+            why = "stressor block started %.1f us after the victim" % ((s.t_start_last_ns - t.t_start_ns) / 1e3)
+        else:
+            why = "stressor block ended %.1f us before the victim" % ((t.t_end_ns - s.t_end_first_ns) / 1e3)
+        out.append({"victim": int(c.victim), "victim_kind": A.VICTIM_NAMES[vkinds[c.victim]],
+                    "stressor": A.STRESSOR_NAMES[base[c.stressor].kind] if c.stressor >= 0 else None,
+                    "level": int(c.level), "reason": why})
+        if len(out) >= cap:
+            break
+    return out
+
+
 def run_config3(args):
     """Configuration 3 (the workload the batched-vs-plain metric is defined on): 64
     victims of uneven shapes x 7 stressor kinds x 8 autotuned intensities + level 0.
@@ -1003,6 +1031,9 @@ def run_config3(args):
         "stressor_peaks": {k: {"peak": v["peak"], "unit": v["unit"], "source": v["peak_source"]}
                            for k, v in solo["stressors"].items()},
         "cells_valid": {"batched": valid_b, "grouped": valid_g, "plain": valid_p}, "cells_total": len(last[2]),
+        "cells_invalid": {m: invalid_cells(last[i], base, vkinds, A)
+                          for m, i in (("batched", 2), ("grouped", 6), ("plain", 3))
+                          if any(not c.valid for c in last[i])},
         "cells_hol": sum(1 for c in last[3] if c.status == A.IFR_ERR_HOL),
         "predictor": pred,
         "sweep_gpu_ms_by_kernel": {k: round(v, 2) for k, v in sorted(busy.items(), key=lambda x: -x[1])},

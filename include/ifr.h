@@ -199,9 +199,8 @@ int ifr_stressor_release(ifr_ctx *ctx, int handle);
 
 /* Allocation-free fixed-work run of the L2/HBM stream stressor (the paper has no
  * counterpart: this is a convenience of the library).  Some callers cannot call
- * cudaMalloc: code running while a stream is being captured into a CUDA graph in a
- * mode that rejects allocation calls, latency-critical loops that must not block
- * on the device allocator (cudaMalloc can synchronise the device), and hosts that
+ * cudaMalloc: latency-critical loops that must not block on the device allocator
+ * (cudaMalloc can synchronise the device), and hosts that
  * own a fixed device-memory budget and so never create an ifr_ctx (ifr_init
  * allocates).  This entry point needs no context and allocates nothing: its
  * control state (stop flag, counters, per-SM claim table) is a 4 KiB file-scope

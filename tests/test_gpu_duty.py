@@ -31,8 +31,11 @@ DUTIES = [0.25, 0.5, 0.75]
 # duty periods: a round of the HBM stressor (8 chunks of 32 KiB per block, 296 blocks
 # streaming at full rate) takes about 12 us, so its period is longer, and its
 # on-window at D = 0.25 holds about four rounds; the FMA and shared-memory rounds are
-# short
-PERIOD_NS = {"hbm": 200_000, "fma": 50_000, "smem_cf": 50_000}
+# short.  A run that ends inside an on-window leaves the rest of its last period
+# (up to (1 - D) * P) out of its span, so the rate reads high by at most
+# (1 - D) * P / span: the shared-memory run lasts about 100 us at duty 1 (400 us at
+# D = 0.25), so its period is 20 us (at most 4 % at D = 0.25; at 50 us it was 9 %)
+PERIOD_NS = {"hbm": 200_000, "fma": 50_000, "smem_cf": 20_000}
 
 
 @pytest.fixture(scope="module")

@@ -1,8 +1,8 @@
 """GPU test of the allocation-free stream-stressor entry point.
 
-Callers that cannot call cudaMalloc (graph-capture code paths that reject
-allocation calls, latency-critical loops that must not block on the allocator,
-hosts with a fixed device-memory budget and no library context) use
+Callers that cannot call cudaMalloc (latency-critical loops that must not block
+on the allocator, hosts with a fixed device-memory budget and no library
+context) use
 ifr_stream_stressor_noalloc, whose control state lives in a file-scope device
 array.  Its per-block results must equal those of the context-based entry point
 (ifr_stressor_launch + ifr_stressor_wait + ifr_stressor_block_logs) for the same
