@@ -95,16 +95,16 @@ class ClockSampler:
 _GEMM_SRC = ("paper_2501_16909_b300/csrc/ifr_gemm.cu",
              "d8eaf3b43e508a20b818daf30899f1ee96a391382bc47b48f399e40fd35408bb")
 _STRESS_SRC = ("paper_2501_16909_b300/csrc/ifr_stressors.cu",
-               "5f4a6fc6cccadf7ff68c92fe11d2b26986921adcb29e645ead622bde8ab9284f")
+               "c13572fbd7a891a1dd68b6828df840a846bf37f2088ed8f036847aae98549ba6")
 NCU_DRAM_BYTES = {
-    "sched": (4864 + 0,) + _STRESS_SRC,
-    "fma": (20736 + 0,) + _STRESS_SRC,
-    "tensor": (47616 + 0,) + _STRESS_SRC,
+    "sched": (8960 + 0,) + _STRESS_SRC,
+    "fma": (70144 + 0,) + _STRESS_SRC,
+    "tensor": (47360 + 0,) + _STRESS_SRC,
     "smem_cf": (16896 + 0,) + _STRESS_SRC,
-    "smem_32w": (22528 + 0,) + _STRESS_SRC,
-    "l2": (16795648 + 0,) + _STRESS_SRC,
-    "hbm": (2483066624 + 2717952,) + _STRESS_SRC,
-    "hbm_tma": (2502484992 + 2684672,) + _STRESS_SRC,
+    "smem_32w": (18944 + 0,) + _STRESS_SRC,
+    "l2": (16795904 + 0,) + _STRESS_SRC,
+    "hbm": (2483067648 + 2719232,) + _STRESS_SRC,
+    "hbm_tma": (2502470656 + 2906624,) + _STRESS_SRC,
     "gemm": (75722496 + 35376896,) + _GEMM_SRC,
     "gemm_v2": (77870080 + 40004608,) + _GEMM_SRC,
     "gemm_v3": (76908032 + 41671168,) + _GEMM_SRC,
@@ -787,6 +787,10 @@ def invalid_cells(cells, base, vkinds, A, cap=8):
             why = "stressor block started %.1f us after the victim" % ((s.t_start_last_ns - t.t_start_ns) / 1e3)
         else:
             why = "stressor block ended %.1f us before the victim" % ((t.t_end_ns - s.t_end_first_ns) / 1e3)
+            if base[c.stressor].kind == A.IFR_S_SCHED:
+                # blocks that worked: those on allowed SMs that started before the stop
+                # request, so a chain that ran out before the victim ended shows no idle tail
+                why += " (%d of %d launched blocks worked)" % (s.work, s.blocks_launched)
         out.append({"victim": int(c.victim), "victim_kind": A.VICTIM_NAMES[vkinds[c.victim]],
                     "stressor": A.STRESSOR_NAMES[base[c.stressor].kind] if c.stressor >= 0 else None,
                     "level": int(c.level), "reason": why})

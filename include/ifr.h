@@ -166,6 +166,11 @@ typedef struct {
     int32_t planned_active;  /* sm_count * blocks_per_sm (work-split stride) */
     double elapsed_ms;       /* cudaEvent time from launch to completion */
 } ifr_stressor_result;
+/* SCHED (a chain of short-block launches): t_start_ns = t_start_last_ns is the start
+ * of the chain's first working block (its first 4096 blocks, and one in 256 after
+ * them, record their starts); one block in 256 records its end, and t_end_ns =
+ * t_end_first_ns is the later of the last recorded end and the first time a recorded
+ * block saw the stop request (the chain was still running then). */
 
 typedef struct {
     uint64_t t_start_ns, t_end_ns; /* %globaltimer at block entry / exit */

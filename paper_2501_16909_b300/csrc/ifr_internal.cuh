@@ -62,6 +62,7 @@ struct DevStress {
     int32_t status;       // first error
     uint64_t t_origin;    // SCHED: first block start (deadline origin)
     uint64_t t_first_start, t_last_end;  // SCHED sampled window
+    uint64_t t_stop_seen;                // SCHED: earliest sampled block that saw the stop request (~0: none)
     uint32_t sm_claim[IFR_MAX_SMS];
     uint32_t sched_xor[64];
     uint32_t sched_cnt[64];

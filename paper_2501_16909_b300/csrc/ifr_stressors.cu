@@ -80,6 +80,7 @@ __global__ void stress_reset_kernel(DevStress *st) {
         st->t_origin = 0ull;
         st->t_first_start = ~0ull;
         st->t_last_end = 0ull;
+        st->t_stop_seen = ~0ull;
     }
 }
 
@@ -105,6 +106,17 @@ __device__ int claim_slot(DevStress *st, const StressParams &p, uint32_t sm) {
             __nanosleep(256);
     }
     return k;
+}
+
+// Sleep part of the way toward a %globaltimer target `left` ns away.  __nanosleep's
+// duration is approximate (the PTX ISA allows anything up to twice the request), so
+// a request of the whole distance can wake a block microseconds late, and blocks
+// sharing an SM then start their on-phases apart (one of them runs alone, faster
+// than beside its sibling, and the stressor does more than D x its full-rate work).
+// Half the distance (at most 20 us) never passes the target; the last microsecond
+// is polled.
+__device__ __forceinline__ void sleep_toward(uint64_t left) {
+    if (left > 1000u) __nanosleep((unsigned)(left > 40000u ? 20000u : left / 2));
 }
 
 // Thread 0 only: should the block run round `round`?  Sleeps through the
@@ -164,8 +176,7 @@ __device__ int round_decision(DevStress *st, const StressParams &p, int64_t roun
                     return 0;
                 }
                 if (ifr_ld_volatile(&st->stop) || ++it > kMaxSpin) return 0;
-                const uint64_t left = d.next - now;
-                __nanosleep((unsigned)(left > 20000u ? 20000u : left));
+                sleep_toward(d.next - now);
                 now = ifr_gtimer();
             }
         }
@@ -571,8 +582,7 @@ __global__ void __launch_bounds__(1024) sleep_stress_kernel(DevStress *st, Stres
                         break;
                     }
                     if (ifr_ld_volatile(&st->stop) || ++it > kMaxSpin) break;
-                    const uint64_t left = until - now;
-                    __nanosleep((unsigned)(left > 20000u ? 20000u : left));
+                    sleep_toward(until - now);
                 }
             }
             s_go[round & 1] = go;
@@ -792,9 +802,19 @@ __global__ void __launch_bounds__(32) sched_stress_kernel(DevStress *st, StressP
         if (origin == 0ull) origin = now;
         if (now > origin + p.deadline_ns) {
             atomicCAS(&st->status, 0, IFR_ERR_TIMEOUT);
-        } else if (!ifr_ld_volatile(&st->stop) && sm_allowed(p, ifr_smid())) {
+        } else if (ifr_ld_volatile(&st->stop)) {
+            // The chain was still being dispatched when the stop request came (the
+            // sweeps request it after the victim's end): sampled blocks record when
+            // they saw it.  The sampled working-block ends alone can fall short of the
+            // victim's end by the gap between two samples.  (Reductions whose result
+            // is unused: no round trip lengthens a block.)
+            if ((q & 255) == 0) atomicMin((unsigned long long *)&st->t_stop_seen, (unsigned long long)now);
+        } else if (sm_allowed(p, ifr_smid())) {
             work = 1;
-            if ((q & 255) == 0) atomicMin((unsigned long long *)&st->t_first_start, (unsigned long long)now);
+            // the chain's first 4096 blocks all record their start, so that its first
+            // working block is seen whatever SMs the level allows; later ones sample
+            if (q < 4096 || (q & 255) == 0)
+                atomicMin((unsigned long long *)&st->t_first_start, (unsigned long long)now);
         }
     }
     work = __shfl_sync(0xffffffffu, work, 0);
@@ -1236,7 +1256,8 @@ int ifr_stressor_collect(ifr_ctx *ctx, int slot) {
         r.sms_used = 0;
         if (cnt > 0) {
             r.t_start_ns = r.t_start_last_ns = h.t_first_start;
-            r.t_end_ns = r.t_end_first_ns = h.t_last_end;
+            const bool seen = h.t_stop_seen != ~0ull && h.t_stop_seen > h.t_last_end;
+            r.t_end_ns = r.t_end_first_ns = seen ? h.t_stop_seen : h.t_last_end;
         }
         s.h_nlogs = 0;
         s.finished = 1;
