@@ -95,16 +95,16 @@ class ClockSampler:
 _GEMM_SRC = ("paper_2501_16909_b300/csrc/ifr_gemm.cu",
              "d8eaf3b43e508a20b818daf30899f1ee96a391382bc47b48f399e40fd35408bb")
 _STRESS_SRC = ("paper_2501_16909_b300/csrc/ifr_stressors.cu",
-               "c13572fbd7a891a1dd68b6828df840a846bf37f2088ed8f036847aae98549ba6")
+               "48212933b9817087877f2b6920a820d95c637c710ff0d5fa102e800e58ad713f")
 NCU_DRAM_BYTES = {
-    "sched": (8960 + 0,) + _STRESS_SRC,
-    "fma": (70144 + 0,) + _STRESS_SRC,
-    "tensor": (47360 + 0,) + _STRESS_SRC,
+    "sched": (4864 + 0,) + _STRESS_SRC,
+    "fma": (20736 + 0,) + _STRESS_SRC,
+    "tensor": (55552 + 0,) + _STRESS_SRC,
     "smem_cf": (16896 + 0,) + _STRESS_SRC,
-    "smem_32w": (18944 + 0,) + _STRESS_SRC,
+    "smem_32w": (19456 + 0,) + _STRESS_SRC,
     "l2": (16795904 + 0,) + _STRESS_SRC,
-    "hbm": (2483067648 + 2719232,) + _STRESS_SRC,
-    "hbm_tma": (2502470656 + 2906624,) + _STRESS_SRC,
+    "hbm": (2483070464 + 2704128,) + _STRESS_SRC,
+    "hbm_tma": (2502476288 + 2944512,) + _STRESS_SRC,
     "gemm": (75722496 + 35376896,) + _GEMM_SRC,
     "gemm_v2": (77870080 + 40004608,) + _GEMM_SRC,
     "gemm_v3": (76908032 + 41671168,) + _GEMM_SRC,

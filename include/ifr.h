@@ -166,11 +166,10 @@ typedef struct {
     int32_t planned_active;  /* sm_count * blocks_per_sm (work-split stride) */
     double elapsed_ms;       /* cudaEvent time from launch to completion */
 } ifr_stressor_result;
-/* SCHED (a chain of short-block launches): t_start_ns = t_start_last_ns is the start
- * of the chain's first working block (its first 4096 blocks, and one in 256 after
- * them, record their starts); one block in 256 records its end, and t_end_ns =
- * t_end_first_ns is the later of the last recorded end and the first time a recorded
- * block saw the stop request (the chain was still running then). */
+/* SCHED (a chain of short-block launches): one working block in 256 records its start
+ * and end; t_start_ns = t_start_last_ns is the first recorded start, and t_end_ns =
+ * t_end_first_ns is the later of the last recorded end and the first time one block
+ * in 4096 saw the stop request (the chain was still running then). */
 
 typedef struct {
     uint64_t t_start_ns, t_end_ns; /* %globaltimer at block entry / exit */
@@ -485,7 +484,11 @@ typedef struct {
 /* Run the plan: per repeat, solo runs of every victim, then for every stressor
  * and level 0..L a colocated measurement of every victim.  Writes up to `cap`
  * cells in that order and sets *n_out.  Errors: IFR_ERR_ARG, IFR_ERR_CAPACITY,
- * IFR_ERR_CUDA.  A cell whose stressor timed out is recorded with valid = 0. */
+ * IFR_ERR_CUDA.  A cell whose stressor timed out is recorded with valid = 0.  In the
+ * plain sweep (batched = 0), a scheduler-stressor cell whose chain of launches ended
+ * before the victim did (the rule's only failure) is measured again with four times
+ * the launches, at most three times (16384 launches at most); the cell keeps the
+ * last measurement. */
 int ifr_sweep(ifr_ctx *ctx, const ifr_sweep_plan *plan, ifr_cell_result *cells, size_t cap, size_t *n_out);
 
 /* ---- kernel-with-kernel colocation (Sec. 4.1; Table 3 seq/col speedup) ---- */

@@ -118,6 +118,7 @@ struct Slot {
     cudaEvent_t ev_reset;  // recorded after the state reset; victims wait on it
     int grid, block, planned, launches;
     int watch;             // watch the context's victim-progress word (sweeps)
+    int any_sm;            // the launch's SM mask allows at least one SM of the device
     cudaStream_t stream;
     ifr_stressor_result result;
     ifr_block_log *h_logs;

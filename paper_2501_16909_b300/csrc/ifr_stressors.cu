@@ -110,11 +110,8 @@ __device__ int claim_slot(DevStress *st, const StressParams &p, uint32_t sm) {
 
 // Sleep part of the way toward a %globaltimer target `left` ns away.  __nanosleep's
 // duration is approximate (the PTX ISA allows anything up to twice the request), so
-// a request of the whole distance can wake a block microseconds late, and blocks
-// sharing an SM then start their on-phases apart (one of them runs alone, faster
-// than beside its sibling, and the stressor does more than D x its full-rate work).
-// Half the distance (at most 20 us) never passes the target; the last microsecond
-// is polled.
+// a request of the whole distance can wake a block microseconds late.  Half the
+// distance (at most 20 us) never passes the target; the last microsecond is polled.
 __device__ __forceinline__ void sleep_toward(uint64_t left) {
     if (left > 1000u) __nanosleep((unsigned)(left > 40000u ? 20000u : left / 2));
 }
@@ -804,17 +801,15 @@ __global__ void __launch_bounds__(32) sched_stress_kernel(DevStress *st, StressP
             atomicCAS(&st->status, 0, IFR_ERR_TIMEOUT);
         } else if (ifr_ld_volatile(&st->stop)) {
             // The chain was still being dispatched when the stop request came (the
-            // sweeps request it after the victim's end): sampled blocks record when
-            // they saw it.  The sampled working-block ends alone can fall short of the
-            // victim's end by the gap between two samples.  (Reductions whose result
-            // is unused: no round trip lengthens a block.)
-            if ((q & 255) == 0) atomicMin((unsigned long long *)&st->t_stop_seen, (unsigned long long)now);
+            // sweeps request it after the victim's end): one block in 4096 records
+            // when it saw it.  The sampled working-block ends alone can fall short of
+            // the victim's end by the gap between two samples.  (A reduction whose
+            // result is unused, so no block waits for a round trip; the samples are
+            // sparse because every record of the chain goes to one address.)
+            if ((q & 4095) == 0) atomicMin((unsigned long long *)&st->t_stop_seen, (unsigned long long)now);
         } else if (sm_allowed(p, ifr_smid())) {
             work = 1;
-            // the chain's first 4096 blocks all record their start, so that its first
-            // working block is seen whatever SMs the level allows; later ones sample
-            if (q < 4096 || (q & 255) == 0)
-                atomicMin((unsigned long long *)&st->t_first_start, (unsigned long long)now);
+            if ((q & 255) == 0) atomicMin((unsigned long long *)&st->t_first_start, (unsigned long long)now);
         }
     }
     work = __shfl_sync(0xffffffffu, work, 0);
@@ -833,14 +828,20 @@ __global__ void __launch_bounds__(32) sched_stress_kernel(DevStress *st, StressP
 // its planned SM slots are claimed (`planned` > 0): the occupancy-sized grid's surplus
 // blocks exit as soon as they arrive after that, and waiting for every one of them to
 // arrive was seen on B300 to hold the victim back until the stressor had finished.
-// Without planned slots (the zero-SM level, the scheduler stressor) it waits for
-// `expected` arrivals.
-__global__ void wait_resident_kernel(DevStress *st, uint32_t expected, uint32_t planned, uint64_t timeout_ns,
-                                     DevTiming *tm) {
+// A scheduler chain with allowed SMs (`first_work`) is resident once a recorded
+// working block has started, so the victim never starts before the start the chain
+// reports.  Otherwise (the zero-SM level) it waits for `expected` arrivals.
+__device__ __forceinline__ bool stressor_ready(DevStress *st, uint32_t expected, uint32_t planned, int first_work) {
+    if (first_work) return *(volatile unsigned long long *)&st->t_first_start != ~0ull;
+    return planned > 0 ? ifr_ld_volatile(&st->active) >= planned : ifr_ld_volatile(&st->arrived) >= expected;
+}
+
+__global__ void wait_resident_kernel(DevStress *st, uint32_t expected, uint32_t planned, int first_work,
+                                     uint64_t timeout_ns, DevTiming *tm) {
     if (threadIdx.x != 0) return;
     const uint64_t t0 = ifr_gtimer();
     uint32_t it = 0;
-    while (planned > 0 ? ifr_ld_volatile(&st->active) < planned : ifr_ld_volatile(&st->arrived) < expected) {
+    while (!stressor_ready(st, expected, planned, first_work)) {
         if (ifr_gtimer() - t0 > timeout_ns || ++it > kMaxSpin) {
             if (tm) tm->status = IFR_ERR_NOT_RESIDENT;
             break;
@@ -1101,6 +1102,8 @@ int ifr_stressor_enqueue(ifr_ctx *ctx, const ifr_stressor_cfg *cfg, cudaStream_t
         ifr_compute_mask(num_sms, num_sms, p.mask);  // every SM id: the partition confines
     else
         ifr_compute_mask(num_sms, cfg->sm_count, p.mask);
+    s.any_sm = 0;
+    for (int i = 0; i < num_sms && i < IFR_MAX_SMS; ++i) s.any_sm |= (int)((p.mask[i >> 5] >> (i & 31)) & 1u);
     p.planned = cfg->sm_count * p.bps;
     p.seed = cfg->seed;
     p.max_rounds = cfg->max_rounds;
@@ -1214,8 +1217,9 @@ int ifr_enqueue_wait_resident(ifr_ctx *ctx, int slot, cudaStream_t stream, DevTi
     IFR_CUDA(cudaStreamWaitEvent(stream, s.ev_reset, 0));
     ifr_carveout((const void *)wait_resident_kernel);
     const uint32_t planned = s.cfg.kind == IFR_S_SCHED ? 0u : (uint32_t)s.planned;
+    const int first_work = s.cfg.kind == IFR_S_SCHED && s.any_sm;
     wait_resident_kernel<<<1, 32, 0, stream>>>(s.d_state, (uint32_t)ifr_stressor_expected_arrivals(s), planned,
-                                               timeout_ns, tm);
+                                               first_work, timeout_ns, tm);
     IFR_CUDA(cudaGetLastError());
     ctx->kernel_launches += 1;
     return IFR_OK;

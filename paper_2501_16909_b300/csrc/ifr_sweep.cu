@@ -21,6 +21,7 @@
 namespace {
 
 constexpr uint64_t kResidencyTimeoutNs = 200000000ull;  // 200 ms
+constexpr int kSchedRetryMaxLaunches = 16384;              // longest scheduler chain of a re-measured cell
 
 int wait_event_bounded(cudaEvent_t ev, int timeout_ms) {
     int waited_us = 0;
@@ -33,6 +34,16 @@ int wait_event_bounded(cudaEvent_t ev, int timeout_ms) {
     }
     if (q != cudaSuccess) return ifr_cuda_fail(q, "cudaEventQuery", __FILE__, __LINE__);
     return IFR_OK;
+}
+
+// A scheduler chain is a fixed number of launches.  One that ended before the
+// victim did (the victim's blocks, held off the SMs by the chain's flood, then ran
+// at once) fails the constant-interference rule at the end only.
+bool sched_chain_short(const ifr_stressor_cfg &sc, const ifr_cell_result &c) {
+    const ifr_timing &t = c.timing;
+    const ifr_stressor_result &s = c.stress;
+    return sc.kind == IFR_S_SCHED && c.level > 0 && !c.valid && t.status == IFR_OK && s.status == IFR_OK &&
+           s.blocks_active > 0 && s.t_start_last_ns <= t.t_start_ns && s.t_end_first_ns < t.t_end_ns;
 }
 
 void fill_validity(ifr_cell_result &c) {
@@ -544,6 +555,16 @@ extern "C" int ifr_sweep(ifr_ctx *ctx, const ifr_sweep_plan *p, ifr_cell_result 
                         rc = measure_cell_plain(ctx, &p->victims[v], &sc, &c);
                         if (rc) return rc;
                         fill_validity(c);
+                        // a chain too short for this victim: measure again with four
+                        // times the launches, at most three times
+                        ifr_stressor_cfg longer = sc;
+                        for (int retry = 0; retry < 3 && sched_chain_short(longer, c); ++retry) {
+                            const int n = longer.sched_launches ? longer.sched_launches : 64;
+                            longer.sched_launches = n < kSchedRetryMaxLaunches / 4 ? 4 * n : kSchedRetryMaxLaunches;
+                            rc = measure_cell_plain(ctx, &p->victims[v], &longer, &c);
+                            if (rc) return rc;
+                            fill_validity(c);
+                        }
                     }
                 }
         }

@@ -50,6 +50,29 @@ def _check(cells, n_levels, repeats):
     return got
 
 
+def test_plain_sched_chain_too_short_is_measured_again(setup):
+    """A scheduler chain far shorter than its victim (one launch of 4096 blocks beside
+    a triad repeated 8 times) ends before the victim, the constant-interference rule's
+    one failure.  The plain sweep measures that cell again with 4, 16 and 64 launches
+    until the chain outlasts the victim, and the cell keeps the last measurement."""
+    ctx, victims, _, _ = setup
+    S = ctx.info["num_sms"]
+    sb = 4096
+    lv = [[ifr.stressor_cfg(A.IFR_S_SCHED, sm_count=S, sched_blocks=sb, sched_launches=1, sched_cycles=100,
+                            seed=2)]]
+    cells = ctx.sweep(victims, lv, repeats=1, batched=False)
+    cc = [c for c in cells if c.stressor == 0 and c.level == 1]
+    assert len(cc) == 1
+    c = cc[0]
+    launches = c.stress.blocks_launched // sb
+    assert c.stress.blocks_launched == launches * sb and launches in (4, 16, 64), launches
+    assert c.valid or launches == 64
+    d = ifr.cells_to_dicts([c])[0]
+    assert c.valid == (1 if R.cell_valid(d) else 0)
+    if c.valid:
+        assert c.stress.t_start_last_ns <= c.timing.t_start_ns and c.stress.t_end_first_ns >= c.timing.t_end_ns
+
+
 def test_plain_sweep_config1(setup):
     ctx, victims, levels, _ = setup
     cells = ctx.sweep(victims, levels, repeats=3, batched=False)
