@@ -33,11 +33,12 @@ DUTIES = [0.25, 0.5, 0.75]
 # on-window at D = 0.25 holds about four rounds; the FMA and shared-memory rounds are
 # short.  Two effects move a fixed-work rate above D: a run that ends inside an
 # on-window leaves the rest of its last period (up to (1 - D) * P) out of its span,
-# and a duty-cycled stressor does about 1 us of full-rate work per period beyond
-# D * P (measured: the shared-memory stressor read 10 % high at D = 0.25 with a 50 us
-# period, 20 % with 20 us).  The shared-memory run (2 blocks per SM, rounds of about
-# 1.6 us) therefore does 1024 rounds (1.6 ms at duty 1) with a 200 us period: at
-# D = 0.25 the first effect is at most 2.3 % and the second about 2 %.
+# and blocks that share an SM keep separate budgets, so one of them sometimes runs
+# alone, faster than beside its sibling (measured: the shared-memory stressor with 2
+# blocks per SM read 10 % high at D = 0.25 with a 50 us period, 19 % with 20 us; with
+# one block per SM, 1 % low).  The shared-memory run (2 blocks per SM, rounds of
+# about 16 us) therefore does 1024 rounds (17 ms at duty 1) with a 200 us period: at
+# D = 0.25 the first effect is at most 0.3 % and the second about 2 %.
 PERIOD_NS = {"hbm": 200_000, "fma": 50_000, "smem_cf": 200_000}
 
 
