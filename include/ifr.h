@@ -487,8 +487,8 @@ typedef struct {
  * IFR_ERR_CUDA.  A cell whose stressor timed out is recorded with valid = 0.  In the
  * plain sweep (batched = 0), a scheduler-stressor cell whose chain of launches ended
  * before the victim did (the rule's only failure) is measured again with four times
- * the launches, at most three times (16384 launches at most); the cell keeps the
- * last measurement. */
+ * the launches, at most three times and up to 16384 launches (a chain already that
+ * long is not measured again); the cell keeps the last measurement. */
 int ifr_sweep(ifr_ctx *ctx, const ifr_sweep_plan *plan, ifr_cell_result *cells, size_t cap, size_t *n_out);
 
 /* ---- kernel-with-kernel colocation (Sec. 4.1; Table 3 seq/col speedup) ---- */

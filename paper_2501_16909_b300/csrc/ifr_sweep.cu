@@ -37,8 +37,8 @@ int wait_event_bounded(cudaEvent_t ev, int timeout_ms) {
 }
 
 // A scheduler chain is a fixed number of launches.  One that ended before the
-// victim did (the victim's blocks, held off the SMs by the chain's flood, then ran
-// at once) fails the constant-interference rule at the end only.
+// victim did (no recorded block saw the stop request, which follows the victim)
+// fails the constant-interference rule at the end only.
 bool sched_chain_short(const ifr_stressor_cfg &sc, const ifr_cell_result &c) {
     const ifr_timing &t = c.timing;
     const ifr_stressor_result &s = c.stress;
@@ -560,7 +560,9 @@ extern "C" int ifr_sweep(ifr_ctx *ctx, const ifr_sweep_plan *p, ifr_cell_result 
                         ifr_stressor_cfg longer = sc;
                         for (int retry = 0; retry < 3 && sched_chain_short(longer, c); ++retry) {
                             const int n = longer.sched_launches ? longer.sched_launches : 64;
-                            longer.sched_launches = n < kSchedRetryMaxLaunches / 4 ? 4 * n : kSchedRetryMaxLaunches;
+                            const int m = n < kSchedRetryMaxLaunches / 4 ? 4 * n : kSchedRetryMaxLaunches;
+                            if (m <= n) break;
+                            longer.sched_launches = m;
                             rc = measure_cell_plain(ctx, &p->victims[v], &longer, &c);
                             if (rc) return rc;
                             fill_validity(c);
