@@ -81,6 +81,9 @@ def test_plain_sweep_config1(setup):
     # harness-only launch (level 0) does not slow the victim; the full HBM stressor does
     assert abs(sd[0] - 1.0) <= 3 * got["noise"] + 0.1
     assert sd[3] > 1.2
+    # the slowdown is monotone in the HBM stressor's intensity (0, 25, 50, 100 % of
+    # the SMs), within three times the solo noise
+    assert got["monotone"] == [1], sd
     # every colocated cell recorded a running stressor
     for c in cells:
         if c.stressor >= 0 and c.level > 0:
@@ -92,6 +95,7 @@ def test_batched_sweep_config1(setup):
     cells = ctx.sweep(victims, levels, repeats=3, batched=True)
     got = _check(cells, 3, 3)
     assert got["slowdown"][0][3] > 1.2
+    assert got["monotone"] == [1], got["slowdown"][0]
 
 
 def test_corun_two_kernels_valid_and_consistent(setup):
