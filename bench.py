@@ -85,26 +85,29 @@ class ClockSampler:
 
 
 # DRAM bytes (read + write) per launch of the roofline kernels from ncu captures of
-# the same launch shape, each with the SHA-256 of the kernel's source file at capture
-# time; when that file has changed since, the line reports null instead.  Captured
-# with `ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
+# the same launch shape, each with the SHA-256 of the files that define the launch at
+# capture time (the kernel's source; for the stressors also the module that sets
+# their shapes); when one of them has changed since, the line reports null instead.
+# Captured with `ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
 # --clock-control none -k regex:<kernel> -c 1 python -m paper_2501_16909_b300.profile_case
 # <case>` (cases sched, fma, tensor, smem_cf, smem_32w, l2, hbm, `hbm --staging 1`,
 # `gemm --variant {0,2,3}`), after the same command ran clean; the stressors' shapes
 # and rounds are those of the solo runs below, the GEMM is the same 4096^3 launch.
-_GEMM_SRC = ("paper_2501_16909_b300/csrc/ifr_gemm.cu",
-             "d8eaf3b43e508a20b818daf30899f1ee96a391382bc47b48f399e40fd35408bb")
-_STRESS_SRC = ("paper_2501_16909_b300/csrc/ifr_stressors.cu",
-               "48212933b9817087877f2b6920a820d95c637c710ff0d5fa102e800e58ad713f")
+_GEMM_SRC = ((("paper_2501_16909_b300/csrc/ifr_gemm.cu",
+               "d8eaf3b43e508a20b818daf30899f1ee96a391382bc47b48f399e40fd35408bb"),),)
+_STRESS_SRC = ((("paper_2501_16909_b300/csrc/ifr_stressors.cu",
+                 "48212933b9817087877f2b6920a820d95c637c710ff0d5fa102e800e58ad713f"),
+                ("paper_2501_16909_b300/workloads.py",
+                 "1745acd7eabd2e2a5e4d5cbf6edecfb64f956ed8117fbc55fdcfd96fe2f01ad4")),)
 NCU_DRAM_BYTES = {
-    "sched": (4864 + 0,) + _STRESS_SRC,
-    "fma": (20736 + 0,) + _STRESS_SRC,
-    "tensor": (55552 + 0,) + _STRESS_SRC,
-    "smem_cf": (16896 + 0,) + _STRESS_SRC,
-    "smem_32w": (19456 + 0,) + _STRESS_SRC,
+    "sched": (4608 + 0,) + _STRESS_SRC,
+    "fma": (20480 + 0,) + _STRESS_SRC,
+    "tensor": (47616 + 0,) + _STRESS_SRC,
+    "smem_cf": (17152 + 0,) + _STRESS_SRC,
+    "smem_32w": (18944 + 0,) + _STRESS_SRC,
     "l2": (16795904 + 0,) + _STRESS_SRC,
-    "hbm": (2483070464 + 2704128,) + _STRESS_SRC,
-    "hbm_tma": (2502476288 + 2944512,) + _STRESS_SRC,
+    "hbm": (2483070208 + 2708736,) + _STRESS_SRC,
+    "hbm_tma": (2502471424 + 3041024,) + _STRESS_SRC,
     "gemm": (75722496 + 35376896,) + _GEMM_SRC,
     "gemm_v2": (77870080 + 40004608,) + _GEMM_SRC,
     "gemm_v3": (76908032 + 41671168,) + _GEMM_SRC,
@@ -123,8 +126,8 @@ def ncu_traffic(name):
     e = NCU_DRAM_BYTES.get(name)
     if not e:
         return None
-    nbytes, src, sha = e
-    return nbytes if _src_sha(src) == sha else None
+    nbytes, srcs = e
+    return nbytes if all(_src_sha(f) == h for f, h in srcs) else None
 
 
 def dist_env():

@@ -74,9 +74,12 @@ STRESSOR_DEFAULTS = {
     A.IFR_S_TENSOR: dict(blocks_per_sm=1),
     A.IFR_S_SMEM_CF: dict(block=256, blocks_per_sm=2),
     A.IFR_S_SMEM_32W: dict(block=256, blocks_per_sm=2),
-    # four blocks of 256 hold the same threads and registers per SM as two of 512 and
-    # stream 17.2 TB/s from the L2 against 14.2 (B300, same box)
-    A.IFR_S_L2: dict(block=256, blocks_per_sm=4),
+    # two blocks of 512 hold the same threads and registers per SM as four of 256;
+    # with the word-load stream kernel they keep the L2-to-crossbar ports 76.3 % busy
+    # against 73.0 %, at the same ALU share (9.4 % against 9.3 %; ncu, B300, same box).
+    # One block of 1024 reached 78.6 % but runs the kernel with its block size read at
+    # run time, whose per-chunk fold takes the ALU to 12.4 %.
+    A.IFR_S_L2: dict(block=512, blocks_per_sm=2),
     A.IFR_S_HBM: dict(block=512, blocks_per_sm=2),
     # two blocks of 256, 8 chains each: the fp64 pipe 84.0 % active (ncu) against 80.0 %
     # for the paper's one 128-thread block per SM with 4 chains (Sec. 4.4.3), which the
